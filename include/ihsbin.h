@@ -1,0 +1,211 @@
+/* ihsbin.h -- C ABI of a GB300 (sm_103a) implementation of IHS-BIN, the iterative
+ * Hessian sketch with binomial decomposition of Wang & Pilanci, "Sketching the
+ * Krylov Subspace: Faster Computation of the Entire Ridge Regularization Path".
+ *
+ * Problem (Section 1, eq. 1):  x*(lam) = argmin 1/2||A x - b||^2 + lam/2 ||x||^2
+ *                                       = (A^T A + lam I)^-1 A^T b,
+ * for every lam of a grid Lambda in [lambda_min, lambda_max]; matrix-valued
+ * right-hand sides B (n x K) per Section 5.3; under-determined A (n < d)
+ * through the dual of Section 5.2 (x = A^T z).
+ *
+ * Call order on a problem:  ihsbin_sketch -> ihsbin_build_basis -> ihsbin_eval_path
+ * (eval may be repeated with any lambdas inside the range).  Any other order
+ * returns IHSBIN_ERR_STATE.
+ *
+ * Conventions for every call:
+ *  - returns an ihsbin_status; no C++ exception crosses the ABI and no device
+ *    kernel traps: faults detected on the device (non-positive pivot, NaN)
+ *    come back through a device status word read at the call's synchronisation
+ *    point;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream); every call is stream-ordered and returns after its own work on
+ *    that stream has completed (the status word is read there);
+ *  - on error, outputs are unspecified and the problem keeps its previous state;
+ *  - ihsbin_last_error() returns a thread-local description of the last error.
+ */
+#ifndef IHSBIN_H
+#define IHSBIN_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IHSBIN_API __attribute__((visibility("default")))
+#else
+#define IHSBIN_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IHSBIN_OK = 0,
+  IHSBIN_ERR_INVALID_ARG = 1,
+  IHSBIN_ERR_OUT_OF_MEMORY = 2,
+  IHSBIN_ERR_CUDA = 3,
+  IHSBIN_ERR_NOT_SPD = 4,      /* a factor of (SA)^T SA + lam0 I had a non-positive pivot  */
+  IHSBIN_ERR_LAMBDA_RANGE = 5, /* a requested lambda lies outside [lambda_min, lambda_max] */
+  IHSBIN_ERR_STATE = 6,        /* call out of order                                      */
+  IHSBIN_ERR_TIMEOUT = 7,      /* a bounded wait expired                                 */
+  IHSBIN_ERR_ADMISSION = 8,    /* request larger than the device-memory budget           */
+  IHSBIN_ERR_UNSUPPORTED = 9,
+  IHSBIN_ERR_NAN = 11          /* a non-finite value was produced on the device          */
+} ihsbin_status;
+
+/* Element type of caller-provided arrays. */
+typedef enum { IHSBIN_F64 = 0, IHSBIN_F32 = 1, IHSBIN_BF16 = 2 } ihsbin_dtype;
+
+/* Arithmetic of the accuracy-critical contractions (Gram, preconditioner,
+ * basis loop, right-hand side, path evaluation):
+ *  IHSBIN_COMPUTE_F64  IEEE double throughout;
+ *  IHSBIN_COMPUTE_F32X2 float-float pairs (about 44 significant bits) built from
+ *                      error-free transformations on the FP32 pipe; the
+ *                      sketch itself is applied in FP64 (Gaussian, SRHT) or
+ *                      with FP64 accumulation (CountSketch). */
+typedef enum { IHSBIN_COMPUTE_F64 = 0, IHSBIN_COMPUTE_F32X2 = 1 } ihsbin_compute;
+
+typedef enum { IHSBIN_DENSE_ROWMAJOR = 0, IHSBIN_CSR = 1 } ihsbin_layout;
+
+/* Section 3: Gaussian N(0, 1/m); CountSketch (s = 1) / SJLT (s > 1 stacked
+ * CountSketches of m/s rows, entries +-1/sqrt(s)); SRHT (1/sqrt(m)) R H D on
+ * the rows zero-padded to a power of two. */
+typedef enum { IHSBIN_SK_GAUSSIAN = 0, IHSBIN_SK_SRHT = 1, IHSBIN_SK_COUNTSKETCH = 2 } ihsbin_sketch_kind;
+
+/* How A^T (A V) is formed inside the basis loop (Algorithm 2):
+ *  IHSBIN_PRODUCT_AUTO   GRAM for dense A, ASPACE for CSR;
+ *  IHSBIN_PRODUCT_GRAM   form G = A^T A once, then every product is G V;
+ *  IHSBIN_PRODUCT_ASPACE stream A twice per step: W = A V, Y = A^T W. */
+typedef enum { IHSBIN_PRODUCT_AUTO = 0, IHSBIN_PRODUCT_GRAM = 1, IHSBIN_PRODUCT_ASPACE = 2 } ihsbin_product;
+
+/* The data matrix A (n x d).  Borrowed: when on_device = 1 the arrays must stay
+ * valid until the problem is destroyed; when on_device = 0 they are copied
+ * during ihsbin_problem_create.
+ *  dense: `values` row-major with row stride `ld` (>= d) elements of `dtype`;
+ *  CSR:   row_ptr[n+1] (int64), col_idx[nnz] (int32, sorted within each row,
+ *         no duplicates), values[nnz] of `dtype`. */
+typedef struct {
+  int64_t n, d;
+  ihsbin_layout layout;
+  ihsbin_dtype dtype;
+  const void* values;
+  int64_t ld;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  int64_t nnz;
+  int on_device;
+} ihsbin_matrix;
+
+typedef struct {
+  ihsbin_sketch_kind kind;
+  int64_t m;     /* sketch rows (m % s == 0 for CountSketch/SJLT)           */
+  int32_t s;     /* SJLT sparsity; 1 = CountSketch; ignored for other kinds */
+  uint64_t seed; /* Philox4x32-10 key                                       */
+} ihsbin_sketch_desc;
+
+/* Interval plan and iteration parameters (Section 4.2, Theorem 4).
+ *  L        number of intervals; 0 selects floor(2 ln(lambda_max/lambda_min)) (at least 1).
+ *           Interval l covers [lambda_min beta^(l/L), lambda_min beta^((l+1)/L)),
+ *           the last one closed; lam0_l is the geometric mean of its ends.
+ *  k        per-interval term counts k_l (array of L), or NULL to use k_default.
+ *  rho1/rho2 per-interval eigenvalue bounds of the sketched Hessian (arrays of L),
+ *           or NULL to use rho: rho1 = (1+sqrt rho)^2, rho2 = (1-sqrt rho)^2
+ *           (Gaussian-sketch theorem with ||D||_2 = 1); rho <= 0 selects
+ *           min(D/m, 0.81) with D the dimension of the (dual) unknown.
+ *  tau_l = 2 lam0_l / (lo_l/rho1_l + hi_l/rho2_l)   (Theorem 4, from its proof).
+ *  jmax     0 keeps every basis term utilde_0..utilde_{k-1} (Algorithm 2); a
+ *           positive value keeps only the terms j < jmax.  The recursion for
+ *           j < jmax is unchanged, so the result differs from the full basis
+ *           only by the omitted high-order terms of the expansion in
+ *           theta = tau (lam - lam0) / lam0. */
+typedef struct {
+  double lambda_min, lambda_max;
+  int32_t L;
+  const int32_t* k;
+  int32_t k_default;
+  const double* rho1;
+  const double* rho2;
+  double rho;
+  int32_t jmax;
+  ihsbin_compute compute;
+  ihsbin_product product;
+} ihsbin_path_desc;
+
+typedef struct ihsbin_ctx ihsbin_ctx;
+typedef struct ihsbin_problem ihsbin_problem;
+
+/* Library context bound to CUDA device `device`.  hbm_budget_bytes caps the
+ * device memory all problems of this context may hold (0 = no cap); a problem
+ * that would exceed it fails with IHSBIN_ERR_ADMISSION.  Owned by the caller;
+ * release with ihsbin_ctx_destroy after every problem of it is destroyed. */
+IHSBIN_API ihsbin_status ihsbin_ctx_create(int device, uint64_t hbm_budget_bytes, ihsbin_ctx** out);
+IHSBIN_API ihsbin_status ihsbin_ctx_destroy(ihsbin_ctx* ctx);
+/* Bytes of device memory currently held by the context's problems. */
+IHSBIN_API ihsbin_status ihsbin_ctx_memory(const ihsbin_ctx* ctx, uint64_t* bytes_in_use);
+IHSBIN_API const char* ihsbin_last_error(void);
+
+/* Create a problem for A and right-hand side(s) B (n x K, row stride ldb >= K,
+ * element type b_dtype, host or device per b_on_device; copied).  If n < d the
+ * problem is solved through the dual (Section 5.2).  Allocates the problem's
+ * device state (counted against the context budget).  Release with
+ * ihsbin_problem_destroy. */
+IHSBIN_API ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, const void* B,
+                                    int64_t K, int64_t ldb, ihsbin_dtype b_dtype, int b_on_device,
+                                    ihsbin_problem** out);
+IHSBIN_API ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p);
+
+/* Step a1 of the hot path: S A_hat (m x D) for the sketch of Section 3 and
+ * its Gram (S A_hat)^T (S A_hat), where A_hat = A (over-determined) or A^T
+ * (under-determined).  Re-sketching an already sketched problem discards the
+ * basis. */
+IHSBIN_API ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream);
+
+/* Bit-exact export of the sketch's integer draws, for tests.
+ *  SRHT:        idx[0..m) = kept rows of H (ascending), sign[0..N_pad) = diagonal of D;
+ *  CountSketch: idx[i*s+t] = row of S hit by input row i in block t, sign[i*s+t];
+ *  Gaussian:    nothing (count = 0).
+ * `cap` bounds both arrays; *count receives the number of idx entries. */
+IHSBIN_API ihsbin_status ihsbin_sketch_export(ihsbin_problem* p, int64_t* idx, int8_t* sign, int64_t cap,
+                                   int64_t* count);
+
+/* Copy S A_hat (m x D, row-major FP64) and/or its Gram (D x D) to host arrays
+ * (either may be NULL), for tests. */
+IHSBIN_API ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* SA, double* GS);
+
+/* Steps a2-a4: per interval, the factor of (S A_hat)^T S A_hat + lam0_l I and
+ * its explicit inverse P_l; the right-hand side c = A^T B (dual: c = B); then
+ * Algorithm 2 / 5 (Proposition 1's recursion, re-centred at lam0_l):
+ *   u_00 = P c;  for i = 1..k_l-1:  u_i = -lam0 P u_{i-1},
+ *   u_j <- u_j - P(tau (A^T A u_j + lam0 u_j) + lam0 u_{j-1})  (j = i-1..1),
+ *   u_0 <- u_0 - P tau (A^T A u_0 + lam0 u_0),  utilde_j += u_j.
+ * The bases stay resident on the device until the problem is destroyed. */
+IHSBIN_API ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* desc, void* stream);
+
+/* The plan the library derived from the descriptor: arrays of L (edges: L+1),
+ * any may be NULL; *L_out receives L.  Fails with INVALID_ARG if cap_L < L. */
+IHSBIN_API ihsbin_status ihsbin_plan_export(ihsbin_problem* p, double* edges, double* lam0, double* tau,
+                                 int32_t* k, int32_t* jcount, int32_t cap_L, int32_t* L_out);
+
+/* Copy interval l's basis utilde_j (j < jcount_l) to host as FP64, layout
+ * [j][r][i] (D x K per term); *need receives the element count. */
+IHSBIN_API ihsbin_status ihsbin_basis_export(ihsbin_problem* p, int32_t l, double* buf, int64_t cap,
+                                  int64_t* need);
+
+/* Steps a5-a6: X(:, :, t) = tau_l sum_j theta_t^j utilde_j with
+ * theta_t = tau_l (lambdas[t] - lam0_l) / lam0_l for the interval l holding
+ * lambdas[t] (Algorithm 3 / 6 composition); for an under-determined problem
+ * the primal x = A^T z is returned.  lambdas: host array of T doubles.  X:
+ * T x d x K row-major per lambda (element [t][i][r]), caller-owned, on the
+ * device or host per x_on_device, element type F64 or F32.  Any lambda outside
+ * [lambda_min, lambda_max] fails with IHSBIN_ERR_LAMBDA_RANGE before anything
+ * is written. */
+IHSBIN_API ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t T, void* X,
+                               ihsbin_dtype x_dtype, int x_on_device, void* stream);
+
+/* Device time (ms) of the phases of the last sketch / build_basis / eval_path
+ * calls: [0] sketch, [1] factor+inverse, [2] Gram+rhs, [3] basis loop, [4] eval. */
+IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IHSBIN_H */

@@ -1,0 +1,529 @@
+// extern "C" entry points of libihsbin (declared in include/ihsbin.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace ihsbin;
+
+namespace {
+
+thread_local std::string g_err;
+
+ihsbin_status fail(ihsbin_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+ihsbin_status cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation) return fail(IHSBIN_ERR_OUT_OF_MEMORY, std::string(where) + ": out of device memory");
+  if (e == cudaErrorNotSupported) return fail(IHSBIN_ERR_UNSUPPORTED, std::string(where) + ": combination not supported");
+  if (e == cudaErrorInvalidValue && g_err.rfind("admission", 0) == 0) return IHSBIN_ERR_ADMISSION;
+  return fail(IHSBIN_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+thread_local std::vector<DevBuf>* g_scratch = nullptr;
+
+size_t elem_size(int dt) { return dt == IHSBIN_F64 ? 8 : dt == IHSBIN_F32 ? 4 : 2; }
+
+void free_list(ihsbin_problem* p, std::vector<DevBuf>& v) {
+  std::lock_guard<std::mutex> g(p->ctx->mu);
+  for (auto& b : v) {
+    cudaFree(b.p);
+    p->ctx->in_use -= b.bytes;
+  }
+  v.clear();
+}
+
+struct ScratchScope {  // frees the call's scratch allocations when the call returns
+  ihsbin_problem* p;
+  std::vector<DevBuf> bufs;
+  explicit ScratchScope(ihsbin_problem* pp) : p(pp) { g_scratch = &bufs; }
+  ~ScratchScope() {
+    g_scratch = nullptr;
+    free_list(p, bufs);
+  }
+};
+
+// Status word check after a synchronisation point.
+ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  int s = 0;
+  e = cudaMemcpy(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, where);
+  if (s != 0) {
+    cudaMemset(p->status, 0, sizeof(int));
+    if (s == DEV_NOT_SPD) return fail(IHSBIN_ERR_NOT_SPD, std::string(where) + ": non-positive pivot in a factor of (SA)^T SA + lam0 I");
+    if (s == DEV_NAN) return fail(IHSBIN_ERR_NAN, std::string(where) + ": non-finite value on the device");
+    return fail(IHSBIN_ERR_CUDA, std::string(where) + ": device status " + std::to_string(s));
+  }
+  return IHSBIN_OK;
+}
+
+}  // namespace
+
+namespace ihsbin {
+
+cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
+  *out = nullptr;
+  if (bytes == 0) bytes = 16;
+  {
+    std::lock_guard<std::mutex> g(p->ctx->mu);
+    if (p->ctx->budget && p->ctx->in_use + bytes > p->ctx->budget) {
+      g_err = "admission: request exceeds the context's device-memory budget";
+      return cudaErrorInvalidValue;
+    }
+    p->ctx->in_use += bytes;
+  }
+  cudaError_t e = cudaMalloc(out, bytes);
+  if (e != cudaSuccess) {
+    std::lock_guard<std::mutex> g(p->ctx->mu);
+    p->ctx->in_use -= bytes;
+    *out = nullptr;
+    return e;
+  }
+  DevBuf b{*out, bytes};
+  if (scope == SCOPE_SCRATCH && g_scratch) g_scratch->push_back(b);
+  else if (scope == SCOPE_PERSIST) p->owned.push_back(b);
+  else p->basis_bufs.push_back(b);
+  return cudaSuccess;
+}
+
+CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaError_t* err) {
+  CBuf b;
+  if (*err != cudaSuccess) return b;
+  cudaError_t e;
+  if (compute == IHSBIN_COMPUTE_F64) {
+    e = prob_alloc(p, elems * 8, &b.p0, scope);
+  } else {
+    e = prob_alloc(p, elems * 4, &b.p0, scope);
+    if (e == cudaSuccess) e = prob_alloc(p, elems * 4, &b.p1, scope);
+  }
+  if (e != cudaSuccess) *err = e;
+  return b;
+}
+
+void prob_free_basis(ihsbin_problem* p) {
+  free_list(p, p->basis_bufs);
+  p->G = CBuf{};
+  p->Pinv = CBuf{};
+  p->Ut = CBuf{};
+  p->W = CBuf{};
+  p->built = false;
+}
+
+}  // namespace ihsbin
+
+extern "C" {
+
+const char* ihsbin_last_error(void) { return g_err.c_str(); }
+
+ihsbin_status ihsbin_ctx_create(int device, uint64_t budget, ihsbin_ctx** out) {
+  if (!out) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return fail(IHSBIN_ERR_CUDA, "ctx_create: no CUDA device available");
+  if (device < 0 || device >= n) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_create: device index out of range");
+  if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "ctx_create");
+  if ((e = cudaFree(nullptr)) != cudaSuccess) return cuda_fail(e, "ctx_create");
+  ihsbin_ctx* c = new (std::nothrow) ihsbin_ctx();
+  if (!c) return fail(IHSBIN_ERR_OUT_OF_MEMORY, "ctx_create: host allocation failed");
+  c->device = device;
+  c->budget = budget;
+  *out = c;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_ctx_destroy(ihsbin_ctx* c) {
+  if (!c) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_destroy: NULL");
+  if (c->in_use) return fail(IHSBIN_ERR_STATE, "ctx_destroy: problems still hold device memory");
+  delete c;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_ctx_memory(const ihsbin_ctx* c, uint64_t* bytes) {
+  if (!c || !bytes) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_memory: NULL argument");
+  *bytes = c->in_use;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, const void* B, int64_t K, int64_t ldb,
+                                    ihsbin_dtype b_dtype, int b_on_device, ihsbin_problem** out) {
+  if (!ctx || !A || !B || !out) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: NULL argument");
+  *out = nullptr;
+  if (A->n <= 0 || A->d <= 0 || K <= 0 || ldb < K) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad sizes");
+  if (A->dtype < IHSBIN_F64 || A->dtype > IHSBIN_BF16) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad dtype");
+  if (b_dtype != IHSBIN_F64 && b_dtype != IHSBIN_F32) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: B must be F64 or F32");
+  if (A->layout == IHSBIN_DENSE_ROWMAJOR) {
+    if (!A->values || A->ld < A->d) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: dense values NULL or ld < d");
+  } else if (A->layout == IHSBIN_CSR) {
+    if (!A->values || !A->row_ptr || !A->col_idx || A->nnz < 0)
+      return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: CSR arrays NULL or nnz < 0");
+  } else {
+    return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad layout");
+  }
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "problem_create");
+  ihsbin_problem* p = new (std::nothrow) ihsbin_problem();
+  if (!p) return fail(IHSBIN_ERR_OUT_OF_MEMORY, "problem_create: host allocation failed");
+  p->ctx = ctx;
+  p->n = A->n;
+  p->d = A->d;
+  p->K = K;
+  p->dual = A->n < A->d;
+  auto bail = [&](cudaError_t err, const char* where) {
+    ihsbin_status s = cuda_fail(err, where);
+    ihsbin_problem_destroy(p);
+    return s;
+  };
+  const size_t es = elem_size(A->dtype);
+  Tall& T = p->A;
+  T.layout = A->layout;
+  T.elem = A->dtype == IHSBIN_F64 ? ELEM_F64 : A->dtype == IHSBIN_F32 ? ELEM_F32 : ELEM_BF16;
+  if ((e = prob_alloc(p, sizeof(int), (void**)&p->status, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
+  cudaMemset(p->status, 0, sizeof(int));
+  if (A->layout == IHSBIN_DENSE_ROWMAJOR) {
+    const void* src = A->values;
+    int64_t ld = A->ld;
+    if (!A->on_device) {  // copy, packing rows to ld = d
+      void* dptr = nullptr;
+      if ((e = prob_alloc(p, (size_t)A->n * A->d * es, &dptr, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
+      e = cudaMemcpy2D(dptr, A->d * es, A->values, A->ld * es, A->d * es, A->n, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return bail(e, "problem_create");
+      src = dptr;
+      ld = A->d;
+    }
+    if (!p->dual) {
+      T.N = A->n;
+      T.D = A->d;
+      T.A = src;
+      T.ld = ld;
+    } else {  // A_hat = A^T, materialised row-major (d x n)
+      void* tptr = nullptr;
+      if ((e = prob_alloc(p, (size_t)A->n * A->d * es, &tptr, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
+      if ((e = launch_transpose_dense(src, T.elem, A->n, A->d, ld, tptr, 0)) != cudaSuccess) return bail(e, "problem_create");
+      T.N = A->d;
+      T.D = A->n;
+      T.A = tptr;
+      T.ld = A->n;
+    }
+  } else {
+    return bail(cudaErrorNotSupported, "problem_create (CSR)");
+  }
+  // B -> device FP64, packed n x K
+  if ((e = prob_alloc(p, (size_t)A->n * K * 8, (void**)&p->B, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
+  const size_t bes = elem_size(b_dtype);
+  if (!b_on_device) {
+    std::vector<double> hb((size_t)A->n * K);
+    for (int64_t i = 0; i < A->n; ++i)
+      for (int64_t r = 0; r < K; ++r)
+        hb[i * K + r] = b_dtype == IHSBIN_F64 ? ((const double*)B)[i * ldb + r] : (double)((const float*)B)[i * ldb + r];
+    e = cudaMemcpy(p->B, hb.data(), hb.size() * 8, cudaMemcpyHostToDevice);
+  } else if (b_dtype == IHSBIN_F64 && ldb == K) {
+    e = cudaMemcpy(p->B, B, (size_t)A->n * K * 8, cudaMemcpyDeviceToDevice);
+  } else {
+    e = launch_convert_to_f64(B, b_dtype == IHSBIN_F64 ? ELEM_F64 : ELEM_F32, A->n, K, ldb, p->B, 0);
+    (void)bes;
+  }
+  if (e != cudaSuccess) return bail(e, "problem_create");
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "problem_create");
+  *out = p;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "problem_destroy: NULL");
+  cudaSetDevice(p->ctx->device);
+  cudaDeviceSynchronize();
+  prob_free_basis(p);
+  free_list(p, p->owned);
+  delete p;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream) {
+  if (!p || !sk) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = p->A.N, D = p->A.D;
+  if (sk->m <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: m must be positive");
+  int64_t Np = 1;
+  while (Np < N) Np <<= 1;
+  if (sk->kind == IHSBIN_SK_COUNTSKETCH) {
+    if (sk->s <= 0 || sk->m % sk->s) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: need s >= 1 and m % s == 0");
+  } else if (sk->kind == IHSBIN_SK_SRHT) {
+    if (sk->m > Np) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: SRHT needs m <= padded row count");
+    if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: SRHT needs dense A");
+  } else if (sk->kind == IHSBIN_SK_GAUSSIAN) {
+    if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: Gaussian needs dense A");
+  } else {
+    return fail(IHSBIN_ERR_INVALID_ARG, "sketch: unknown kind");
+  }
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "sketch");
+  // discard any previous sketch and basis
+  prob_free_basis(p);
+  p->sketched = false;
+  p->sk = *sk;
+  {
+    std::vector<DevBuf> keep;
+    for (auto& b : p->owned) {
+      if (b.p == p->SA || b.p == p->GS || b.p == p->sk_idx || b.p == p->sk_sign) {
+        std::lock_guard<std::mutex> g(p->ctx->mu);
+        cudaFree(b.p);
+        p->ctx->in_use -= b.bytes;
+      } else {
+        keep.push_back(b);
+      }
+    }
+    p->owned.swap(keep);
+    p->SA = p->GS = nullptr;
+    p->sk_idx = nullptr;
+    p->sk_sign = nullptr;
+  }
+  ScratchScope scratch(p);
+  if ((e = prob_alloc(p, (size_t)sk->m * D * 8, (void**)&p->SA, SCOPE_PERSIST)) != cudaSuccess) return cuda_fail(e, "sketch");
+  if ((e = prob_alloc(p, (size_t)D * D * 8, (void**)&p->GS, SCOPE_PERSIST)) != cudaSuccess) return cuda_fail(e, "sketch");
+  p->sk_idx_count = p->sk_sign_count = 0;
+  if (sk->kind == IHSBIN_SK_SRHT) {
+    p->sk_idx_count = sk->m;
+    p->sk_sign_count = Np;
+  } else if (sk->kind == IHSBIN_SK_COUNTSKETCH) {
+    p->sk_idx_count = p->sk_sign_count = N * sk->s;
+  }
+  if ((e = prob_alloc(p, std::max<int64_t>(1, p->sk_idx_count) * 8, (void**)&p->sk_idx, SCOPE_PERSIST)) != cudaSuccess)
+    return cuda_fail(e, "sketch");
+  if ((e = prob_alloc(p, std::max<int64_t>(1, p->sk_sign_count), (void**)&p->sk_sign, SCOPE_PERSIST)) != cudaSuccess)
+    return cuda_fail(e, "sketch");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  if (sk->kind == IHSBIN_SK_GAUSSIAN) e = sketch_gaussian(p, st);
+  else if (sk->kind == IHSBIN_SK_SRHT) e = sketch_srht(p, st);
+  else e = sketch_countsketch(p, st);
+  if (e == cudaSuccess) e = sketch_gram(p, st);
+  cudaEventRecord(e1, st);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_fail(e, "sketch");
+  }
+  ihsbin_status s = check_status(p, st, "sketch");
+  cudaEventElapsedTime(&p->phase_ms[0], e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != IHSBIN_OK) return s;
+  p->sketched = true;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_sketch_export(ihsbin_problem* p, int64_t* idx, int8_t* sign, int64_t cap, int64_t* count) {
+  if (!p || !count) return fail(IHSBIN_ERR_INVALID_ARG, "sketch_export: NULL argument");
+  if (!p->sketched) return fail(IHSBIN_ERR_STATE, "sketch_export: not sketched");
+  *count = p->sk_idx_count;
+  if (idx && p->sk_idx_count) {
+    if (cap < p->sk_idx_count) return fail(IHSBIN_ERR_INVALID_ARG, "sketch_export: cap too small");
+    if (cudaMemcpy(idx, p->sk_idx, p->sk_idx_count * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "sketch_export: copy failed");
+  }
+  if (sign && p->sk_sign_count) {
+    if (cap < p->sk_sign_count) return fail(IHSBIN_ERR_INVALID_ARG, "sketch_export: cap too small");
+    if (cudaMemcpy(sign, p->sk_sign, p->sk_sign_count, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "sketch_export: copy failed");
+  }
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* SA, double* GS) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "sketch_matrix_export: NULL");
+  if (!p->sketched) return fail(IHSBIN_ERR_STATE, "sketch_matrix_export: not sketched");
+  const int64_t D = p->A.D;
+  if (SA && cudaMemcpy(SA, p->SA, (size_t)p->sk.m * D * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(IHSBIN_ERR_CUDA, "sketch_matrix_export: copy failed");
+  if (GS && cudaMemcpy(GS, p->GS, (size_t)D * D * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return fail(IHSBIN_ERR_CUDA, "sketch_matrix_export: copy failed");
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, void* stream) {
+  if (!p || !d) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: NULL argument");
+  if (!p->sketched) return fail(IHSBIN_ERR_STATE, "build_basis: call ihsbin_sketch first");
+  if (!(d->lambda_min > 0) || !(d->lambda_max >= d->lambda_min) || !std::isfinite(d->lambda_max))
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: need 0 < lambda_min <= lambda_max < inf");
+  if (d->L < 0 || d->jmax < 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: negative L or jmax");
+  if (d->compute != IHSBIN_COMPUTE_F64 && d->compute != IHSBIN_COMPUTE_F32X2)
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown compute mode");
+  Plan pl;
+  const double beta = d->lambda_max / d->lambda_min;
+  pl.L = d->L > 0 ? d->L : std::max(1, (int)std::floor(2.0 * std::log(beta)));
+  const int L = pl.L;
+  pl.edges.resize(L + 1);
+  for (int l = 0; l <= L; ++l) pl.edges[l] = d->lambda_min * std::pow(beta, (double)l / L);
+  pl.edges[0] = d->lambda_min;
+  pl.edges[L] = d->lambda_max;
+  pl.lam0.resize(L);
+  pl.tau.resize(L);
+  pl.k.resize(L);
+  pl.jcount.resize(L);
+  double rho = d->rho;
+  if (!(rho > 0)) rho = std::min((double)p->A.D / (double)p->sk.m, 0.81);
+  for (int l = 0; l < L; ++l) {
+    const double lo = pl.edges[l], hi = pl.edges[l + 1];
+    pl.lam0[l] = std::sqrt(lo * hi);
+    double r1, r2;
+    if (d->rho1 && d->rho2) {
+      r1 = d->rho1[l];
+      r2 = d->rho2[l];
+    } else {
+      r1 = (1.0 + std::sqrt(rho)) * (1.0 + std::sqrt(rho));
+      r2 = (1.0 - std::sqrt(rho)) * (1.0 - std::sqrt(rho));
+    }
+    if (!(r1 > 0) || !(r2 > 0)) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: rho1 and rho2 must be positive");
+    pl.tau[l] = 2.0 * pl.lam0[l] / (lo / r1 + hi / r2);
+    const int kl = d->k ? d->k[l] : d->k_default;
+    if (kl <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: every k_l must be >= 1");
+    pl.k[l] = kl;
+    pl.jcount[l] = d->jmax > 0 ? std::min(kl, d->jmax) : kl;
+  }
+  pl.jmax = d->jmax;
+  pl.jc = *std::max_element(pl.jcount.begin(), pl.jcount.end());
+  pl.kmax = *std::max_element(pl.k.begin(), pl.k.end());
+  pl.compute = d->compute;
+  pl.product = d->product == IHSBIN_PRODUCT_AUTO
+                   ? (p->A.layout == IHSBIN_CSR ? IHSBIN_PRODUCT_ASPACE : IHSBIN_PRODUCT_GRAM)
+                   : d->product;
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "build_basis");
+  prob_free_basis(p);
+  p->plan = pl;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[5];
+  for (auto& x : ev) cudaEventCreate(&x);
+  ihsbin_status s;
+  {
+    ScratchScope scratch(p);
+    // persistent members (Pinv, G, Ut, W) are taken out of the scratch scope by the device code
+    e = build_basis_device(p, st, ev);
+    if (e != cudaSuccess) {
+      for (auto& x : ev) cudaEventDestroy(x);
+      cudaStreamSynchronize(st);
+      prob_free_basis(p);
+      return cuda_fail(e, "build_basis");
+    }
+    s = check_status(p, st, "build_basis");
+  }
+  float t01 = 0, t12 = 0, t23 = 0;
+  cudaEventElapsedTime(&t01, ev[0], ev[1]);
+  cudaEventElapsedTime(&t12, ev[1], ev[2]);
+  cudaEventElapsedTime(&t23, ev[2], ev[3]);
+  p->phase_ms[1] = t01;
+  p->phase_ms[2] = t12;
+  p->phase_ms[3] = t23;
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (s != IHSBIN_OK) {
+    prob_free_basis(p);
+    return s;
+  }
+  p->built = true;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_plan_export(ihsbin_problem* p, double* edges, double* lam0, double* tau, int32_t* k,
+                                 int32_t* jcount, int32_t cap_L, int32_t* L_out) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "plan_export: NULL");
+  if (!p->built) return fail(IHSBIN_ERR_STATE, "plan_export: no basis");
+  const Plan& pl = p->plan;
+  if (L_out) *L_out = pl.L;
+  if ((edges || lam0 || tau || k || jcount) && cap_L < pl.L) return fail(IHSBIN_ERR_INVALID_ARG, "plan_export: cap_L < L");
+  for (int l = 0; l < pl.L; ++l) {
+    if (lam0) lam0[l] = pl.lam0[l];
+    if (tau) tau[l] = pl.tau[l];
+    if (k) k[l] = pl.k[l];
+    if (jcount) jcount[l] = pl.jcount[l];
+  }
+  if (edges) {
+    if (cap_L < pl.L + 1) return fail(IHSBIN_ERR_INVALID_ARG, "plan_export: edges need L+1 entries");
+    for (int l = 0; l <= pl.L; ++l) edges[l] = pl.edges[l];
+  }
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_basis_export(ihsbin_problem* p, int32_t l, double* buf, int64_t cap, int64_t* need) {
+  if (!p || !need) return fail(IHSBIN_ERR_INVALID_ARG, "basis_export: NULL argument");
+  if (!p->built) return fail(IHSBIN_ERR_STATE, "basis_export: no basis");
+  const Plan& pl = p->plan;
+  if (l < 0 || l >= pl.L) return fail(IHSBIN_ERR_INVALID_ARG, "basis_export: interval out of range");
+  const int64_t D = p->A.D, K = p->K;
+  const int64_t cnt = (int64_t)pl.jcount[l] * K * D;
+  *need = cnt;
+  if (!buf) return IHSBIN_OK;
+  if (cap < cnt) return fail(IHSBIN_ERR_INVALID_ARG, "basis_export: cap too small");
+  const int64_t off = (int64_t)l * pl.jc * K * D;
+  if (pl.compute == IHSBIN_COMPUTE_F64) {
+    if (cudaMemcpy(buf, (double*)p->Ut.p0 + off, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "basis_export: copy failed");
+  } else {
+    std::vector<float> hi(cnt), lo(cnt);
+    if (cudaMemcpy(hi.data(), (float*)p->Ut.p0 + off, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lo.data(), (float*)p->Ut.p1 + off, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "basis_export: copy failed");
+    for (int64_t i = 0; i < cnt; ++i) buf[i] = (double)hi[i] + (double)lo[i];
+  }
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t T, void* X, ihsbin_dtype x_dtype,
+                               int x_on_device, void* stream) {
+  if (!p || !lambdas || !X) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: NULL argument");
+  if (!p->built) return fail(IHSBIN_ERR_STATE, "eval_path: call ihsbin_build_basis first");
+  if (T <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: T must be positive");
+  if (x_dtype != IHSBIN_F64 && x_dtype != IHSBIN_F32) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: X must be F64 or F32");
+  const Plan& pl = p->plan;
+  for (int64_t t = 0; t < T; ++t)
+    if (!(lambdas[t] >= pl.edges[0] && lambdas[t] <= pl.edges[pl.L]))
+      return fail(IHSBIN_ERR_LAMBDA_RANGE, "eval_path: lambda outside [lambda_min, lambda_max]");
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "eval_path");
+  cudaStream_t st = (cudaStream_t)stream;
+  ScratchScope scratch(p);
+  double* lam_dev = nullptr;
+  if ((e = prob_alloc(p, T * 8, (void**)&lam_dev, SCOPE_SCRATCH)) != cudaSuccess) return cuda_fail(e, "eval_path");
+  if ((e = cudaMemcpyAsync(lam_dev, lambdas, T * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "eval_path");
+  const int64_t outN = (int64_t)T * p->d * p->K;
+  const size_t oes = x_dtype == IHSBIN_F64 ? 8 : 4;
+  void* Xd = X;
+  if (!x_on_device) {
+    if ((e = prob_alloc(p, outN * oes, &Xd, SCOPE_SCRATCH)) != cudaSuccess) return cuda_fail(e, "eval_path");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  e = eval_device(p, lam_dev, T, Xd, x_dtype == IHSBIN_F64 ? ELEM_F64 : ELEM_F32, st);
+  cudaEventRecord(e1, st);
+  if (e == cudaSuccess && !x_on_device) e = cudaMemcpyAsync(X, Xd, outN * oes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return cuda_fail(e, "eval_path");
+  }
+  ihsbin_status s = check_status(p, st, "eval_path");
+  cudaEventElapsedTime(&p->phase_ms[4], e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return s;
+}
+
+ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5) {
+  if (!p || !ms5) return fail(IHSBIN_ERR_INVALID_ARG, "phase_times: NULL argument");
+  for (int i = 0; i < 5; ++i) ms5[i] = p->phase_ms[i];
+  return IHSBIN_OK;
+}
+
+}  // extern "C"

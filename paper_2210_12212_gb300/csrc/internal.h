@@ -1,0 +1,112 @@
+// Internal interfaces between the ABI layer (api.cu) and the kernel launchers (kernels.cu).
+#pragma once
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ihsbin.h"
+#include "common.cuh"
+
+struct ihsbin_ctx {
+  int device = 0;
+  uint64_t budget = 0;
+  uint64_t in_use = 0;
+  std::mutex mu;
+};
+
+namespace ihsbin {
+
+// Tall view A_hat (N x D, N >= D) of the data: A itself, or A^T for the dual.
+struct Tall {
+  int64_t N = 0, D = 0;
+  int layout = IHSBIN_DENSE_ROWMAJOR;
+  int elem = ELEM_F64;
+  // dense row-major (N x D) with row stride ld
+  const void* A = nullptr;
+  int64_t ld = 0;
+  // CSR of A_hat (N rows) and of A_hat^T (D rows)
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const void* val = nullptr;
+  const int64_t* rpT = nullptr;
+  const int32_t* ciT = nullptr;
+  const void* valT = nullptr;
+  int64_t nnz = 0;
+};
+
+struct Plan {
+  int L = 0;
+  std::vector<double> edges, lam0, tau;
+  std::vector<int32_t> k, jcount;
+  int32_t jmax = 0;   // 0 = full basis
+  int jc = 0;         // max jcount (buffer stride)
+  int kmax = 0;
+  int compute = IHSBIN_COMPUTE_F64;
+  int product = IHSBIN_PRODUCT_GRAM;
+};
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace ihsbin
+
+struct ihsbin_problem {
+  ihsbin_ctx* ctx = nullptr;
+  int64_t n = 0, d = 0, K = 0;
+  bool dual = false;
+  ihsbin::Tall A;
+  std::vector<ihsbin::DevBuf> owned;     // every device allocation of this problem
+  double* B = nullptr;                   // n x K (FP64, device)
+  int* status = nullptr;                 // device status word
+  // sketch
+  bool sketched = false;
+  ihsbin_sketch_desc sk{};
+  double* SA = nullptr;                  // m x D FP64
+  double* GS = nullptr;                  // D x D FP64
+  int64_t* sk_idx = nullptr;             // device
+  int8_t* sk_sign = nullptr;             // device
+  int64_t sk_idx_count = 0, sk_sign_count = 0;
+  // basis
+  bool built = false;
+  ihsbin::Plan plan;
+  ihsbin::CBuf G;                        // D x D (gram product mode)
+  ihsbin::CBuf Pinv;                     // L x D x D
+  ihsbin::CBuf Ut;                       // L x jc x K x D
+  ihsbin::CBuf W;                        // dual: L x jc x K x N (primal basis)
+  std::vector<ihsbin::DevBuf> basis_bufs;
+  float phase_ms[5] = {0, 0, 0, 0, 0};
+};
+
+namespace ihsbin {
+
+// ----- allocation helpers (api.cu) --------------------------------------------
+// Lifetime of a device allocation: the problem, the current basis, or the current call.
+enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2 };
+cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope);
+void prob_free_basis(ihsbin_problem* p);
+CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaError_t* err);
+
+// ----- kernel launchers (kernels.cu); all return the first CUDA error --------
+cudaError_t launch_transpose_dense(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
+                                   void* dst, cudaStream_t st);
+cudaError_t launch_csr_transpose(ihsbin_problem* p, const int64_t* rp, const int32_t* ci, const void* val,
+                                 int elem, int64_t rows, int64_t cols, int64_t nnz, int64_t** rpT,
+                                 int32_t** ciT, void** valT, cudaStream_t st);
+cudaError_t launch_convert_to_f64(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
+                                  double* dst, cudaStream_t st);
+
+cudaError_t sketch_gaussian(ihsbin_problem* p, cudaStream_t st);
+cudaError_t sketch_countsketch(ihsbin_problem* p, cudaStream_t st);
+cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st);
+cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st);
+
+cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev);
+cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,
+                        cudaStream_t st);
+
+}  // namespace ihsbin

@@ -1,0 +1,1147 @@
+// Kernels and launchers of the IHS-BIN hot path (sm_103a).
+//
+//  a1  sketch        Gaussian (Philox draws + contraction), SRHT (two-level
+//                    shared-memory Walsh-Hadamard + row selection), CountSketch/SJLT
+//  a2  factor        Gram of S A_hat, batched blocked Cholesky of G_S + lam0_l I for
+//                    all intervals at once, explicit inverse P_l = L^-T L^-1
+//  a3  rhs           c = A_hat^T B (dual: c = B), u_00 = P_l c
+//  a4  basis loop    Proposition 1 / Algorithm 2 recursion, all live intervals per launch
+//  a5  dual map      W_l = A_hat utilde_l
+//  a6  path eval     X(:, :, t) = tau_l sum_j theta_t^j utilde_j (FP64 coefficients)
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "gemm.cuh"
+#include "internal.h"
+
+namespace ihsbin {
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e_ = (x);                  \
+    if (e_ != cudaSuccess) return e_;      \
+  } while (0)
+
+static inline unsigned nblocks(int64_t n, int b) { return (unsigned)std::max<int64_t>(1, (n + b - 1) / b); }
+
+// =============================================================== utilities
+__global__ void k_convert_f64(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld, double* dst) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  int64_t r = i / cols, c = i % cols;
+  dst[i] = load_elem_d(src, elem, r * ld + c);
+}
+
+cudaError_t launch_convert_to_f64(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
+                                  double* dst, cudaStream_t st) {
+  if (rows * cols == 0) return cudaSuccess;
+  k_convert_f64<<<nblocks(rows * cols, 256), 256, 0, st>>>(src, elem, rows, cols, ld, dst);
+  return cudaGetLastError();
+}
+
+template <class E>
+__global__ void k_transpose(const E* src, int64_t rows, int64_t cols, int64_t ld, E* dst) {
+  __shared__ E t[32][33];
+  int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int64_t r = r0 + y, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[y][threadIdx.x] = src[r * ld + c];
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    int64_t c = c0 + y, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[c * rows + r] = t[threadIdx.x][y];
+  }
+}
+
+cudaError_t launch_transpose_dense(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
+                                   void* dst, cudaStream_t st) {
+  dim3 grid(nblocks(cols, 32), nblocks(rows, 32)), blk(32, 8);
+  if (elem == ELEM_F64)
+    k_transpose<double><<<grid, blk, 0, st>>>((const double*)src, rows, cols, ld, (double*)dst);
+  else if (elem == ELEM_F32)
+    k_transpose<float><<<grid, blk, 0, st>>>((const float*)src, rows, cols, ld, (float*)dst);
+  else
+    k_transpose<uint16_t><<<grid, blk, 0, st>>>((const uint16_t*)src, rows, cols, ld, (uint16_t*)dst);
+  return cudaGetLastError();
+}
+
+// ============================================================ loaders (gemm)
+// Raw data element as a contraction operand.  F64 mode widens to double; DD
+// mode keeps FP32/BF16 data as exact floats and splits FP64 data into dd.
+template <class Mode, int ET>
+struct ElemOp;
+template <int ET>
+struct ElemOp<F64, ET> {
+  using T = double;
+  __device__ __forceinline__ static T get(const void* p, int64_t i) { return load_elem_d(p, ET, i); }
+};
+template <>
+struct ElemOp<DD, ELEM_F32> {
+  using T = float;
+  __device__ __forceinline__ static T get(const void* p, int64_t i) { return ((const float*)p)[i]; }
+};
+template <>
+struct ElemOp<DD, ELEM_BF16> {
+  using T = float;
+  __device__ __forceinline__ static T get(const void* p, int64_t i) { return bf16_to_f(((const uint16_t*)p)[i]); }
+};
+template <>
+struct ElemOp<DD, ELEM_F64> {
+  using T = dd;
+  __device__ __forceinline__ static T get(const void* p, int64_t i) { return dd_from_double(((const double*)p)[i]); }
+};
+
+// X (rows x cols, row stride ld) read as X^T: operand (i, k) = X[k, i]   (A side, i = column of X)
+template <class Mode, int ET>
+struct LdTrans {
+  using T = typename ElemOp<Mode, ET>::T;
+  static constexpr bool k_contig = false;
+  const void* X;
+  int64_t ld;
+  __device__ __forceinline__ T operator()(int, int64_t i, int64_t k) const { return ElemOp<Mode, ET>::get(X, k * ld + i); }
+};
+// X read as-is on the B side: operand (k, j) = X[k, j]
+template <class Mode, int ET>
+struct LdRowB {
+  using T = typename ElemOp<Mode, ET>::T;
+  static constexpr bool k_contig = false;
+  const void* X;
+  int64_t ld;
+  __device__ __forceinline__ T operator()(int, int64_t k, int64_t j) const { return ElemOp<Mode, ET>::get(X, k * ld + j); }
+};
+// X read as-is on the A side: operand (i, k) = X[i, k]   (row-major, k contiguous)
+template <class Mode, int ET>
+struct LdRowA {
+  using T = typename ElemOp<Mode, ET>::T;
+  static constexpr bool k_contig = true;
+  const void* X;
+  int64_t ld;
+  int64_t gstride;  // per-group offset in elements
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    return ElemOp<Mode, ET>::get(X, g * gstride + i * ld + k);
+  }
+};
+// compute-precision square matrix (row-major), one per group (stride gs) or shared (gs = 0)
+template <class Mode>
+struct LdCMatA {
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf M;
+  int64_t D, gs;
+  const int* perm;  // group -> matrix index (nullptr = identity)
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    int64_t gi = perm ? perm[g] : g;
+    return Mode::ld(M, gi * gs + i * D + k);
+  }
+};
+// compute-precision column-major panel (column j contiguous over k), per group stride gs
+template <class Mode>
+struct LdCColB {
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf M;
+  int64_t D, gs;
+  const int* perm;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    int64_t gi = perm ? perm[g] : g;
+    return Mode::ld(M, gi * gs + j * D + k);
+  }
+};
+
+// ============================================================ epilogues
+template <class Mode>
+struct EpStoreSym {  // symmetric result: write (i, j) and (j, i) into a D x D matrix (group stride gs)
+  CBuf M;
+  int64_t D, gs;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+    if (i > j) return;
+    Mode::st(M, g * gs + i * D + j, a);
+    Mode::st(M, g * gs + j * D + i, a);
+  }
+};
+struct EpStoreSymF64 {  // symmetric result into an FP64 matrix
+  double* M;
+  int64_t D;
+  template <class V>
+  __device__ __forceinline__ void operator()(int, int64_t i, int64_t j, V a) const;
+};
+template <>
+__device__ __forceinline__ void EpStoreSymF64::operator()<double>(int, int64_t i, int64_t j, double a) const {
+  if (i > j) return;
+  M[i * D + j] = a;
+  M[j * D + i] = a;
+}
+template <>
+__device__ __forceinline__ void EpStoreSymF64::operator()<dd>(int, int64_t i, int64_t j, dd a) const {
+  if (i > j) return;
+  double v = dd_to_double(a);
+  M[i * D + j] = v;
+  M[j * D + i] = v;
+}
+struct EpStoreF64 {  // plain store into an FP64 row-major matrix with row stride ld (group stride gs)
+  double* M;
+  int64_t ld, gs;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, double a) const { M[g * gs + i * ld + j] = a; }
+};
+template <class Mode>
+struct EpStoreColMajor {  // result (i, j) -> M[g*gs + j*D + i]
+  CBuf M;
+  int64_t D, gs;
+  const int* perm;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+    int64_t gi = perm ? perm[g] : g;
+    Mode::st(M, gi * gs + j * D + i, a);
+  }
+};
+
+// =============================================================== a1: sketches
+// Gaussian entries S[i][j] = z_ij / sqrt(m), z by Box-Muller on (w0, w1) of
+// draw(seed, stream 5, i * N + j); written for a block of columns [j0, j0 + nc).
+__global__ void k_gauss_fill(double* S, int64_t m, int64_t N, int64_t j0, int64_t nc, uint64_t seed, double inv_sqrt_m) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * nc) return;
+  int64_t i = e / nc, jj = e % nc;
+  u32x4 w = rng_draw(seed, STREAM_GAUSSIAN, (uint64_t)i * (uint64_t)N + (uint64_t)(j0 + jj));
+  double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+  double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+  double z = sqrt(-2.0 * log(u0)) * cospi(2.0 * u1);
+  S[e] = z * inv_sqrt_m;
+}
+
+template <class Mode>
+struct LdGaussS {  // S block (m x nc, row-major FP64) as the A operand
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  const double* S;
+  int64_t nc;
+  __device__ __forceinline__ T operator()(int, int64_t i, int64_t k) const { return Mode::from_d(S[i * nc + k]); }
+};
+template <class Mode, int ET>
+struct LdRowsB {  // rows [r0, r0 + nc) of A_hat as the B operand (k = row, j = column)
+  using T = typename ElemOp<Mode, ET>::T;
+  static constexpr bool k_contig = false;
+  const void* X;
+  int64_t ld, r0;
+  __device__ __forceinline__ T operator()(int, int64_t k, int64_t j) const { return ElemOp<Mode, ET>::get(X, (r0 + k) * ld + j); }
+};
+struct EpAccumF64 {  // SA[i][j] += acc (FP64; each element owned by one thread per launch)
+  double* M;
+  int64_t ld;
+  template <class V>
+  __device__ __forceinline__ void operator()(int, int64_t i, int64_t j, V a) const;
+};
+template <>
+__device__ __forceinline__ void EpAccumF64::operator()<double>(int, int64_t i, int64_t j, double a) const { M[i * ld + j] += a; }
+template <>
+__device__ __forceinline__ void EpAccumF64::operator()<dd>(int, int64_t i, int64_t j, dd a) const {
+  M[i * ld + j] += dd_to_double(a);
+}
+
+template <class Mode, int ET>
+static cudaError_t gauss_apply(ihsbin_problem* p, double* Sbuf, int64_t chunk, cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t m = p->sk.m, N = A.N, D = A.D;
+  const double ism = 1.0 / std::sqrt((double)m);
+  for (int64_t j0 = 0; j0 < N; j0 += chunk) {
+    int64_t nc = std::min(chunk, N - j0);
+    k_gauss_fill<<<nblocks(m * nc, 256), 256, 0, st>>>(Sbuf, m, N, j0, nc, p->sk.seed, ism);
+    CK(cudaGetLastError());
+    GemmShape sh{m, D, nc, 0};
+    CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdGaussS<Mode>{Sbuf, nc},
+                                            LdRowsB<Mode, ET>{A.A, A.ld, j0}, EpAccumF64{p->SA, D}, st)));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t sketch_gaussian(ihsbin_problem* p, cudaStream_t st) {
+  const Tall& A = p->A;
+  if (A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  const int64_t m = p->sk.m, N = A.N;
+  int64_t chunk = std::max<int64_t>(16, std::min<int64_t>(N, (int64_t)((256ll << 20) / (8 * m))));
+  double* Sbuf = nullptr;
+  CK(ihsbin::prob_alloc(p, (size_t)m * chunk * sizeof(double), (void**)&Sbuf, SCOPE_SCRATCH));
+  CK(cudaMemsetAsync(p->SA, 0, (size_t)m * A.D * sizeof(double), st));
+  // the sketch is applied in FP64 arithmetic in both compute modes
+  if (A.elem == ELEM_F64) return gauss_apply<F64, ELEM_F64>(p, Sbuf, chunk, st);
+  if (A.elem == ELEM_F32) return gauss_apply<F64, ELEM_F32>(p, Sbuf, chunk, st);
+  return gauss_apply<F64, ELEM_BF16>(p, Sbuf, chunk, st);
+}
+
+// ---- CountSketch / SJLT: row of S and sign for every (input row i, block t)
+__global__ void k_cs_map(int64_t N, int s, int64_t mb, uint64_t seed, int64_t* idx, int8_t* sign) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * s) return;
+  int t = (int)(e % s);
+  u32x4 w = rng_draw(seed, STREAM_COUNTSKETCH, (uint64_t)e);
+  int64_t bucket = (int64_t)(((uint64_t)w.x * (uint64_t)mb) >> 32);
+  idx[e] = (int64_t)t * mb + bucket;
+  sign[e] = (w.y & 1u) ? (int8_t)-1 : (int8_t)1;
+}
+// dense rows: SA[idx[i*s+t], :] += sign * A[i, :] / sqrt(s)   (FP64 atomics); one CTA per row
+__global__ void k_cs_dense(const void* A, int elem, int64_t N, int64_t D, int64_t ld, int s, const int64_t* idx,
+                           const int8_t* sign, double scale, double* SA) {
+  for (int64_t i = blockIdx.x; i < N; i += gridDim.x) {
+    for (int64_t c = threadIdx.x; c < D; c += blockDim.x) {
+      double v = load_elem_d(A, elem, i * ld + c) * scale;
+      for (int t = 0; t < s; ++t) atomicAdd(&SA[idx[i * s + t] * D + c], sign[i * s + t] * v);
+    }
+  }
+}
+// CSR rows: one warp per row
+__global__ void k_cs_csr(const int64_t* rp, const int32_t* ci, const void* val, int elem, int64_t N, int64_t D,
+                         int s, const int64_t* idx, const int8_t* sign, double scale, double* SA) {
+  int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += 32) {
+    double v = load_elem_d(val, elem, e) * scale;
+    int64_t c = ci[e];
+    for (int t = 0; t < s; ++t) atomicAdd(&SA[idx[row * s + t] * D + c], sign[row * s + t] * v);
+  }
+}
+
+cudaError_t sketch_countsketch(ihsbin_problem* p, cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t m = p->sk.m, N = A.N, D = A.D;
+  const int s = p->sk.s;
+  k_cs_map<<<nblocks(N * s, 256), 256, 0, st>>>(N, s, m / s, p->sk.seed, p->sk_idx, p->sk_sign);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(p->SA, 0, (size_t)m * D * sizeof(double), st));
+  const double scale = 1.0 / std::sqrt((double)s);
+  if (A.layout == IHSBIN_DENSE_ROWMAJOR) {
+    k_cs_dense<<<(unsigned)std::min<int64_t>(N, 1 << 20), 256, 0, st>>>(A.A, A.elem, N, D, A.ld, s, p->sk_idx, p->sk_sign, scale, p->SA);
+  } else {
+    k_cs_csr<<<nblocks(N * 32, 256), 256, 0, st>>>(A.rp, A.ci, A.val, A.elem, N, D, s, p->sk_idx, p->sk_sign,
+                                                   scale, p->SA);
+  }
+  return cudaGetLastError();
+}
+
+// ---- SRHT
+__global__ void k_srht_draws(int64_t Np, uint64_t seed, uint64_t* key, int8_t* sign) {
+  int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= Np) return;
+  u32x4 a = rng_draw(seed, STREAM_SRHT_SIGN, (uint64_t)r);
+  sign[r] = (a.x & 1u) ? (int8_t)-1 : (int8_t)1;
+  u32x4 b = rng_draw(seed, STREAM_SRHT_KEY, (uint64_t)r);
+  key[r] = ((uint64_t)b.y << 32) | (uint64_t)b.x;
+}
+
+// Select the m smallest keys (ties to the lower index) by an 8-pass MSB radix
+// select in one CTA, then list the kept rows in ascending order and record
+// each row's rank (rowmap[r] = rank or -1).
+__global__ void __launch_bounds__(1024) k_srht_select(const uint64_t* key, int64_t Np, int64_t m, int64_t* sel,
+                                                      int* rowmap) {
+  __shared__ unsigned int hist[256];
+  __shared__ uint64_t s_prefix;
+  __shared__ int64_t s_need;
+  __shared__ int64_t warp_sums[32];
+  __shared__ int64_t s_base;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    s_prefix = 0;
+    s_need = m;
+  }
+  __syncthreads();
+  uint64_t mask = 0;
+  for (int pass = 7; pass >= 0; --pass) {
+    for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    const uint64_t prefix = s_prefix;
+    for (int64_t r = tid; r < Np; r += blockDim.x) {
+      uint64_t k = key[r];
+      if ((k & mask) == prefix) atomicAdd(&hist[(k >> (8 * pass)) & 0xFF], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int64_t need = s_need;
+      int b = 0;
+      for (; b < 256; ++b) {
+        if ((int64_t)hist[b] >= need) break;
+        need -= hist[b];
+      }
+      if (b > 255) b = 255;
+      s_need = need;
+      s_prefix = prefix | ((uint64_t)b << (8 * pass));
+    }
+    mask |= (uint64_t)0xFF << (8 * pass);
+    __syncthreads();
+  }
+  const uint64_t thr = s_prefix;  // the m-th smallest key; s_need copies of it are kept
+  const int64_t need_eq = s_need;
+  // scan in index order: keep key < thr, and the first need_eq rows with key == thr
+  if (tid == 0) s_base = 0;
+  __syncthreads();
+  int64_t eq_seen_before = 0;
+  for (int64_t base = 0; base < Np; base += blockDim.x) {
+    int64_t r = base + tid;
+    int flag_lt = 0, flag_eq = 0;
+    if (r < Np) {
+      uint64_t k = key[r];
+      flag_lt = k < thr;
+      flag_eq = k == thr;
+    }
+    // block-wide exclusive scan of flag_eq then of keep
+    int lane = tid & 31, wid = tid >> 5;
+    int v = flag_eq;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t w = (lane < (int)(blockDim.x / 32)) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int64_t eq_rank = eq_seen_before + (v - flag_eq) + (wid > 0 ? warp_sums[wid - 1] : 0);
+    int64_t eq_total = warp_sums[blockDim.x / 32 - 1];
+    __syncthreads();
+    int keep = flag_lt || (flag_eq && eq_rank < need_eq);
+    v = keep;
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+      int64_t w = (lane < (int)(blockDim.x / 32)) ? warp_sums[lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int64_t pos = s_base + (v - keep) + (wid > 0 ? warp_sums[wid - 1] : 0);
+    if (r < Np) {
+      if (keep && pos < m) {
+        sel[pos] = r;
+        rowmap[r] = (int)pos;
+      } else {
+        rowmap[r] = -1;
+      }
+    }
+    int64_t tot = warp_sums[blockDim.x / 32 - 1];
+    __syncthreads();
+    if (tid == 0) s_base += tot;
+    eq_seen_before += eq_total;
+    __syncthreads();
+  }
+}
+
+// One level of the Walsh-Hadamard transform along rows: butterflies over the
+// address bits [b0, b0 + q) of the row index, for a tile of w columns.  The
+// first level reads A_hat (applying the signs D and the zero padding); the
+// last level writes only the kept rows, scaled by 1/sqrt(m), into SA.
+__global__ void k_fwht_level(const void* A, int elem, int64_t N, int64_t D, int64_t ld, const int8_t* dsign,
+                             const double* Yin, double* Yout, int64_t Np, int b0, int q, int w, bool first,
+                             bool last, const int* rowmap, double scale, double* SA) {
+  extern __shared__ double sm[];
+  const int G = 1 << q;
+  const int64_t ngroups = Np >> q;
+  const int64_t grp = blockIdx.y;   // group id: the bits outside [b0, b0+q)
+  const int64_t c0 = (int64_t)blockIdx.x * w;
+  const int64_t lowmask = ((int64_t)1 << b0) - 1;
+  const int64_t base = (grp & lowmask) | ((grp >> b0) << (b0 + q));
+  (void)ngroups;
+  auto row_of = [&](int t) -> int64_t { return base | ((int64_t)t << b0); };
+  for (int e = threadIdx.x; e < G * w; e += blockDim.x) {
+    int t = e / w, cc = e % w;
+    int64_t r = row_of(t), c = c0 + cc;
+    double v = 0.0;
+    if (c < D) {
+      if (first) {
+        if (r < N) v = load_elem_d(A, elem, r * ld + c) * (double)dsign[r];
+      } else {
+        v = Yin[r * D + c];
+      }
+    }
+    sm[t * w + cc] = v;
+  }
+  __syncthreads();
+  for (int h = 1; h < G; h <<= 1) {
+    for (int e = threadIdx.x; e < (G / 2) * w; e += blockDim.x) {
+      int pr = e / w, cc = e % w;
+      int lo = (pr / h) * (2 * h) + (pr % h);
+      int hi = lo + h;
+      double a = sm[lo * w + cc], b = sm[hi * w + cc];
+      sm[lo * w + cc] = a + b;
+      sm[hi * w + cc] = a - b;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < G * w; e += blockDim.x) {
+    int t = e / w, cc = e % w;
+    int64_t r = row_of(t), c = c0 + cc;
+    if (c >= D) continue;
+    if (last) {
+      int k = rowmap[r];
+      if (k >= 0) SA[(int64_t)k * D + c] = sm[t * w + cc] * scale;
+    } else {
+      Yout[r * D + c] = sm[t * w + cc];
+    }
+  }
+}
+
+cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
+  const Tall& A = p->A;
+  if (A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  const int64_t N = A.N, D = A.D, m = p->sk.m;
+  int pbits = 0;
+  while (((int64_t)1 << pbits) < N) ++pbits;
+  const int64_t Np = (int64_t)1 << pbits;
+  uint64_t* keys = nullptr;
+  int* rowmap = nullptr;
+  CK(prob_alloc(p, Np * sizeof(uint64_t), (void**)&keys, SCOPE_SCRATCH));
+  CK(prob_alloc(p, Np * sizeof(int), (void**)&rowmap, SCOPE_SCRATCH));
+  k_srht_draws<<<nblocks(Np, 256), 256, 0, st>>>(Np, p->sk.seed, keys, p->sk_sign);
+  CK(cudaGetLastError());
+  k_srht_select<<<1, 1024, 0, st>>>(keys, Np, m, p->sk_idx, rowmap);
+  CK(cudaGetLastError());
+  const double scale = 1.0 / std::sqrt((double)m);
+  // split the pbits address bits into levels of at most 12 bits
+  std::vector<std::pair<int, int>> levels;
+  if (pbits == 0) levels.push_back({0, 0});
+  int nlev = (pbits + 11) / 12;
+  if (nlev == 0) nlev = 1;
+  int done = 0;
+  for (int l = 0; l < nlev && pbits > 0; ++l) {
+    int q = (pbits - done + (nlev - l) - 1) / (nlev - l);
+    levels.push_back({done, q});
+    done += q;
+  }
+  double* Y0 = nullptr;
+  double* Y1 = nullptr;
+  if (levels.size() > 1) {
+    CK(prob_alloc(p, Np * D * sizeof(double), (void**)&Y0, SCOPE_SCRATCH));
+    if (levels.size() > 2) CK(prob_alloc(p, Np * D * sizeof(double), (void**)&Y1, SCOPE_SCRATCH));
+  }
+  const double* yin = nullptr;
+  double* yout = Y0;
+  for (size_t l = 0; l < levels.size(); ++l) {
+    int b0 = levels[l].first, q = levels[l].second;
+    int G = 1 << q;
+    int w = std::max(1, std::min(32, 6144 / G));
+    size_t smem = (size_t)G * w * sizeof(double);
+    dim3 grid(nblocks(D, w), (unsigned)(Np >> q));
+    bool first = (l == 0), last = (l + 1 == levels.size());
+    if (smem > 48 * 1024)
+      CK(cudaFuncSetAttribute(k_fwht_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_fwht_level<<<grid, 256, smem, st>>>(A.A, A.elem, N, D, A.ld, p->sk_sign, yin, yout, Np, b0, q, w, first, last,
+                                           rowmap, scale, p->SA);
+    CK(cudaGetLastError());
+    yin = yout;
+    yout = (yout == Y0) ? Y1 : Y0;
+  }
+  return cudaSuccess;
+}
+
+// G_S = (S A_hat)^T (S A_hat) in FP64 (the sketched Hessian without the shift).
+cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) {
+  const int64_t m = p->sk.m, D = p->A.D;
+  GemmShape sh{D, D, m, 1};
+  return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
+                                             EpStoreSymF64{p->GS, D}, st);
+}
+
+// ======================================================= a2: factor and inverse
+// H_l = G_S + lam0_l I in compute precision, for every interval l.
+template <class Mode>
+__global__ void k_shift_copy(const double* GS, int64_t D, const double* lam0, CBuf H) {
+  int l = blockIdx.y;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D * D) return;
+  int64_t i = e / D, j = e % D;
+  double v = GS[e];
+  typename Mode::V x = Mode::from_d(v);
+  if (i == j) x = Mode::add(x, Mode::from_d(lam0[l]));
+  Mode::st(H, (int64_t)l * D * D + e, x);
+}
+
+constexpr int NB = 32;
+
+// Factor the diagonal block kb of every interval in place (unblocked, column by
+// column) and store the inverse of the resulting lower-triangular block.
+template <class Mode>
+__global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, CBuf dinv, int* status) {
+  using V = typename Mode::V;
+  const int l = blockIdx.x;
+  const int64_t off = (int64_t)l * D * D;
+  const int64_t r0 = (int64_t)kb * NB;
+  const int nb = (D - r0 < NB) ? (int)(D - r0) : NB;
+  __shared__ V a[NB][NB + 1];
+  __shared__ V inv[NB][NB + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  if (tid == 0) bad = 0;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int i = e / NB, j = e % NB;
+    a[i][j] = (i < nb && j < nb) ? Mode::ld(H, off + (r0 + i) * D + r0 + j) : Mode::zero();
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      V s = a[j][j];
+      double sd = Mode::to_d(s);
+      if (!(sd > 0.0)) {
+        bad = (sd != sd) ? DEV_NAN : DEV_NOT_SPD;
+        s = Mode::from_d(1.0);
+      }
+      a[j][j] = Mode::sqrt_(s);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] = Mode::div(a[i][j], a[j][j]);
+    __syncthreads();
+    // rank-1 update of the trailing lower triangle
+    for (int e = tid; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
+      int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
+      if (c <= i) a[i][c] = Mode::sub(a[i][c], Mode::mul(a[i][j], a[c][j]));
+    }
+    __syncthreads();
+  }
+  // inverse of the lower-triangular block by forward substitution, one column per thread
+  for (int c = tid; c < NB; c += blockDim.x) {
+    for (int i = 0; i < NB; ++i) {
+      if (i < c || i >= nb || c >= nb) {
+        inv[i][c] = Mode::zero();
+        continue;
+      }
+      V s = (i == c) ? Mode::from_d(1.0) : Mode::zero();
+      for (int k = c; k < i; ++k) s = Mode::sub(s, Mode::mul(a[i][k], inv[k][c]));
+      inv[i][c] = Mode::div(s, a[i][i]);
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int i = e / NB, j = e % NB;
+    if (i < nb && j < nb) Mode::st(H, off + (r0 + i) * D + r0 + j, j <= i ? a[i][j] : Mode::zero());
+    Mode::st(dinv, ((int64_t)l * ((D + NB - 1) / NB) + kb) * NB * NB + e, inv[i][j]);
+  }
+  if (tid == 0 && bad) dev_fail(status, bad);
+}
+
+// panel rows below the diagonal block: L[i, kb] = H[i, kb] * Linv_kk^T  (in place)
+template <class Mode>
+struct LdPanel {
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf H;
+  int64_t D, r0, c0;
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    return Mode::ld(H, (int64_t)g * D * D + (r0 + i) * D + c0 + k);
+  }
+};
+template <class Mode>
+struct LdDinvT {  // operand (k, j) = Linv_kk[j][k]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf dinv;
+  int64_t nblk;
+  int kb;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    return Mode::ld(dinv, ((int64_t)g * nblk + kb) * NB * NB + j * NB + k);
+  }
+};
+template <class Mode>
+struct EpPanel {
+  CBuf H;
+  int64_t D, r0, c0;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+    Mode::st(H, (int64_t)g * D * D + (r0 + i) * D + c0 + j, a);
+  }
+};
+template <class Mode>
+struct LdPanelT {  // operand (k, j) = L[r0 + j][c0 + k]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf H;
+  int64_t D, r0, c0;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    return Mode::ld(H, (int64_t)g * D * D + (r0 + j) * D + c0 + k);
+  }
+};
+template <class Mode>
+struct EpTrailing {  // H[r0+i][r0+j] -= acc on the lower triangle
+  CBuf H;
+  int64_t D, r0;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+    if (j > i) return;
+    int64_t o = (int64_t)g * D * D + (r0 + i) * D + r0 + j;
+    Mode::st(H, o, Mode::sub(Mode::ld(H, o), a));
+  }
+};
+
+// W = L^-1 (lower triangular) by block forward substitution; one CTA per
+// (column block cb, interval).  W[rb][cb] = Linv_rb (delta_{rb,cb} I - sum_{kb<rb} L[rb][kb] W[kb][cb]).
+template <class Mode>
+__global__ void __launch_bounds__(256) k_trtri(CBuf H, CBuf dinv, CBuf Wm, int64_t D) {
+  using V = typename Mode::V;
+  const int cb = blockIdx.x, l = blockIdx.y;
+  const int64_t nblk = (D + NB - 1) / NB;
+  const int64_t off = (int64_t)l * D * D;
+  __shared__ V Lt[NB][NB + 1];
+  __shared__ V Wt[NB][NB + 1];
+  __shared__ V T[NB][NB + 1];
+  const int tid = threadIdx.x;
+  // zero the strictly-upper blocks of this column block
+  for (int64_t rb = 0; rb < cb; ++rb)
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int64_t i = rb * NB + e / NB, j = (int64_t)cb * NB + e % NB;
+      if (i < D && j < D) Mode::st(Wm, off + i * D + j, Mode::zero());
+    }
+  for (int64_t rb = cb; rb < nblk; ++rb) {
+    // T = delta I - sum_kb L[rb][kb] W[kb][cb]
+    V acc[4];
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + q * 256;
+      int i = e / NB, j = e % NB;
+      acc[q] = (rb == cb && i == j) ? Mode::from_d(1.0) : Mode::zero();
+    }
+    for (int64_t kb = cb; kb < rb; ++kb) {
+      __syncthreads();
+      for (int e = tid; e < NB * NB; e += blockDim.x) {
+        int i = e / NB, j = e % NB;
+        int64_t gi = rb * NB + i, gk = kb * NB + j, gj = (int64_t)cb * NB + i;
+        Lt[i][j] = (gi < D && gk < D) ? Mode::ld(H, off + gi * D + gk) : Mode::zero();
+        int64_t wk = kb * NB + i, wj = (int64_t)cb * NB + j;
+        Wt[i][j] = (wk < D && wj < D) ? Mode::ld(Wm, off + wk * D + wj) : Mode::zero();
+        (void)gj;
+      }
+      __syncthreads();
+      for (int q = 0; q < 4; ++q) {
+        int e = tid + q * 256;
+        int i = e / NB, j = e % NB;
+        V s = Mode::zero();
+        for (int k = 0; k < NB; ++k) Mode::mac(s, Lt[i][k], Wt[k][j]);
+        acc[q] = Mode::sub(acc[q], Mode::renorm(s));
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + q * 256;
+      T[e / NB][e % NB] = acc[q];
+    }
+    for (int e = tid; e < NB * NB; e += blockDim.x) {
+      int i = e / NB, j = e % NB;
+      Lt[i][j] = Mode::ld(dinv, ((int64_t)l * nblk + rb) * NB * NB + i * NB + j);
+    }
+    __syncthreads();
+    for (int q = 0; q < 4; ++q) {
+      int e = tid + q * 256;
+      int i = e / NB, j = e % NB;
+      V s = Mode::zero();
+      for (int k = 0; k < NB; ++k) Mode::mac(s, Lt[i][k], T[k][j]);
+      int64_t gi = rb * NB + i, gj = (int64_t)cb * NB + j;
+      if (gi < D && gj < D) Mode::st(Wm, off + gi * D + gj, Mode::renorm(s));
+    }
+  }
+}
+
+template <class Mode>
+struct LdWT {  // operand (i, k) = W[k][i] (zero above the diagonal)
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  CBuf Wm;
+  int64_t D;
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    return Mode::ld(Wm, (int64_t)g * D * D + k * D + i);
+  }
+};
+template <class Mode>
+struct LdW {  // operand (k, j) = W[k][j]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  CBuf Wm;
+  int64_t D;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    return Mode::ld(Wm, (int64_t)g * D * D + k * D + j);
+  }
+};
+
+template <class Mode>
+static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf dinv, const double* lam0_dev,
+                                     cudaStream_t st) {
+  const int64_t D = p->A.D;
+  const int L = p->plan.L;
+  const int64_t nblk = (D + NB - 1) / NB;
+  k_shift_copy<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(p->GS, D, lam0_dev, H);
+  CK(cudaGetLastError());
+  for (int kb = 0; kb < nblk; ++kb) {
+    k_potrf_diag<Mode><<<L, 256, 0, st>>>(H, D, kb, dinv, p->status);
+    CK(cudaGetLastError());
+    const int64_t r0 = (int64_t)(kb + 1) * NB;
+    if (r0 >= D) break;
+    const int64_t rem = D - r0;
+    const int64_t c0 = (int64_t)kb * NB;
+    GemmShape sp{rem, NB, NB, 0};
+    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sp, L, LdPanel<Mode>{H, D, r0, c0}, LdDinvT<Mode>{dinv, nblk, kb},
+                                            EpPanel<Mode>{H, D, r0, c0}, st)));
+    GemmShape su{rem, rem, NB, 2};
+    CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(su, L, LdPanel<Mode>{H, D, r0, c0}, LdPanelT<Mode>{H, D, r0, c0},
+                                            EpTrailing<Mode>{H, D, r0}, st)));
+  }
+  k_trtri<Mode><<<dim3((unsigned)nblk, L), 256, 0, st>>>(H, dinv, Wm, D);
+  CK(cudaGetLastError());
+  // P_l = W^T W
+  GemmShape sh{D, D, D, 1};
+  return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, L, LdWT<Mode>{Wm, D}, LdW<Mode>{Wm, D},
+                                             EpStoreSym<Mode>{p->Pinv, D, D * D}, st);
+}
+
+// ============================================================ a3: Gram and rhs
+template <class Mode, int ET>
+static cudaError_t gram_dense(ihsbin_problem* p, cudaStream_t st) {
+  const Tall& A = p->A;
+  GemmShape sh{A.D, A.D, A.N, 1};
+  return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdRowB<Mode, ET>{A.A, A.ld},
+                                             EpStoreSym<Mode>{p->G, A.D, 0}, st);
+}
+
+template <class Mode>
+struct LdBcol {  // B (n x K, FP64 row-major) as the B operand: (k, j) = B[k][j]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  const double* B;
+  int64_t K;
+  __device__ __forceinline__ T operator()(int, int64_t k, int64_t j) const { return Mode::from_d(B[k * K + j]); }
+};
+
+template <class Mode>
+__global__ void k_copy_B_colmajor(const double* B, int64_t n, int64_t K, CBuf c) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * K) return;
+  int64_t i = e / K, r = e % K;
+  Mode::st(c, r * n + i, Mode::from_d(B[e]));
+}
+
+template <class Mode, int ET>
+static cudaError_t rhs_dense(ihsbin_problem* p, CBuf c, cudaStream_t st) {
+  const Tall& A = p->A;
+  GemmShape sh{A.D, p->K, A.N, 0};
+  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdBcol<Mode>{p->B, p->K},
+                                             EpStoreColMajor<Mode>{c, A.D, 0, nullptr}, st);
+}
+
+// ===================================================== a4: the basis recursion
+// Per-interval state: U (ping-pong), Ut (the accumulated basis), Y = A^T A U;
+// column (j, r) of interval l lives at offset (l * jc * K + j * K + r) * D.
+template <class Mode>
+struct EpInit {  // u_00 = P c: write U0 and Ut
+  CBuf U, Ut;
+  int64_t D, gs;
+  const int* perm;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+    int64_t o = (int64_t)perm[g] * gs + j * D + i;
+    a = Mode::renorm(a);
+    Mode::st(U, o, a);
+    Mode::st(Ut, o, a);
+  }
+};
+
+// B operand of the preconditioner product: column (j, r) of
+//   R = tau (Y_j + lam0 u_j) + lam0 u_{j-1}   (j < i; no shift term for j = 0)
+//   R = lam0 u_{i-1}                          (j = i, the new column)
+template <class Mode>
+struct LdR {
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf U, Y;
+  int64_t D, K, gs, ys;
+  int i;
+  const int* perm;
+  const double* tau;
+  const double* lam0;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t col) const {
+    const int l = perm[g];
+    const int64_t j = col / K;
+    const int64_t o = (int64_t)l * gs + col * D + k;
+    const T lm = Mode::from_d(lam0[l]);
+    if (j == i) return Mode::mul(lm, Mode::ld(U, o - K * D));
+    T u = Mode::ld(U, o);
+    T y = Mode::ld(Y, (int64_t)g * ys + col * D + k);
+    T r = Mode::mul(Mode::from_d(tau[l]), Mode::add(y, Mode::mul(lm, u)));
+    if (j > 0) r = Mode::add(r, Mode::mul(lm, Mode::ld(U, o - K * D)));
+    return r;
+  }
+};
+template <class Mode>
+struct EpUpdate {  // u_j <- u_j - P R_j (new column: u_i = -P R_i); utilde_j += u_j
+  CBuf Uin, Uout, Ut;
+  int64_t D, K, gs;
+  int i;
+  const int* perm;
+  __device__ __forceinline__ void operator()(int g, int64_t row, int64_t col, typename Mode::V a) const {
+    const int64_t o = (int64_t)perm[g] * gs + col * D + row;
+    const int64_t j = col / K;
+    typename Mode::V u = (j < i) ? Mode::ld(Uin, o) : Mode::zero();
+    u = Mode::sub(u, Mode::renorm(a));
+    Mode::st(Uout, o, u);
+    Mode::st(Ut, o, Mode::add(Mode::ld(Ut, o), u));
+  }
+};
+// Y = A^T A U for the Gram product: the B operand is U (column j, contiguous over k)
+template <class Mode>
+struct EpY {
+  CBuf Y;
+  int64_t D, ys;
+  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t col, typename Mode::V a) const {
+    Mode::st(Y, (int64_t)g * ys + col * D + i, Mode::renorm(a));
+  }
+};
+
+// A-space product, first half: W = A_hat U  (N x ncol per live interval)
+template <class Mode, int ET>
+struct LdAhatRow {  // operand (i, k) = A_hat[i][k]
+  using T = typename ElemOp<Mode, ET>::T;
+  static constexpr bool k_contig = true;
+  const void* A;
+  int64_t ld;
+  __device__ __forceinline__ T operator()(int, int64_t i, int64_t k) const { return ElemOp<Mode, ET>::get(A, i * ld + k); }
+};
+template <class Mode>
+struct LdWcol {  // operand (k, j) = Wtmp[g][j][k] (column-major, N rows)
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf Wt;
+  int64_t N, ws;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const { return Mode::ld(Wt, (int64_t)g * ws + j * N + k); }
+};
+
+template <class Mode, int ET>
+static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf Y, CBuf Wtmp, const int* perm_dev,
+                              const double* tau_dev, const double* lam0_dev, const std::vector<int>& order,
+                              cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t D = A.D, K = p->K;
+  const Plan& pl = p->plan;
+  const int64_t gs = (int64_t)pl.jc * K * D;  // per-interval stride of U / Ut
+  const int L = pl.L;
+  // u_00 = P_l c for every interval
+  {
+    GemmShape sh{D, K, D, 0};
+    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, L, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
+                                            LdCColB<Mode>{c, D, 0, nullptr}, EpInit<Mode>{U0, p->Ut, D, gs, perm_dev},
+                                            st)));
+  }
+  CBuf Uin = U0, Uout = U1;
+  const int J = pl.jmax > 0 ? pl.jmax : (1 << 30);
+  for (int i = 1; i < pl.kmax; ++i) {
+    int live = 0;
+    while (live < L && pl.k[order[live]] > i) ++live;
+    if (live == 0) break;
+    const int64_t nold = (int64_t)std::min(i, J) * K;
+    const int64_t nnew = (int64_t)std::min(i + 1, J) * K;
+    const int64_t ys = nold * D;
+    if (pl.product == IHSBIN_PRODUCT_GRAM) {
+      GemmShape sh{D, nold, D, 0};
+      CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, live, LdCMatA<Mode>{p->G, D, 0, nullptr},
+                                              LdCColB<Mode>{Uin, D, gs, perm_dev}, EpY<Mode>{Y, D, ys}, st)));
+    } else {
+      // W = A_hat U (N x nold), then Y = A_hat^T W
+      const int64_t N = A.N;
+      GemmShape s1{N, nold, D, 0};
+      CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(s1, live, LdAhatRow<Mode, ET>{A.A, A.ld},
+                                              LdCColB<Mode>{Uin, D, gs, perm_dev},
+                                              EpStoreColMajor<Mode>{Wtmp, N, nold * N, nullptr}, st)));
+      GemmShape s2{D, nold, N, 0};
+      CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(s2, live, LdTrans<Mode, ET>{A.A, A.ld},
+                                              LdWcol<Mode>{Wtmp, N, nold * N}, EpY<Mode>{Y, D, ys}, st)));
+    }
+    GemmShape sp{D, nnew, D, 0};
+    const int inew = (i < J) ? i : -1;
+    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(
+        sp, live, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
+        LdR<Mode>{Uin, Y, D, K, gs, ys, inew, perm_dev, tau_dev, lam0_dev},
+        EpUpdate<Mode>{Uin, Uout, p->Ut, D, K, gs, inew < 0 ? (1 << 30) : i, perm_dev}, st)));
+    std::swap(Uin, Uout);
+  }
+  return cudaSuccess;
+}
+
+// ===================================================== a6: path evaluation
+// coefficient table coef[t][j] = tau_l theta_t^j (FP64), interval per lambda
+__global__ void k_eval_coef(const double* lam, int64_t T, const double* edges, int L, const double* tau,
+                            const double* lam0, const int* jcount, int jc, int* tint, double* coef) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T) return;
+  double x = lam[t];
+  // half-open [edge_l, edge_{l+1}), last interval closed
+  int lo = 0, hi = L;  // find the largest l with edges[l] <= x
+  while (hi - lo > 1) {
+    int mid = (lo + hi) / 2;
+    if (edges[mid] <= x) lo = mid; else hi = mid;
+  }
+  int l = lo;
+  tint[t] = l;
+  double th = tau[l] * (x - lam0[l]) / lam0[l];
+  double cf = tau[l];
+  for (int j = 0; j < jc; ++j) {
+    coef[t * jc + j] = (j < jcount[l]) ? cf : 0.0;
+    cf *= th;
+  }
+}
+
+// X[t][i][r] = sum_j coef[t][j] * B_l[j][r][i]   (B = utilde, or its primal image for the dual)
+template <class Mode>
+__global__ void k_eval(CBuf Bm, int64_t rows, int64_t K, int jc, int64_t gs, const int* tint, const double* coef,
+                       const int* jcount, int64_t T, void* X, int x_elem) {
+  const int64_t t = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T || e >= rows * K) return;
+  const int64_t r = e / rows, i = e % rows;
+  const int l = tint[t];
+  const int jn = jcount[l];
+  typename Mode::V acc = Mode::zero();
+  for (int j = 0; j < jn; ++j) {
+    typename Mode::V b = Mode::ld(Bm, (int64_t)l * gs + ((int64_t)j * K + r) * rows + i);
+    typename Mode::V cf = Mode::from_d(coef[t * jc + j]);
+    acc = Mode::add(acc, Mode::mul(cf, b));
+  }
+  const int64_t o = t * rows * K + i * K + r;
+  double v = Mode::to_d(acc);
+  if (x_elem == ELEM_F64) ((double*)X)[o] = v;
+  else ((float*)X)[o] = (float)v;
+}
+
+// ============================================================ orchestration
+template <class Mode, int ET>
+static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev) {
+  const Tall& A = p->A;
+  const int64_t D = A.D, K = p->K;
+  Plan& pl = p->plan;
+  const int L = pl.L;
+  const int cm = pl.compute;
+  cudaError_t err = cudaSuccess;
+  auto cb = [&](size_t elems) { return alloc_cbuf(p, cm, elems, SCOPE_SCRATCH, &err); };
+
+  // plan arrays on the device
+  std::vector<int> order(L);
+  for (int l = 0; l < L; ++l) order[l] = l;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.k[a] > pl.k[b]; });
+  double* tau_dev = nullptr;
+  double* lam0_dev = nullptr;
+  int* perm_dev = nullptr;
+  CK(prob_alloc(p, L * sizeof(double), (void**)&tau_dev, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(double), (void**)&lam0_dev, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(int), (void**)&perm_dev, SCOPE_SCRATCH));
+  CK(cudaMemcpyAsync(tau_dev, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lam0_dev, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+
+  // a2: factor + inverse of the shifted sketched Hessians
+  CK(cudaEventRecord(ev[0], st));
+  CBuf H = cb((size_t)L * D * D);
+  CBuf Wm = cb((size_t)L * D * D);
+  const int64_t nblk = (D + NB - 1) / NB;
+  CBuf dinv = cb((size_t)L * nblk * NB * NB);
+  p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
+  CK(err);
+  CK(factor_and_invert<Mode>(p, H, Wm, dinv, lam0_dev, st));
+  CK(cudaEventRecord(ev[1], st));
+
+  // a3: Gram (product mode GRAM) and right-hand side
+  CBuf c = cb((size_t)D * K);
+  CK(err);
+  if (pl.product == IHSBIN_PRODUCT_GRAM) {
+    p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
+    CK(err);
+    CK((gram_dense<Mode, ET>(p, st)));
+  }
+  if (p->dual) {
+    k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(p->B, D, K, c);
+    CK(cudaGetLastError());
+  } else {
+    CK((rhs_dense<Mode, ET>(p, c, st)));
+  }
+  CK(cudaEventRecord(ev[2], st));
+
+  // a4: the recursion
+  const size_t per = (size_t)pl.jc * K * D;
+  CBuf U0 = cb(per * L), U1 = cb(per * L);
+  p->Ut = alloc_cbuf(p, cm, per * L, SCOPE_BASIS, &err);
+  CK(err);
+  const int64_t ncol_max = (int64_t)pl.jc * K;
+  CBuf Y = cb((size_t)ncol_max * D * L);
+  CBuf Wtmp{};
+  if (pl.product == IHSBIN_PRODUCT_ASPACE) Wtmp = cb((size_t)ncol_max * A.N * L);
+  CK(err);
+  CK(cudaMemsetAsync(U0.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
+  if (U0.p1) CK(cudaMemsetAsync(U0.p1, 0, per * L * 4, st));
+  CK(cudaMemsetAsync(p->Ut.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
+  if (p->Ut.p1) CK(cudaMemsetAsync(p->Ut.p1, 0, per * L * 4, st));
+  CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Wtmp, perm_dev, tau_dev, lam0_dev, order, st)));
+
+  // a5: primal image of the dual basis, W_l = A_hat utilde_l (N x jc K)
+  if (p->dual) {
+    const int64_t N = A.N;
+    p->W = alloc_cbuf(p, cm, (size_t)L * pl.jc * K * N, SCOPE_BASIS, &err);
+    CK(err);
+    GemmShape sh{N, (int64_t)pl.jc * K, D, 0};
+    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, L, LdAhatRow<Mode, ET>{A.A, A.ld}, LdCColB<Mode>{p->Ut, D, (int64_t)per, nullptr},
+                                            EpStoreColMajor<Mode>{p->W, N, (int64_t)pl.jc * K * N, nullptr}, st)));
+  }
+  CK(cudaEventRecord(ev[3], st));
+  return cudaSuccess;
+}
+
+cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev) {
+  const int cm = p->plan.compute, et = p->A.elem;
+  if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  if (cm == IHSBIN_COMPUTE_F64) {
+    if (et == ELEM_F64) return build_typed<F64, ELEM_F64>(p, st, ev);
+    if (et == ELEM_F32) return build_typed<F64, ELEM_F32>(p, st, ev);
+    return build_typed<F64, ELEM_BF16>(p, st, ev);
+  }
+  if (et == ELEM_F64) return build_typed<DD, ELEM_F64>(p, st, ev);
+  if (et == ELEM_F32) return build_typed<DD, ELEM_F32>(p, st, ev);
+  return build_typed<DD, ELEM_BF16>(p, st, ev);
+}
+
+template <class Mode>
+static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_dev, int64_t T, void* X, int x_elem,
+                              cudaStream_t st) {
+  const Plan& pl = p->plan;
+  const int L = pl.L, jc = pl.jc;
+  double *edges = nullptr, *tau = nullptr, *lam0 = nullptr, *coef = nullptr;
+  int *jcount = nullptr, *tint = nullptr;
+  CK(prob_alloc(p, (L + 1) * sizeof(double), (void**)&edges, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(double), (void**)&tau, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(double), (void**)&lam0, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(int), (void**)&jcount, SCOPE_SCRATCH));
+  CK(prob_alloc(p, T * sizeof(int), (void**)&tint, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)T * jc * sizeof(double), (void**)&coef, SCOPE_SCRATCH));
+  CK(cudaMemcpyAsync(edges, pl.edges.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(tau, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lam0, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(jcount, pl.jcount.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef);
+  CK(cudaGetLastError());
+  const int64_t K = p->K;
+  const int64_t rows = p->dual ? p->A.N : p->A.D;
+  const CBuf Bm = p->dual ? p->W : p->Ut;
+  const int64_t gs = (int64_t)jc * K * rows;
+  dim3 grid(nblocks(rows * K, 256), (unsigned)T);
+  k_eval<Mode><<<grid, 256, 0, st>>>(Bm, rows, K, jc, gs, tint, coef, jcount, T, X, x_elem);
+  return cudaGetLastError();
+}
+
+cudaError_t eval_device(ihsbin_problem* p, const double* lam_dev, int64_t T, void* X, int x_elem, cudaStream_t st) {
+  if (p->plan.compute == IHSBIN_COMPUTE_F64) return eval_typed<F64>(p, lam_dev, T, X, x_elem, st);
+  return eval_typed<DD>(p, lam_dev, T, X, x_elem, st);
+}
+
+cudaError_t launch_csr_transpose(ihsbin_problem*, const int64_t*, const int32_t*, const void*, int, int64_t, int64_t,
+                                 int64_t, int64_t**, int32_t**, void**, cudaStream_t) {
+  return cudaErrorNotSupported;
+}
+
+}  // namespace ihsbin

@@ -1,0 +1,269 @@
+"""ctypes binding of libihsbin (include/ihsbin.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts Python
+arguments (numpy arrays, torch tensors, integers) into the C ABI's plain
+pointers and sizes and turns non-zero statuses into exceptions.  Loading
+fails loudly when the in-tree library has not been built: there is no other
+code path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libihsbin.so")
+
+# ---- enums (mirror include/ihsbin.h)
+OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_SPD, ERR_LAMBDA_RANGE, ERR_STATE, \
+    ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(10)
+ERR_NAN = 11
+F64, F32, BF16 = 0, 1, 2
+COMPUTE_F64, COMPUTE_F32X2 = 0, 1
+DENSE, CSR = 0, 1
+SK_GAUSSIAN, SK_SRHT, SK_COUNTSKETCH = 0, 1, 2
+PRODUCT_AUTO, PRODUCT_GRAM, PRODUCT_ASPACE = 0, 1, 2
+
+SKETCH_KIND = {"gaussian": SK_GAUSSIAN, "srht": SK_SRHT, "countsketch": SK_COUNTSKETCH}
+DTYPE = {"f64": F64, "f32": F32, "bf16": BF16}
+COMPUTE = {"f64": COMPUTE_F64, "f32x2": COMPUTE_F32X2}
+PRODUCT = {"auto": PRODUCT_AUTO, "gram": PRODUCT_GRAM, "aspace": PRODUCT_ASPACE}
+
+
+class IhsbinError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"ihsbin status {status}: {msg}")
+        self.status = status
+
+
+class Matrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("d", C.c_int64), ("layout", C.c_int), ("dtype", C.c_int),
+                ("values", C.c_void_p), ("ld", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("nnz", C.c_int64), ("on_device", C.c_int)]
+
+
+class SketchDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("m", C.c_int64), ("s", C.c_int32), ("seed", C.c_uint64)]
+
+
+class PathDesc(C.Structure):
+    _fields_ = [("lambda_min", C.c_double), ("lambda_max", C.c_double), ("L", C.c_int32),
+                ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
+                ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
+                ("compute", C.c_int), ("product", C.c_int)]
+
+
+_lib = None
+
+EXPORTED = [
+    "ihsbin_ctx_create", "ihsbin_ctx_destroy", "ihsbin_ctx_memory", "ihsbin_last_error",
+    "ihsbin_problem_create", "ihsbin_problem_destroy", "ihsbin_sketch", "ihsbin_sketch_export",
+    "ihsbin_sketch_matrix_export", "ihsbin_build_basis", "ihsbin_plan_export", "ihsbin_basis_export",
+    "ihsbin_eval_path", "ihsbin_phase_times",
+]
+
+
+def load(path: Optional[str] = None):
+    """Load the in-tree library (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libihsbin not built ({path} missing): run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    sig = {
+        "ihsbin_ctx_create": [C.c_int, C.c_uint64, C.POINTER(vp)],
+        "ihsbin_ctx_destroy": [vp],
+        "ihsbin_ctx_memory": [vp, C.POINTER(C.c_uint64)],
+        "ihsbin_problem_create": [vp, C.POINTER(Matrix), vp, i64, i64, C.c_int, C.c_int, C.POINTER(vp)],
+        "ihsbin_problem_destroy": [vp],
+        "ihsbin_sketch": [vp, C.POINTER(SketchDesc), vp],
+        "ihsbin_sketch_export": [vp, vp, vp, i64, C.POINTER(i64)],
+        "ihsbin_sketch_matrix_export": [vp, vp, vp],
+        "ihsbin_build_basis": [vp, C.POINTER(PathDesc), vp],
+        "ihsbin_plan_export": [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)],
+        "ihsbin_basis_export": [vp, i32, vp, i64, C.POINTER(i64)],
+        "ihsbin_eval_path": [vp, vp, i64, vp, C.c_int, C.c_int, vp],
+        "ihsbin_phase_times": [vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.ihsbin_last_error.argtypes = []
+    lib.ihsbin_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise IhsbinError(status, _lib.ihsbin_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (0 for None)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _on_device(a) -> int:
+    return int(bool(getattr(a, "is_cuda", False)))
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Context:
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        load()
+        h = C.c_void_p()
+        _check(_lib.ihsbin_ctx_create(device, hbm_budget_bytes, C.byref(h)))
+        self.h = h
+
+    def memory(self) -> int:
+        v = C.c_uint64()
+        _check(_lib.ihsbin_ctx_memory(self.h, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.h:
+            _check(_lib.ihsbin_ctx_destroy(self.h))
+            self.h = None
+
+
+class Problem:
+    """A problem handle: ihsbin_problem_create / _sketch / _build_basis / _eval_path."""
+
+    def __init__(self, ctx: Context, A=None, B=None, *, dtype: str = "f64", csr=None, shape=None):
+        """A: dense (n x d) numpy array or CUDA tensor, or csr=(row_ptr, col_idx, values) with shape=(n, d).
+        B: (n,) or (n x K) numpy array (float64/float32) or CUDA tensor."""
+        self.ctx = ctx
+        m = Matrix()
+        self._keep = []
+        if csr is not None:
+            rp, ci, val = csr
+            n, d = shape
+            m.n, m.d, m.layout, m.dtype = n, d, CSR, DTYPE[dtype]
+            m.values, m.row_ptr, m.col_idx, m.nnz = _ptr(val), _ptr(rp), _ptr(ci), int(len(ci))
+            m.ld = 0
+            m.on_device = _on_device(val)
+            self._keep += [rp, ci, val]
+        else:
+            n, d = A.shape
+            m.n, m.d, m.layout, m.dtype = n, d, DENSE, DTYPE[dtype]
+            m.values = _ptr(A)
+            m.ld = A.stride(0) if hasattr(A, "stride") and callable(A.stride) else A.strides[0] // A.itemsize
+            m.on_device = _on_device(A)
+            self._keep.append(A)
+        if B.ndim == 1:
+            B = B.reshape(-1, 1)
+        K = B.shape[1]
+        if hasattr(B, "is_cuda"):
+            bdt = F64 if str(B.dtype) == "torch.float64" else F32
+            ldb = B.stride(0)
+        else:
+            B = np.ascontiguousarray(B)
+            bdt = F64 if B.dtype == np.float64 else F32
+            ldb = B.shape[1]
+        self._keep.append(B)
+        h = C.c_void_p()
+        _check(_lib.ihsbin_problem_create(ctx.h, C.byref(m), _ptr(B), K, ldb, bdt, _on_device(B),
+                                          C.byref(h)))
+        self.h = h
+        self.n, self.d, self.K = n, d, K
+
+    # -- hot path -------------------------------------------------------------------------
+    def sketch(self, kind: str, m: int, s: int = 1, seed: int = 0, stream=None):
+        sd = SketchDesc(SKETCH_KIND[kind], m, s, seed)
+        _check(_lib.ihsbin_sketch(self.h, C.byref(sd), _stream(stream)))
+
+    def build_basis(self, lambda_min: float, lambda_max: float, *, L: int = 0,
+                    k: Optional[Sequence[int]] = None, k_default: int = 20,
+                    rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
+                    rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
+                    stream=None):
+        pd = PathDesc()
+        pd.lambda_min, pd.lambda_max, pd.L = lambda_min, lambda_max, L
+        ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
+        r1 = np.ascontiguousarray(rho1, dtype=np.float64) if rho1 is not None else None
+        r2 = np.ascontiguousarray(rho2, dtype=np.float64) if rho2 is not None else None
+        pd.k = _ptr(ka)
+        pd.k_default = k_default
+        pd.rho1, pd.rho2 = _ptr(r1), _ptr(r2)
+        pd.rho, pd.jmax = rho, jmax
+        pd.compute, pd.product = COMPUTE[compute], PRODUCT[product]
+        _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
+
+    def eval_path(self, lambdas, out=None, x_dtype: str = "f64", stream=None):
+        """Returns X (T x d x K) as a numpy array, or fills `out` (a CUDA tensor) in place."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        T = lam.shape[0]
+        if out is None:
+            out = np.empty((T, self.d, self.K), dtype=np.float64 if x_dtype == "f64" else np.float32)
+            on_dev = 0
+        else:
+            on_dev = _on_device(out)
+        _check(_lib.ihsbin_eval_path(self.h, _ptr(lam), T, _ptr(out), DTYPE[x_dtype], on_dev,
+                                     _stream(stream)))
+        return out
+
+    # -- exports ---------------------------------------------------------------------------
+    def sketch_export(self, cap: int):
+        idx = np.empty(cap, dtype=np.int64)
+        sign = np.empty(cap, dtype=np.int8)
+        cnt = C.c_int64()
+        _check(_lib.ihsbin_sketch_export(self.h, _ptr(idx), _ptr(sign), cap, C.byref(cnt)))
+        return idx, sign, cnt.value
+
+    def sketch_matrices(self, m: int, D: int):
+        SA = np.empty((m, D))
+        GS = np.empty((D, D))
+        _check(_lib.ihsbin_sketch_matrix_export(self.h, _ptr(SA), _ptr(GS)))
+        return SA, GS
+
+    def plan(self):
+        Lv = C.c_int32()
+        _check(_lib.ihsbin_plan_export(self.h, None, None, None, None, None, 0, C.byref(Lv)))
+        L = Lv.value
+        edges = np.empty(L + 1)
+        lam0, tau = np.empty(L), np.empty(L)
+        k, jc = np.empty(L, np.int32), np.empty(L, np.int32)
+        _check(_lib.ihsbin_plan_export(self.h, _ptr(edges), _ptr(lam0), _ptr(tau), _ptr(k), _ptr(jc),
+                                       L + 1, C.byref(Lv)))
+        return dict(L=L, edges=edges, lam0=lam0, tau=tau, k=k, jcount=jc)
+
+    def basis(self, l: int, D: int):
+        need = C.c_int64()
+        _check(_lib.ihsbin_basis_export(self.h, l, None, 0, C.byref(need)))
+        buf = np.empty(need.value)
+        _check(_lib.ihsbin_basis_export(self.h, l, _ptr(buf), need.value, C.byref(need)))
+        return buf.reshape(-1, self.K, D).transpose(0, 2, 1)   # (j, D, K)
+
+    def phase_times(self):
+        out = np.zeros(5, dtype=np.float32)
+        _check(_lib.ihsbin_phase_times(self.h, _ptr(out)))
+        return dict(zip(["sketch", "factor", "gram_rhs", "basis", "eval"], out.tolist()))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(_lib.ihsbin_problem_destroy(self.h))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
