@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Ridge-path benchmark: IHS-BIN on GB300 through the C ABI.
+
+Workload (default `c2`): dense FP32 A 65536 x 1024 with singular values 1/k and
+Haar factors, b from a planted x* plus 1% noise, SRHT sketch m = 2048, T = 200
+lambdas log-spaced in [1e-6, 1] * ||A||_2^2, L = 27 intervals, per-interval
+(rho1, rho2, k) from tests/golden/c2_params.json.
+
+One step = one whole path: sketch (a1), factor + inverse (a2), Gram + rhs
+(a3), basis recursion (a4), evaluation of all T lambdas (a6), with A and B
+resident in HBM.  `e2e` repeats the step through the same C ABI from pinned
+host buffers (problem creation with its host->device copy, and the device->
+host read of X, inside the timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload
+(weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ridge paths/sec at rel-err≤1e-6 vs FP64 oracle; p50/p99 latency; %HBM peak"
+WORKLOADS = {
+    "c2": "dense FP32 A 65536x1024, sigma_k=1/k with Haar factors, b=Ax*+1% noise, SRHT m=2048, "
+          "T=200 lambdas log-spaced in [1e-6,1]*||A||_2^2, L=27",
+    "c1": "dense FP64 A 2000x100, columns (1+j)^-0.8, Gaussian sketch m=200, T=50 lambdas in "
+          "[1e-4,1e2]*||A||_2^2, L=27",
+}
+# FP32 lanes per SM and SM count of GB300; max SM clock 2070 MHz
+FP32_INSTR_PEAK = 152 * 128 * 2.07e9
+FP64_FMA_PEAK = 152 * 2 * 2.07e9
+# FP32 instructions per float-float multiply-add as implemented (common.cuh):
+# two_prod 2, cross terms 2 (dd x dd) / 1 (float x dd), TwoSum 6, low-word add 2
+INSTR_PER_MAC = {"gram": 10, "sketch_gram": None, "loop_gram_product": 12, "loop_precond_update": 12,
+                 "inverse_syrk": 12, "factor_syrk": 12, "factor_trsm": 12, "rhs": 11, "dual_map": 11}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ihsbin", choices=["ihsbin", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--compute", default="f32x2", choices=["f32x2", "f64"])
+    ap.add_argument("--jmax", type=int, default=32)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    return ap.parse_args()
+
+
+def load_params(config):
+    with open(os.path.join(ROOT, "tests", "golden", f"{config}_params.json")) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region (read-only query)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3] not in ("", "[N/A]"))}
+
+
+# ------------------------------------------------------------------------ CPU oracle
+def oracle_sample(prob, par, reps=1):
+    """The FP64 oracle, as it stands, on a bounded sample of the path: the sketch, the Gram
+    matrix and right-hand side, the factor of one interval, that interval's basis and the
+    evaluation of its lambdas.  Per-path time = fixed part + per-column time x all basis columns."""
+    from oracle import ihsbin as ob
+    from oracle import sketch as osk
+    A = prob.dense_f64()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
+    t0 = time.perf_counter()
+    SA = osk.apply(prob.sketch, A, prob.m, prob.s, prob.sketch_seed)
+    GS = SA.T @ SA
+    G = A.T @ A
+    c = A.T @ prob.B
+    t_fixed = time.perf_counter() - t0
+    ks = np.array(par["k"])
+    l = int(np.argsort(ks)[len(ks) // 2])          # the median-k interval
+    samples = []
+    for _ in range(reps):
+        t1 = time.perf_counter()
+        P = ob.precond(GS, plan.lam0[l])
+        ut = ob.basis(lambda V: G @ V, P, c, plan.tau[l], int(ks[l]))
+        for lam in prob.lambdas[(prob.lambdas >= plan.edges[l]) & (prob.lambdas <= plan.edges[l + 1])]:
+            ob.evaluate(ut, plan.tau[l], plan.lam0[l], lam)
+        samples.append(time.perf_counter() - t1)
+    t_int = min(samples)
+    cols = ks * (ks + 1) / 2
+    per_path = t_fixed + t_int * cols.sum() / cols[l]
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return dict(value=1.0 / per_path, unit="paths/s", cores=cores, kind="oracle",
+                sample=f"FP64 numpy oracle: sketch+Gram+rhs ({t_fixed:.2f}s) and interval {l} "
+                       f"(k={int(ks[l])}, {t_int:.2f}s) of the {prob.name} path; per-path time "
+                       f"extrapolated by basis columns sum_l k_l(k_l+1)/2", t_fixed=t_fixed, t_interval=t_int)
+
+
+def reference_arm(args, prob, par):
+    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(prob, par)
+    times, vals = [], []
+    t0 = time.perf_counter()
+    info = None
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        info = oracle_sample(prob, par)
+        times.append(time.perf_counter() - t1)
+        vals.append(info["value"])
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS.get(args.config, args.config), "l2": "inputs larger than L2"},
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "paths/s", "cores": info["cores"], "kind": "oracle",
+                             "sample": info["sample"]},
+            "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    from synthetic import make_problem
+    prob = make_problem(args.config, seed=0)
+    par = load_params(args.config)
+    if args.impl == "reference":
+        reference_arm(args, prob, par)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2210_12212_gb300 import ihsbin as ihs
+
+    ctx = ihs.Context(local)
+    es = {"f64": np.float64, "f32": np.float32}
+    A_dev = torch.from_numpy(np.ascontiguousarray(prob.A)).cuda()
+    B_dev = torch.from_numpy(np.ascontiguousarray(prob.B)).cuda()
+    T = len(prob.lambdas)
+    X_dev = torch.empty((T, prob.d, prob.K), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
+               compute=args.compute)
+    p = ihs.Problem(ctx, A_dev, B_dev, dtype=prob.storage)
+
+    def step(pp, out=None):
+        pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, stream=stream)
+        pp.build_basis(prob.lambda_min, prob.lambda_max, stream=stream, **bkw)
+        return pp.eval_path(prob.lambdas, out=out, stream=stream)
+
+    for _ in range(max(args.warmup, 0)):
+        step(p, X_dev)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-kernel events on the launching stream
+    p.set_timing(True)
+    p.reset_stats()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e_start = torch.cuda.Event(enable_timing=True)
+        e_stop = torch.cuda.Event(enable_timing=True)
+        e_start.record(stream)
+        for s in range(args.steps):
+            evs[s][0].record(stream)
+            step(p, X_dev)
+            evs[s][1].record(stream)
+        e_stop.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = e_start.elapsed_time(e_stop)
+    if dist:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    lat = sorted(a.elapsed_time(b) for a, b in evs)
+    stats = p.kernel_stats()
+    p.set_timing(False)
+    phases = p.phase_times()
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_pin = torch.from_numpy(np.ascontiguousarray(prob.A)).pin_memory()
+        B_host = np.ascontiguousarray(prob.B)
+        ke = max(1, min(args.steps, 5))
+        q = ihs.Problem(ctx, A_pin, B_host, dtype=prob.storage)   # warm the host path once
+        step(q)
+        q.close()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            q = ihs.Problem(ctx, A_pin, B_host, dtype=prob.storage)
+            Xh = step(q)
+            q.close()
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([te], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": world * ke / te, "unit": "paths/s",
+               "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size() + B_host.nbytes
+                                         + prob.lambdas.nbytes),
+               "d2h_bytes_per_step": int(Xh.nbytes)}
+
+    # ---- parity of the timed result against the FP64 oracle (sampled lambdas, rank 0)
+    check = None
+    if rank == 0 and not args.no_check:
+        check = parity_sample(prob, par, X_dev.cpu().numpy())
+
+    # ---- roofline of the dominant kernel (largest device time in the timed region)
+    dom = max(stats.items(), key=lambda kv: kv[1][1])
+    name, (launches, ms, flops, byts) = dom
+    instr = INSTR_PER_MAC.get(name) or 12
+    if args.compute == "f64":
+        peak = 2 * FP64_FMA_PEAK / 1e12
+        peak_note = "FP64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2070 MHz)"
+    else:
+        peak = 2 * FP32_INSTR_PEAK / instr / 1e12
+        peak_note = (f"float-float multiply-add rate from unit counts: 152 SMs x 128 FP32 lanes x 2070 MHz "
+                     f"/ {instr} FP32 instructions per multiply-add")
+    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    traffic = read_traffic(name, launches / args.steps if args.steps else 0)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic, "kernel": name, "launches_per_step": launches / args.steps,
+            "avg_launch_ms": ms / launches, "peak_basis": peak_note}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu and world == 1:
+        info = oracle_sample(prob, par)
+        cpu = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    gpu_launches = int(sum(v[0] for v in stats.values()))
+    value = world * args.steps / (elapsed_ms * 1e-3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
+            "config": {"workload": WORKLOADS.get(args.config, args.config), "jmax": args.jmax,
+                       "storage": prob.storage, "l2": "inputs larger than L2 (A is 256 MiB)",
+                       "params": f"tests/golden/{args.config}_params.json",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+            "phase_ms": phases,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clk.summary(), "parity": check,
+            "kernels": {k: {"launches": v[0], "ms": v[1], "tflops": (v[2] / (v[1] * 1e-3) / 1e12 if v[1] else 0)}
+                        for k, v in stats.items()},
+        }
+        print(json.dumps(line), flush=True)
+    p.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def parity_sample(prob, par, X):
+    """Max relative error of the GPU path against the oracle's k_l-step IHS (Gram space) at 9 lambdas
+    (the endpoints and 7 interior grid points), plus the distance of the oracle to x*(lambda)."""
+    from oracle import ihsbin as ob
+    from oracle import sketch as osk
+    A = prob.dense_f64()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
+    idx = np.unique(np.linspace(0, len(prob.lambdas) - 1, 9).round().astype(int))
+    lams = prob.lambdas[idx]
+    SA = osk.apply(prob.sketch, A, prob.m, prob.s, prob.sketch_seed)
+    ref = ob.direct_path(A, prob.B, SA.T @ SA, plan, lams)
+    err = [float(np.linalg.norm(X[i] - ref[t]) / np.linalg.norm(ref[t])) for t, i in enumerate(idx)]
+    G = A.T @ A
+    c = A.T @ prob.B
+    conv = [float(np.linalg.norm(ref[t] - np.linalg.solve(G + lam * np.eye(G.shape[0]), c))
+                  / np.linalg.norm(ref[t])) for t, lam in enumerate(lams)]
+    return {"max_rel_err_vs_oracle": max(err), "lambdas_checked": len(idx), "pass": max(err) <= 1e-6,
+            "oracle_max_rel_dist_to_exact_ridge": max(conv)}
+
+
+def read_traffic(kernel, launches_per_step):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it matches the current
+    kernel source (the summary records a hash of csrc/); otherwise null."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2210_12212_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    digest = h.hexdigest()[:16]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and f[0] == kernel and f[1] == digest:
+            return float(f[2])
+    return None
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,18 @@ IHSBIN_API ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambd
  * calls: [0] sketch, [1] factor+inverse, [2] Gram+rhs, [3] basis loop, [4] eval. */
 IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
 
+/* Per-kernel accounting, for measurement.  Every launch is counted with its
+ * algorithmic flops (2 per multiply-add of the contraction it performs, FP64
+ * or float-float) and algorithmic HBM bytes; when timing is enabled each launch
+ * is also bracketed by CUDA events on the stream it runs on and its device
+ * time is added at the call's synchronisation point.  Categories 0 ..
+ * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
+#define IHSBIN_KCAT_COUNT 17
+IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
+IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
+IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,
+                                             double* flops, double* bytes, const char** name);
+
 #ifdef __cplusplus
 }
 #endif

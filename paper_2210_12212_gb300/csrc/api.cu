@@ -52,6 +52,7 @@ struct ScratchScope {  // frees the call's scratch allocations when the call ret
 ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where) {
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, where);
+  resolve_timing(p);
   int s = 0;
   e = cudaMemcpy(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, where);
@@ -105,6 +106,35 @@ CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaErr
   }
   if (e != cudaSuccess) *err = e;
   return b;
+}
+
+KTimer::KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes) : p(pp), cat(c), st(s) {
+  KStat& k = p->kstat[c];
+  k.launches += 1;
+  k.flops += flops;
+  k.bytes += bytes;
+  if (!p->timing) return;
+  while (p->ev_pool.size() < p->ev_used + 2) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    p->ev_pool.push_back(e);
+  }
+  idx = p->ev_used;
+  p->ev_used += 2;
+  cudaEventRecord(p->ev_pool[idx], st);
+  p->ev_pending.push_back({c, idx});
+}
+KTimer::~KTimer() {
+  if (p->timing) cudaEventRecord(p->ev_pool[idx + 1], st);
+}
+void resolve_timing(ihsbin_problem* p) {
+  for (auto& pr : p->ev_pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->ev_pool[pr.second], p->ev_pool[pr.second + 1]) == cudaSuccess)
+      p->kstat[pr.first].ms += ms;
+  }
+  p->ev_pending.clear();
+  p->ev_used = 0;
 }
 
 void prob_free_basis(ihsbin_problem* p) {
@@ -240,6 +270,8 @@ ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "problem_destroy: NULL");
   cudaSetDevice(p->ctx->device);
   cudaDeviceSynchronize();
+  for (auto e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pool.clear();
   prob_free_basis(p);
   free_list(p, p->owned);
   delete p;
@@ -518,6 +550,36 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return s;
+}
+
+static const char* kcat_names[K_NCAT] = {
+    "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
+    "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
+    "eval_coef", "eval", "sparse"};
+
+ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");
+  p->timing = enable != 0;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_reset_stats(ihsbin_problem* p) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "reset_stats: NULL");
+  for (auto& k : p->kstat) k = KStat{};
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms, double* flops,
+                                  double* bytes, const char** name) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_stats: NULL");
+  if (cat < 0 || cat >= K_NCAT) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_stats: category out of range");
+  const KStat& k = p->kstat[cat];
+  if (launches) *launches = k.launches;
+  if (ms) *ms = k.ms;
+  if (flops) *flops = k.flops;
+  if (bytes) *bytes = k.bytes;
+  if (name) *name = kcat_names[cat];
+  return IHSBIN_OK;
 }
 
 ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5) {

@@ -53,6 +53,17 @@ struct DevBuf {
   size_t bytes = 0;
 };
 
+// Kernel categories for the opt-in per-launch timing (ihsbin_kernel_stats).
+enum KCat : int {
+  K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
+  K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
+  K_SPARSE, K_NCAT
+};
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0, flops = 0, bytes = 0;
+};
+
 }  // namespace ihsbin
 
 struct ihsbin_problem {
@@ -80,6 +91,12 @@ struct ihsbin_problem {
   ihsbin::CBuf W;                        // dual: L x jc x K x N (primal basis)
   std::vector<ihsbin::DevBuf> basis_bufs;
   float phase_ms[5] = {0, 0, 0, 0, 0};
+  // per-launch accounting: counts and algorithmic work always; event timing when enabled
+  bool timing = false;
+  ihsbin::KStat kstat[ihsbin::K_NCAT];
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (category, index of start event)
 };
 
 namespace ihsbin {
@@ -90,6 +107,19 @@ enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2 };
 cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope);
 void prob_free_basis(ihsbin_problem* p);
 CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaError_t* err);
+
+// Records one launch of category `cat` with its algorithmic flops / bytes, and
+// brackets it with events on `st` when timing is enabled (resolved by
+// resolve_timing after the call's synchronisation point).
+struct KTimer {
+  ihsbin_problem* p;
+  int cat;
+  cudaStream_t st;
+  size_t idx = 0;
+  KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes);
+  ~KTimer();
+};
+void resolve_timing(ihsbin_problem* p);
 
 // ----- kernel launchers (kernels.cu); all return the first CUDA error --------
 cudaError_t launch_transpose_dense(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,

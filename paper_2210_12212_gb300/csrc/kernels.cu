@@ -246,9 +246,13 @@ static cudaError_t gauss_apply(ihsbin_problem* p, double* Sbuf, int64_t chunk, c
   const double ism = 1.0 / std::sqrt((double)m);
   for (int64_t j0 = 0; j0 < N; j0 += chunk) {
     int64_t nc = std::min(chunk, N - j0);
-    k_gauss_fill<<<nblocks(m * nc, 256), 256, 0, st>>>(Sbuf, m, N, j0, nc, p->sk.seed, ism);
+    {
+      KTimer kt(p, K_SKETCH_DRAW, st, 0, (double)m * nc * 8);
+      k_gauss_fill<<<nblocks(m * nc, 256), 256, 0, st>>>(Sbuf, m, N, j0, nc, p->sk.seed, ism);
+    }
     CK(cudaGetLastError());
     GemmShape sh{m, D, nc, 0};
+    KTimer kt(p, K_SKETCH_APPLY, st, 2.0 * m * D * nc, (double)nc * D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
     CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdGaussS<Mode>{Sbuf, nc},
                                             LdRowsB<Mode, ET>{A.A, A.ld, j0}, EpAccumF64{p->SA, D}, st)));
   }
@@ -306,10 +310,16 @@ cudaError_t sketch_countsketch(ihsbin_problem* p, cudaStream_t st) {
   const Tall& A = p->A;
   const int64_t m = p->sk.m, N = A.N, D = A.D;
   const int s = p->sk.s;
-  k_cs_map<<<nblocks(N * s, 256), 256, 0, st>>>(N, s, m / s, p->sk.seed, p->sk_idx, p->sk_sign);
+  {
+    KTimer kt(p, K_SKETCH_DRAW, st, 0, (double)N * s * 9);
+    k_cs_map<<<nblocks(N * s, 256), 256, 0, st>>>(N, s, m / s, p->sk.seed, p->sk_idx, p->sk_sign);
+  }
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(p->SA, 0, (size_t)m * D * sizeof(double), st));
   const double scale = 1.0 / std::sqrt((double)s);
+  const double es = A.elem == ELEM_F64 ? 8 : A.elem == ELEM_F32 ? 4 : 2;
+  KTimer kt(p, K_SKETCH_APPLY, st, 2.0 * s * (A.layout == IHSBIN_CSR ? (double)A.nnz : (double)N * D),
+            A.layout == IHSBIN_CSR ? A.nnz * (es + 4) + 8.0 * (N + 1) : (double)N * D * es);
   if (A.layout == IHSBIN_DENSE_ROWMAJOR) {
     k_cs_dense<<<(unsigned)std::min<int64_t>(N, 1 << 20), 256, 0, st>>>(A.A, A.elem, N, D, A.ld, s, p->sk_idx, p->sk_sign, scale, p->SA);
   } else {
@@ -503,9 +513,15 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
   int* rowmap = nullptr;
   CK(prob_alloc(p, Np * sizeof(uint64_t), (void**)&keys, SCOPE_SCRATCH));
   CK(prob_alloc(p, Np * sizeof(int), (void**)&rowmap, SCOPE_SCRATCH));
-  k_srht_draws<<<nblocks(Np, 256), 256, 0, st>>>(Np, p->sk.seed, keys, p->sk_sign);
+  {
+    KTimer kt(p, K_SKETCH_DRAW, st, 0, (double)Np * 9);
+    k_srht_draws<<<nblocks(Np, 256), 256, 0, st>>>(Np, p->sk.seed, keys, p->sk_sign);
+  }
   CK(cudaGetLastError());
-  k_srht_select<<<1, 1024, 0, st>>>(keys, Np, m, p->sk_idx, rowmap);
+  {
+    KTimer kt(p, K_SKETCH_DRAW, st, 0, (double)Np * 12 + m * 8);
+    k_srht_select<<<1, 1024, 0, st>>>(keys, Np, m, p->sk_idx, rowmap);
+  }
   CK(cudaGetLastError());
   const double scale = 1.0 / std::sqrt((double)m);
   // split the pbits address bits into levels of at most 12 bits
@@ -536,6 +552,10 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
     bool first = (l == 0), last = (l + 1 == levels.size());
     if (smem > 48 * 1024)
       CK(cudaFuncSetAttribute(k_fwht_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const double es = A.elem == ELEM_F64 ? 8 : A.elem == ELEM_F32 ? 4 : 2;
+    const double rd = first ? (double)N * D * es : (double)Np * D * 8;
+    const double wr = last ? (double)m * D * 8 : (double)Np * D * 8;
+    KTimer kt(p, K_SKETCH_APPLY, st, (double)Np * D * q, rd + wr);
     k_fwht_level<<<grid, 256, smem, st>>>(A.A, A.elem, N, D, A.ld, p->sk_sign, yin, yout, Np, b0, q, w, first, last,
                                            rowmap, scale, p->SA);
     CK(cudaGetLastError());
@@ -549,6 +569,7 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
 cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) {
   const int64_t m = p->sk.m, D = p->A.D;
   GemmShape sh{D, D, m, 1};
+  KTimer kt(p, K_SKETCH_GRAM, st, (double)m * D * (D + 1), (double)m * D * 8 + (double)D * D * 8);
   return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
                                              EpStoreSymF64{p->GS, D}, st);
 }
@@ -773,26 +794,43 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
   const int64_t D = p->A.D;
   const int L = p->plan.L;
   const int64_t nblk = (D + NB - 1) / NB;
-  k_shift_copy<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(p->GS, D, lam0_dev, H);
+  const double cs = Mode::id == 0 ? 8 : 8;  // bytes per compute-precision element (double or two floats)
+  {
+    KTimer kt(p, K_FACTOR_SHIFT, st, 0, (double)D * D * (8 + cs * L));
+    k_shift_copy<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(p->GS, D, lam0_dev, H);
+  }
   CK(cudaGetLastError());
   for (int kb = 0; kb < nblk; ++kb) {
-    k_potrf_diag<Mode><<<L, 256, 0, st>>>(H, D, kb, dinv, p->status);
+    {
+      KTimer kt(p, K_FACTOR_POTRF, st, (double)L * NB * NB * NB * 2.0 / 3.0, (double)L * NB * NB * cs * 3);
+      k_potrf_diag<Mode><<<L, 256, 0, st>>>(H, D, kb, dinv, p->status);
+    }
     CK(cudaGetLastError());
     const int64_t r0 = (int64_t)(kb + 1) * NB;
     if (r0 >= D) break;
     const int64_t rem = D - r0;
     const int64_t c0 = (int64_t)kb * NB;
     GemmShape sp{rem, NB, NB, 0};
-    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sp, L, LdPanel<Mode>{H, D, r0, c0}, LdDinvT<Mode>{dinv, nblk, kb},
-                                            EpPanel<Mode>{H, D, r0, c0}, st)));
+    {
+      KTimer kt(p, K_FACTOR_TRSM, st, 2.0 * L * rem * NB * NB, (double)L * rem * NB * cs * 2);
+      CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sp, L, LdPanel<Mode>{H, D, r0, c0}, LdDinvT<Mode>{dinv, nblk, kb},
+                                              EpPanel<Mode>{H, D, r0, c0}, st)));
+    }
     GemmShape su{rem, rem, NB, 2};
-    CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(su, L, LdPanel<Mode>{H, D, r0, c0}, LdPanelT<Mode>{H, D, r0, c0},
-                                            EpTrailing<Mode>{H, D, r0}, st)));
+    {
+      KTimer kt(p, K_FACTOR_SYRK, st, (double)L * rem * (rem + 1) * NB, (double)L * rem * rem * cs);
+      CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(su, L, LdPanel<Mode>{H, D, r0, c0}, LdPanelT<Mode>{H, D, r0, c0},
+                                              EpTrailing<Mode>{H, D, r0}, st)));
+    }
   }
-  k_trtri<Mode><<<dim3((unsigned)nblk, L), 256, 0, st>>>(H, dinv, Wm, D);
+  {
+    KTimer kt(p, K_TRTRI, st, (double)L * D * D * D / 3.0, (double)L * D * D * cs);
+    k_trtri<Mode><<<dim3((unsigned)nblk, L), 256, 0, st>>>(H, dinv, Wm, D);
+  }
   CK(cudaGetLastError());
   // P_l = W^T W
   GemmShape sh{D, D, D, 1};
+  KTimer kt(p, K_INVERSE, st, (double)L * D * D * (D + 1) / 3.0, (double)L * D * D * cs * 2);
   return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, L, LdWT<Mode>{Wm, D}, LdW<Mode>{Wm, D},
                                              EpStoreSym<Mode>{p->Pinv, D, D * D}, st);
 }
@@ -802,6 +840,7 @@ template <class Mode, int ET>
 static cudaError_t gram_dense(ihsbin_problem* p, cudaStream_t st) {
   const Tall& A = p->A;
   GemmShape sh{A.D, A.D, A.N, 1};
+  KTimer kt(p, K_GRAM, st, (double)A.N * A.D * (A.D + 1), (double)A.N * A.D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
   return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdRowB<Mode, ET>{A.A, A.ld},
                                              EpStoreSym<Mode>{p->G, A.D, 0}, st);
 }
@@ -827,6 +866,7 @@ template <class Mode, int ET>
 static cudaError_t rhs_dense(ihsbin_problem* p, CBuf c, cudaStream_t st) {
   const Tall& A = p->A;
   GemmShape sh{A.D, p->K, A.N, 0};
+  KTimer kt(p, K_RHS, st, 2.0 * A.N * A.D * p->K, (double)A.N * A.D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
   return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdBcol<Mode>{p->B, p->K},
                                              EpStoreColMajor<Mode>{c, A.D, 0, nullptr}, st);
 }
@@ -928,6 +968,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
   // u_00 = P_l c for every interval
   {
     GemmShape sh{D, K, D, 0};
+    KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * K * L, (double)L * D * D * 8);
     CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, L, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
                                             LdCColB<Mode>{c, D, 0, nullptr}, EpInit<Mode>{U0, p->Ut, D, gs, perm_dev},
                                             st)));
@@ -943,11 +984,14 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t ys = nold * D;
     if (pl.product == IHSBIN_PRODUCT_GRAM) {
       GemmShape sh{D, nold, D, 0};
+      KTimer kt(p, K_LOOP_Y, st, 2.0 * D * D * nold * live, (double)D * D * 8 + 16.0 * D * nold * live);
       CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, live, LdCMatA<Mode>{p->G, D, 0, nullptr},
                                               LdCColB<Mode>{Uin, D, gs, perm_dev}, EpY<Mode>{Y, D, ys}, st)));
     } else {
       // W = A_hat U (N x nold), then Y = A_hat^T W
       const int64_t N = A.N;
+      const double esz = ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2;
+      KTimer kt(p, K_LOOP_Y, st, 4.0 * N * D * nold * live, 2.0 * N * D * esz * live);
       GemmShape s1{N, nold, D, 0};
       CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(s1, live, LdAhatRow<Mode, ET>{A.A, A.ld},
                                               LdCColB<Mode>{Uin, D, gs, perm_dev},
@@ -958,6 +1002,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     }
     GemmShape sp{D, nnew, D, 0};
     const int inew = (i < J) ? i : -1;
+    KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 32.0 * D * nnew * live);
     CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(
         sp, live, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
         LdR<Mode>{Uin, Y, D, K, gs, ys, inew, perm_dev, tau_dev, lam0_dev},
@@ -1057,6 +1102,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     CK((gram_dense<Mode, ET>(p, st)));
   }
   if (p->dual) {
+    KTimer kt(p, K_RHS, st, 0, (double)D * K * 16);
     k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(p->B, D, K, c);
     CK(cudaGetLastError());
   } else {
@@ -1086,6 +1132,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     p->W = alloc_cbuf(p, cm, (size_t)L * pl.jc * K * N, SCOPE_BASIS, &err);
     CK(err);
     GemmShape sh{N, (int64_t)pl.jc * K, D, 0};
+    KTimer kt(p, K_DUAL_MAP, st, 2.0 * N * D * pl.jc * K * L, (double)N * D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2) * L);
     CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, L, LdAhatRow<Mode, ET>{A.A, A.ld}, LdCColB<Mode>{p->Ut, D, (int64_t)per, nullptr},
                                             EpStoreColMajor<Mode>{p->W, N, (int64_t)pl.jc * K * N, nullptr}, st)));
   }
@@ -1123,13 +1170,17 @@ static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_dev, int64_t 
   CK(cudaMemcpyAsync(tau, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lam0, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(jcount, pl.jcount.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
-  k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef);
+  {
+    KTimer kt(p, K_EVAL_COEF, st, 0, (double)T * jc * 8);
+    k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef);
+  }
   CK(cudaGetLastError());
   const int64_t K = p->K;
   const int64_t rows = p->dual ? p->A.N : p->A.D;
   const CBuf Bm = p->dual ? p->W : p->Ut;
   const int64_t gs = (int64_t)jc * K * rows;
   dim3 grid(nblocks(rows * K, 256), (unsigned)T);
+  KTimer kt(p, K_EVAL, st, 2.0 * T * rows * K * jc, (double)T * rows * K * (x_elem == ELEM_F64 ? 8 : 4));
   k_eval<Mode><<<grid, 256, 0, st>>>(Bm, rows, K, jc, gs, tint, coef, jcount, T, X, x_elem);
   return cudaGetLastError();
 }

@@ -62,8 +62,10 @@ EXPORTED = [
     "ihsbin_ctx_create", "ihsbin_ctx_destroy", "ihsbin_ctx_memory", "ihsbin_last_error",
     "ihsbin_problem_create", "ihsbin_problem_destroy", "ihsbin_sketch", "ihsbin_sketch_export",
     "ihsbin_sketch_matrix_export", "ihsbin_build_basis", "ihsbin_plan_export", "ihsbin_basis_export",
-    "ihsbin_eval_path", "ihsbin_phase_times",
+    "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
+    "ihsbin_kernel_stats",
 ]
+KCAT_COUNT = 17
 
 
 def load(path: Optional[str] = None):
@@ -91,6 +93,9 @@ def load(path: Optional[str] = None):
         "ihsbin_basis_export": [vp, i32, vp, i64, C.POINTER(i64)],
         "ihsbin_eval_path": [vp, vp, i64, vp, C.c_int, C.c_int, vp],
         "ihsbin_phase_times": [vp, vp],
+        "ihsbin_set_timing": [vp, C.c_int],
+        "ihsbin_reset_stats": [vp],
+        "ihsbin_kernel_stats": [vp, i32, vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -256,6 +261,24 @@ class Problem:
         out = np.zeros(5, dtype=np.float32)
         _check(_lib.ihsbin_phase_times(self.h, _ptr(out)))
         return dict(zip(["sketch", "factor", "gram_rhs", "basis", "eval"], out.tolist()))
+
+    def set_timing(self, enable: bool = True):
+        _check(_lib.ihsbin_set_timing(self.h, int(enable)))
+
+    def reset_stats(self):
+        _check(_lib.ihsbin_reset_stats(self.h))
+
+    def kernel_stats(self):
+        """{category: (launches, ms, flops, bytes)} for every category with launches."""
+        out = {}
+        for cat in range(KCAT_COUNT):
+            n, ms, fl, by = C.c_int64(), C.c_double(), C.c_double(), C.c_double()
+            name = C.c_char_p()
+            _check(_lib.ihsbin_kernel_stats(self.h, cat, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by),
+                                            C.byref(name)))
+            if n.value:
+                out[name.value.decode()] = (n.value, ms.value, fl.value, by.value)
+        return out
 
     def close(self):
         if getattr(self, "h", None):

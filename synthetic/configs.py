@@ -222,8 +222,7 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
     cpath = _cache_path(key)
     if cpath and os.path.exists(cpath):
         z = np.load(cpath, allow_pickle=False)
-        fields = {f: (z[f] if z[f].shape != () or f in ("norm2_sq",) else None) for f in z.files}
-        return _from_cached(name, cfg, fields)
+        return _from_cached(name, cfg, {f: z[f] for f in z.files})
 
     rng = np.random.default_rng(seed)
     n, d, K = cfg["n"], cfg["d"], cfg["K"]
@@ -293,10 +292,9 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
                 m=cfg["m"], s=cfg["s"], sketch_seed=seed, lambda_min=lmin, lambda_max=lmax,
                 lambdas=lambdas, norm2_sq=norm2_sq)
     if cpath:
-        np.savez(cpath, **{f.name: (getattr(p, f.name) if getattr(p, f.name) is not None
-                                    else np.array(0))
-                           for f in dataclasses.fields(p)
-                           if f.name not in ("name", "layout", "storage", "sketch")})
+        np.savez(cpath, **{f.name: getattr(p, f.name) for f in dataclasses.fields(p)
+                           if f.name not in ("name", "layout", "storage", "sketch")
+                           and getattr(p, f.name) is not None})
     return p
 
 
@@ -304,14 +302,7 @@ def _from_cached(name, cfg, z) -> Problem:
     layout = "csr" if cfg["kind"] == "csr" else "dense"
 
     def g(f):
-        v = z.get(f)
-        if v is None:
-            return None
-        if layout == "csr" and f == "A":
-            return None
-        if layout == "dense" and f in ("row_ptr", "col_idx", "val"):
-            return None
-        return v
+        return z.get(f)
     return Problem(name=name, n=int(z["n"]), d=int(z["d"]), K=int(z["K"]), layout=layout,
                    storage=cfg["storage"], A=g("A"), row_ptr=g("row_ptr"), col_idx=g("col_idx"),
                    val=g("val"), B=z["B"], x_star=z["x_star"], sketch=cfg["sketch"],
