@@ -72,9 +72,11 @@ typedef enum { IHSBIN_DENSE_ROWMAJOR = 0, IHSBIN_CSR = 1 } ihsbin_layout;
 typedef enum { IHSBIN_SK_GAUSSIAN = 0, IHSBIN_SK_SRHT = 1, IHSBIN_SK_COUNTSKETCH = 2 } ihsbin_sketch_kind;
 
 /* How A^T (A V) is formed inside the basis loop (Algorithm 2):
- *  IHSBIN_PRODUCT_AUTO   GRAM for dense A, ASPACE for CSR;
- *  IHSBIN_PRODUCT_GRAM   form G = A^T A once, then every product is G V;
- *  IHSBIN_PRODUCT_ASPACE stream A twice per step: W = A V, Y = A^T W. */
+ *  IHSBIN_PRODUCT_AUTO   = GRAM;
+ *  IHSBIN_PRODUCT_GRAM   form G = A^T A once (dense: a split-K contraction;
+ *                        CSR: the nonzero pairs of every row), then every
+ *                        product of the loop is G V;
+ *  IHSBIN_PRODUCT_ASPACE stream A twice per step: W = A V, Y = A^T W (dense only). */
 typedef enum { IHSBIN_PRODUCT_AUTO = 0, IHSBIN_PRODUCT_GRAM = 1, IHSBIN_PRODUCT_ASPACE = 2 } ihsbin_product;
 
 /* The data matrix A (n x d).  Borrowed: when on_device = 1 the arrays must stay

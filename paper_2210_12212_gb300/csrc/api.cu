@@ -243,7 +243,44 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
       T.ld = A->n;
     }
   } else {
-    return bail(cudaErrorNotSupported, "problem_create (CSR)");
+    // CSR: device copies if needed, then the transpose, so that both CSR(A_hat) and CSR(A_hat^T) exist
+    const int64_t* rp = A->row_ptr;
+    const int32_t* ci = A->col_idx;
+    const void* val = A->values;
+    if (!A->on_device) {
+      void *drp = nullptr, *dci = nullptr, *dval = nullptr;
+      if ((e = prob_alloc(p, (size_t)(A->n + 1) * 8, &drp, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
+      if ((e = prob_alloc(p, (size_t)std::max<int64_t>(1, A->nnz) * 4, &dci, SCOPE_PERSIST)) != cudaSuccess)
+        return bail(e, "problem_create");
+      if ((e = prob_alloc(p, (size_t)std::max<int64_t>(1, A->nnz) * es, &dval, SCOPE_PERSIST)) != cudaSuccess)
+        return bail(e, "problem_create");
+      if ((e = cudaMemcpy(drp, A->row_ptr, (A->n + 1) * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
+          (e = cudaMemcpy(dci, A->col_idx, A->nnz * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
+          (e = cudaMemcpy(dval, A->values, A->nnz * es, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e, "problem_create");
+      rp = (const int64_t*)drp;
+      ci = (const int32_t*)dci;
+      val = dval;
+    }
+    int64_t* trp = nullptr;
+    int32_t* tci = nullptr;
+    void* tval = nullptr;
+    T.nnz = A->nnz;
+    ScratchScope scratch(p);
+    if ((e = launch_csr_transpose(p, rp, ci, val, T.elem, A->n, A->d, A->nnz, &trp, &tci, &tval, 0)) != cudaSuccess)
+      return bail(e, "problem_create (CSR transpose)");
+    if (!p->dual) {  // A_hat = A
+      T.N = A->n;
+      T.D = A->d;
+      T.rp = rp; T.ci = ci; T.val = val;
+      T.rpT = trp; T.ciT = tci; T.valT = tval;
+    } else {         // A_hat = A^T: its CSR is the transpose just built; CSR(A_hat^T) = A
+      T.N = A->d;
+      T.D = A->n;
+      T.rp = trp; T.ci = tci; T.val = tval;
+      T.rpT = rp; T.ciT = ci; T.valT = val;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "problem_create (CSR transpose)");
   }
   // B -> device FP64, packed n x K
   if ((e = prob_alloc(p, (size_t)A->n * K * 8, (void**)&p->B, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
@@ -289,7 +326,7 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
     if (sk->s <= 0 || sk->m % sk->s) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: need s >= 1 and m % s == 0");
   } else if (sk->kind == IHSBIN_SK_SRHT) {
     if (sk->m > Np) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: SRHT needs m <= padded row count");
-    if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: SRHT needs dense A");
+    if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: SRHT needs dense A (use CountSketch for CSR)");
   } else if (sk->kind == IHSBIN_SK_GAUSSIAN) {
     if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: Gaussian needs dense A");
   } else {
@@ -426,9 +463,9 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.jc = *std::max_element(pl.jcount.begin(), pl.jcount.end());
   pl.kmax = *std::max_element(pl.k.begin(), pl.k.end());
   pl.compute = d->compute;
-  pl.product = d->product == IHSBIN_PRODUCT_AUTO
-                   ? (p->A.layout == IHSBIN_CSR ? IHSBIN_PRODUCT_ASPACE : IHSBIN_PRODUCT_GRAM)
-                   : d->product;
+  pl.product = d->product == IHSBIN_PRODUCT_AUTO ? IHSBIN_PRODUCT_GRAM : d->product;
+  if (p->A.layout == IHSBIN_CSR && pl.product != IHSBIN_PRODUCT_GRAM)
+    return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: CSR data uses the Gram product");
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "build_basis");
   prob_free_basis(p);

@@ -10,7 +10,9 @@
 // Loader contract:  using T = element type (float, double or dd);
 //   static constexpr bool k_contig  -- consecutive k are adjacent in memory;
 //   __device__ T operator()(int g, int64_t row, int64_t col) const  (in range only).
-// Epilogue contract: __device__ void operator()(int g, int64_t i, int64_t j, Mode::V acc) const.
+// Epilogue contract: __device__ void operator()(int g, int s, int64_t i, int64_t j, Mode::V acc) const,
+// where s is the split index when the K range is split over `ksplit` CTAs
+// (each split's epilogue then writes a partial sum that a later pass reduces).
 #pragma once
 #include "common.cuh"
 
@@ -27,8 +29,22 @@ __device__ __forceinline__ dd zero_of<dd>() { return {0.f, 0.f}; }
 
 struct GemmShape {
   int64_t M, N, K;
-  int tri;  // 0: full; 1: only tiles touching i <= j; 2: only tiles touching i >= j
+  int tri;         // 0: full; 1: only tiles touching i <= j; 2: only tiles touching i >= j
+  int ksplit = 1;  // K range split over this many CTAs (partial sums per split)
+  int kdiag = 0;   // 1: operands vanish for k < max(row, col) (triangular factors): skip that range
 };
+
+// Split factor that brings a grid of `ctas` CTAs to about `target` CTAs, with
+// at least `min_tiles` BK-tiles of K per split.
+inline int pick_split(int64_t ctas, int64_t K, int BK, int64_t target = 4 * 152, int min_tiles = 4,
+                      int cap = 64) {
+  if (ctas >= target) return 1;
+  int64_t s = (target + ctas - 1) / ctas;
+  int64_t smax = K / ((int64_t)BK * min_tiles);
+  if (s > smax) s = smax;
+  if (s > cap) s = cap;
+  return s < 1 ? 1 : (int)s;
+}
 
 template <class Mode, int BM, int BN, int BK, int TM, int TN, class LA, class LB, class EP>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
@@ -42,7 +58,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   constexpr int LA_PER = BM * BK / NT;
   constexpr int LB_PER = BK * BN / NT;
 
-  const int g = blockIdx.z;
+  const int g = blockIdx.z / sh.ksplit;
+  const int sp = blockIdx.z % sh.ksplit;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
   const int64_t j0 = (int64_t)blockIdx.x * BN;
   if (i0 >= sh.M || j0 >= sh.N) return;
@@ -64,6 +81,14 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   TA ra[LA_PER];
   TB rb[LB_PER];
 
+  // this CTA's share of the K range
+  const int64_t kc = ((sh.K + sh.ksplit - 1) / sh.ksplit + BK - 1) / BK * BK;
+  int64_t kbeg = (int64_t)sp * kc;
+  const int64_t kend = (kbeg + kc < sh.K) ? kbeg + kc : sh.K;
+  if (sh.kdiag) {
+    const int64_t kd = ((i0 > j0 ? i0 : j0) / BK) * BK;
+    if (kd > kbeg) kbeg = kd;
+  }
   auto load_tiles = [&](int64_t k0) {
 #pragma unroll
     for (int q = 0; q < LA_PER; ++q) {
@@ -71,7 +96,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       int r, c;
       if (LA::k_contig) { r = e / BK; c = e % BK; } else { c = e / BM; r = e % BM; }
       int64_t gi = i0 + r, gk = k0 + c;
-      ra[q] = (gi < sh.M && gk < sh.K) ? la(g, gi, gk) : zero_of<TA>();
+      ra[q] = (gi < sh.M && gk < kend) ? la(g, gi, gk) : zero_of<TA>();
     }
 #pragma unroll
     for (int q = 0; q < LB_PER; ++q) {
@@ -79,7 +104,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       int r, c;  // r: k index, c: column
       if (LB::k_contig) { c = e / BK; r = e % BK; } else { r = e / BN; c = e % BN; }
       int64_t gk = k0 + r, gj = j0 + c;
-      rb[q] = (gk < sh.K && gj < sh.N) ? lb(g, gk, gj) : zero_of<TB>();
+      rb[q] = (gk < kend && gj < sh.N) ? lb(g, gk, gj) : zero_of<TB>();
     }
   };
   auto store_tiles = [&]() {
@@ -99,12 +124,12 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     }
   };
 
-  const int64_t ntiles = (sh.K + BK - 1) / BK;
-  load_tiles(0);
+  const int64_t ntiles = kend > kbeg ? (kend - kbeg + BK - 1) / BK : 0;
+  load_tiles(kbeg);
   for (int64_t kt = 0; kt < ntiles; ++kt) {
     store_tiles();
     __syncthreads();
-    if (kt + 1 < ntiles) load_tiles((kt + 1) * BK);
+    if (kt + 1 < ntiles) load_tiles(kbeg + (kt + 1) * BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       TA av[TM];
@@ -132,7 +157,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 #pragma unroll
     for (int b = 0; b < TN; ++b) {
       int64_t gj = j0 + tx + b * RX;
-      if (gj < sh.N) ep(g, gi, gj, acc[a][b]);
+      if (gj < sh.N) ep(g, sp, gi, gj, acc[a][b]);
     }
   }
 }
@@ -140,7 +165,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 template <class Mode, int BM, int BN, int BK, int TM, int TN, class LA, class LB, class EP>
 inline cudaError_t launch_gemm(GemmShape sh, int groups, LA la, LB lb, EP ep, cudaStream_t st) {
   if (sh.M <= 0 || sh.N <= 0 || groups <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((sh.N + BN - 1) / BN), (unsigned)((sh.M + BM - 1) / BM), (unsigned)groups);
+  dim3 grid((unsigned)((sh.N + BN - 1) / BN), (unsigned)((sh.M + BM - 1) / BM), (unsigned)(groups * sh.ksplit));
   gemm_kernel<Mode, BM, BN, BK, TM, TN, LA, LB, EP><<<grid, (BM / TM) * (BN / TN), 0, st>>>(sh, la, lb, ep);
   return cudaGetLastError();
 }

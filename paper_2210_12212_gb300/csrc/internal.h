@@ -136,6 +136,11 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st);
 cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st);
 
 cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev);
+
+// CSR data (sparse.cu)
+cudaError_t csr_gram(ihsbin_problem* p, int compute, cudaStream_t st);
+cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
+cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
 cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,
                         cudaStream_t st);
 

@@ -155,7 +155,7 @@ template <class Mode>
 struct EpStoreSym {  // symmetric result: write (i, j) and (j, i) into a D x D matrix (group stride gs)
   CBuf M;
   int64_t D, gs;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
     if (i > j) return;
     Mode::st(M, g * gs + i * D + j, a);
     Mode::st(M, g * gs + j * D + i, a);
@@ -165,16 +165,16 @@ struct EpStoreSymF64 {  // symmetric result into an FP64 matrix
   double* M;
   int64_t D;
   template <class V>
-  __device__ __forceinline__ void operator()(int, int64_t i, int64_t j, V a) const;
+  __device__ __forceinline__ void operator()(int, int, int64_t i, int64_t j, V a) const;
 };
 template <>
-__device__ __forceinline__ void EpStoreSymF64::operator()<double>(int, int64_t i, int64_t j, double a) const {
+__device__ __forceinline__ void EpStoreSymF64::operator()<double>(int, int, int64_t i, int64_t j, double a) const {
   if (i > j) return;
   M[i * D + j] = a;
   M[j * D + i] = a;
 }
 template <>
-__device__ __forceinline__ void EpStoreSymF64::operator()<dd>(int, int64_t i, int64_t j, dd a) const {
+__device__ __forceinline__ void EpStoreSymF64::operator()<dd>(int, int, int64_t i, int64_t j, dd a) const {
   if (i > j) return;
   double v = dd_to_double(a);
   M[i * D + j] = v;
@@ -183,18 +183,61 @@ __device__ __forceinline__ void EpStoreSymF64::operator()<dd>(int, int64_t i, in
 struct EpStoreF64 {  // plain store into an FP64 row-major matrix with row stride ld (group stride gs)
   double* M;
   int64_t ld, gs;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, double a) const { M[g * gs + i * ld + j] = a; }
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, double a) const { M[g * gs + i * ld + j] = a; }
 };
 template <class Mode>
 struct EpStoreColMajor {  // result (i, j) -> M[g*gs + j*D + i]
   CBuf M;
   int64_t D, gs;
   const int* perm;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
     int64_t gi = perm ? perm[g] : g;
     Mode::st(M, gi * gs + j * D + i, a);
   }
 };
+
+// split-K partial sums: buf[((s * G + g) * N + j) * M + i]
+template <class Mode>
+struct EpPartial {
+  CBuf buf;
+  int64_t M, N, G;
+  __device__ __forceinline__ void operator()(int g, int s, int64_t i, int64_t j, typename Mode::V a) const {
+    Mode::st(buf, (((int64_t)s * G + g) * N + j) * M + i, Mode::renorm(a));
+  }
+};
+
+// symmetric D x D result from S partials of the upper triangle
+template <class Mode>
+__global__ void k_reduce_sym(CBuf part, int S, int64_t D, CBuf out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D * D) return;
+  int64_t i = e / D, j = e % D;
+  if (i > j) return;
+  typename Mode::V v = Mode::ld(part, j * D + i);
+  for (int s = 1; s < S; ++s) v = Mode::add(v, Mode::ld(part, ((int64_t)s * D + j) * D + i));
+  Mode::st(out, i * D + j, v);
+  Mode::st(out, j * D + i, v);
+}
+// column-major M x N result (one group) from S partials
+template <class Mode>
+__global__ void k_reduce_cols(CBuf part, int S, int64_t M, int64_t N, CBuf out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  typename Mode::V v = Mode::ld(part, e);
+  for (int s = 1; s < S; ++s) v = Mode::add(v, Mode::ld(part, (int64_t)s * M * N + e));
+  Mode::st(out, e, v);
+}
+
+// Tile shape by the column count N (small N: narrow tiles, so that the
+// padded columns do not multiply the work).
+template <class Mode, class LA, class LB, class EP>
+static cudaError_t launch_gemm_n(GemmShape sh, int groups, LA la, LB lb, EP ep, cudaStream_t st) {
+  if (sh.N <= 8) return launch_gemm<Mode, 64, 8, 32, 2, 1>(sh, groups, la, lb, ep, st);
+  if (sh.N <= 16) return launch_gemm<Mode, 64, 16, 16, 4, 1>(sh, groups, la, lb, ep, st);
+  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, groups, la, lb, ep, st);
+}
+static inline int tile_n(int64_t N) { return N <= 8 ? 8 : N <= 16 ? 16 : 32; }
+static inline int tile_k(int64_t N) { return N <= 8 ? 32 : 16; }
 
 // =============================================================== a1: sketches
 // Gaussian entries S[i][j] = z_ij / sqrt(m), z by Box-Muller on (w0, w1) of
@@ -230,12 +273,12 @@ struct EpAccumF64 {  // SA[i][j] += acc (FP64; each element owned by one thread 
   double* M;
   int64_t ld;
   template <class V>
-  __device__ __forceinline__ void operator()(int, int64_t i, int64_t j, V a) const;
+  __device__ __forceinline__ void operator()(int, int, int64_t i, int64_t j, V a) const;
 };
 template <>
-__device__ __forceinline__ void EpAccumF64::operator()<double>(int, int64_t i, int64_t j, double a) const { M[i * ld + j] += a; }
+__device__ __forceinline__ void EpAccumF64::operator()<double>(int, int, int64_t i, int64_t j, double a) const { M[i * ld + j] += a; }
 template <>
-__device__ __forceinline__ void EpAccumF64::operator()<dd>(int, int64_t i, int64_t j, dd a) const {
+__device__ __forceinline__ void EpAccumF64::operator()<dd>(int, int, int64_t i, int64_t j, dd a) const {
   M[i * ld + j] += dd_to_double(a);
 }
 
@@ -568,10 +611,19 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
 // G_S = (S A_hat)^T (S A_hat) in FP64 (the sketched Hessian without the shift).
 cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) {
   const int64_t m = p->sk.m, D = p->A.D;
+  const int64_t tm = (D + 63) / 64;
   GemmShape sh{D, D, m, 1};
+  sh.ksplit = pick_split(tm * (tm + 1) / 2, m, 16);
   KTimer kt(p, K_SKETCH_GRAM, st, (double)m * D * (D + 1), (double)m * D * 8 + (double)D * D * 8);
-  return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
-                                             EpStoreSymF64{p->GS, D}, st);
+  if (sh.ksplit == 1)
+    return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
+                                               EpStoreSymF64{p->GS, D}, st);
+  CBuf part;
+  CK(prob_alloc(p, (size_t)sh.ksplit * D * D * 8, &part.p0, SCOPE_SCRATCH));
+  CK((launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
+                                          EpPartial<F64>{part, D, D, 1}, st)));
+  k_reduce_sym<F64><<<nblocks(D * D, 256), 256, 0, st>>>(part, sh.ksplit, D, CBuf{p->GS, nullptr});
+  return cudaGetLastError();
 }
 
 // ======================================================= a2: factor and inverse
@@ -676,7 +728,7 @@ template <class Mode>
 struct EpPanel {
   CBuf H;
   int64_t D, r0, c0;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
     Mode::st(H, (int64_t)g * D * D + (r0 + i) * D + c0 + j, a);
   }
 };
@@ -694,7 +746,7 @@ template <class Mode>
 struct EpTrailing {  // H[r0+i][r0+j] -= acc on the lower triangle
   CBuf H;
   int64_t D, r0;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
     if (j > i) return;
     int64_t o = (int64_t)g * D * D + (r0 + i) * D + r0 + j;
     Mode::st(H, o, Mode::sub(Mode::ld(H, o), a));
@@ -828,9 +880,10 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
     k_trtri<Mode><<<dim3((unsigned)nblk, L), 256, 0, st>>>(H, dinv, Wm, D);
   }
   CK(cudaGetLastError());
-  // P_l = W^T W
+  // P_l = W^T W  (W lower triangular: the sum starts at k = max(i, j))
   GemmShape sh{D, D, D, 1};
-  KTimer kt(p, K_INVERSE, st, (double)L * D * D * (D + 1) / 3.0, (double)L * D * D * cs * 2);
+  sh.kdiag = 1;
+  KTimer kt(p, K_INVERSE, st, (double)L * D * (D + 1) * (D + 2) / 3.0, (double)L * D * D * cs * 2);
   return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, L, LdWT<Mode>{Wm, D}, LdW<Mode>{Wm, D},
                                              EpStoreSym<Mode>{p->Pinv, D, D * D}, st);
 }
@@ -839,10 +892,21 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
 template <class Mode, int ET>
 static cudaError_t gram_dense(ihsbin_problem* p, cudaStream_t st) {
   const Tall& A = p->A;
-  GemmShape sh{A.D, A.D, A.N, 1};
-  KTimer kt(p, K_GRAM, st, (double)A.N * A.D * (A.D + 1), (double)A.N * A.D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
-  return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdRowB<Mode, ET>{A.A, A.ld},
-                                             EpStoreSym<Mode>{p->G, A.D, 0}, st);
+  const int64_t D = A.D, tm = (D + 63) / 64;
+  GemmShape sh{D, D, A.N, 1};
+  sh.ksplit = pick_split(tm * (tm + 1) / 2, A.N, 16);
+  KTimer kt(p, K_GRAM, st, (double)A.N * D * (D + 1), (double)A.N * D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
+  if (sh.ksplit == 1)
+    return launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdRowB<Mode, ET>{A.A, A.ld},
+                                               EpStoreSym<Mode>{p->G, D, 0}, st);
+  cudaError_t err = cudaSuccess;
+  CBuf part = alloc_cbuf(p, Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2, (size_t)sh.ksplit * D * D,
+                         SCOPE_SCRATCH, &err);
+  CK(err);
+  CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdRowB<Mode, ET>{A.A, A.ld},
+                                          EpPartial<Mode>{part, D, D, 1}, st)));
+  k_reduce_sym<Mode><<<nblocks(D * D, 256), 256, 0, st>>>(part, sh.ksplit, D, p->G);
+  return cudaGetLastError();
 }
 
 template <class Mode>
@@ -865,10 +929,21 @@ __global__ void k_copy_B_colmajor(const double* B, int64_t n, int64_t K, CBuf c)
 template <class Mode, int ET>
 static cudaError_t rhs_dense(ihsbin_problem* p, CBuf c, cudaStream_t st) {
   const Tall& A = p->A;
-  GemmShape sh{A.D, p->K, A.N, 0};
-  KTimer kt(p, K_RHS, st, 2.0 * A.N * A.D * p->K, (double)A.N * A.D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
-  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdBcol<Mode>{p->B, p->K},
-                                             EpStoreColMajor<Mode>{c, A.D, 0, nullptr}, st);
+  const int64_t D = A.D, K = p->K;
+  GemmShape sh{D, K, A.N, 0};
+  sh.ksplit = pick_split(((D + 63) / 64) * ((K + tile_n(K) - 1) / tile_n(K)), A.N, tile_k(K));
+  KTimer kt(p, K_RHS, st, 2.0 * A.N * D * K, (double)A.N * D * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
+  if (sh.ksplit == 1)
+    return launch_gemm_n<Mode>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdBcol<Mode>{p->B, K},
+                               EpStoreColMajor<Mode>{c, D, 0, nullptr}, st);
+  cudaError_t err = cudaSuccess;
+  CBuf part = alloc_cbuf(p, Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2, (size_t)sh.ksplit * D * K,
+                         SCOPE_SCRATCH, &err);
+  CK(err);
+  CK((launch_gemm_n<Mode>(sh, 1, LdTrans<Mode, ET>{A.A, A.ld}, LdBcol<Mode>{p->B, K}, EpPartial<Mode>{part, D, K, 1},
+                          st)));
+  k_reduce_cols<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(part, sh.ksplit, D, K, c);
+  return cudaGetLastError();
 }
 
 // ===================================================== a4: the basis recursion
@@ -879,7 +954,7 @@ struct EpInit {  // u_00 = P c: write U0 and Ut
   CBuf U, Ut;
   int64_t D, gs;
   const int* perm;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t j, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
     int64_t o = (int64_t)perm[g] * gs + j * D + i;
     a = Mode::renorm(a);
     Mode::st(U, o, a);
@@ -895,11 +970,13 @@ struct LdR {
   using T = typename Mode::V;
   static constexpr bool k_contig = true;
   CBuf U, Y;
-  int64_t D, K, gs, ys;
+  int64_t D, K, gs, ys;   // ys: per-group stride of Y; the ny splits of Y are ny_stride apart
   int i;
   const int* perm;
   const double* tau;
   const double* lam0;
+  int ny;
+  int64_t ny_stride;
   __device__ __forceinline__ T operator()(int g, int64_t k, int64_t col) const {
     const int l = perm[g];
     const int64_t j = col / K;
@@ -907,7 +984,9 @@ struct LdR {
     const T lm = Mode::from_d(lam0[l]);
     if (j == i) return Mode::mul(lm, Mode::ld(U, o - K * D));
     T u = Mode::ld(U, o);
-    T y = Mode::ld(Y, (int64_t)g * ys + col * D + k);
+    const int64_t yo = (int64_t)g * ys + col * D + k;
+    T y = Mode::ld(Y, yo);
+    for (int s = 1; s < ny; ++s) y = Mode::add(y, Mode::ld(Y, s * ny_stride + yo));
     T r = Mode::mul(Mode::from_d(tau[l]), Mode::add(y, Mode::mul(lm, u)));
     if (j > 0) r = Mode::add(r, Mode::mul(lm, Mode::ld(U, o - K * D)));
     return r;
@@ -919,7 +998,7 @@ struct EpUpdate {  // u_j <- u_j - P R_j (new column: u_i = -P R_i); utilde_j +=
   int64_t D, K, gs;
   int i;
   const int* perm;
-  __device__ __forceinline__ void operator()(int g, int64_t row, int64_t col, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t row, int64_t col, typename Mode::V a) const {
     const int64_t o = (int64_t)perm[g] * gs + col * D + row;
     const int64_t j = col / K;
     typename Mode::V u = (j < i) ? Mode::ld(Uin, o) : Mode::zero();
@@ -928,12 +1007,59 @@ struct EpUpdate {  // u_j <- u_j - P R_j (new column: u_i = -P R_i); utilde_j +=
     Mode::st(Ut, o, Mode::add(Mode::ld(Ut, o), u));
   }
 };
+// The preconditioner's right-hand sides of one step, once per element:
+//   R_j = tau (sum_s Y_s,j + lam0 u_j) + lam0 u_{j-1}   (j < i; no shift term for j = 0)
+//   R_i = lam0 u_{i-1}                                 (the new column, when i < jmax)
+template <class Mode>
+__global__ void k_make_R(CBuf Y, int ny, int64_t ny_stride, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D,
+                         int64_t K, int inew, const int* perm, const double* tau, const double* lam0, int64_t gs,
+                         CBuf R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)live * nnew * D) return;
+  const int g = (int)(e / (nnew * D));
+  const int64_t col = (e / D) % nnew, k = e % D;
+  const int l = perm[g];
+  const int64_t j = col / K;
+  const int64_t o = (int64_t)l * gs + col * D + k;
+  const typename Mode::V lm = Mode::from_d(lam0[l]);
+  typename Mode::V r;
+  if (j == inew) {
+    r = Mode::mul(lm, Mode::ld(U, o - K * D));
+  } else {
+    const int64_t yo = ((int64_t)g * nold + col) * D + k;
+    typename Mode::V y = Mode::ld(Y, yo);
+    for (int s = 1; s < ny; ++s) y = Mode::add(y, Mode::ld(Y, s * ny_stride + yo));
+    r = Mode::mul(Mode::from_d(tau[l]), Mode::add(y, Mode::mul(lm, Mode::ld(U, o))));
+    if (j > 0) r = Mode::add(r, Mode::mul(lm, Mode::ld(U, o - K * D)));
+  }
+  Mode::st(R, e, r);
+}
+
+// u_j <- u_j - sum_s Z_s (new column: -sum_s Z_s); utilde_j += u_j, from split partials of P R
+template <class Mode>
+__global__ void k_update(CBuf Z, int S, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin, CBuf Uout,
+                         CBuf Ut, const int* perm, int64_t gs) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)live * ncol * D) return;
+  const int g = (int)(e / (ncol * D));
+  const int64_t col = (e / D) % ncol, row = e % D;
+  const int64_t zo = ((int64_t)g * ncol + col) * D + row;
+  typename Mode::V z = Mode::ld(Z, zo);
+  for (int s = 1; s < S; ++s) z = Mode::add(z, Mode::ld(Z, (int64_t)s * live * ncol * D + zo));
+  const int64_t o = (int64_t)perm[g] * gs + col * D + row;
+  const int64_t j = col / K;
+  typename Mode::V u = (j < i) ? Mode::ld(Uin, o) : Mode::zero();
+  u = Mode::sub(u, z);
+  Mode::st(Uout, o, u);
+  Mode::st(Ut, o, Mode::add(Mode::ld(Ut, o), u));
+}
+
 // Y = A^T A U for the Gram product: the B operand is U (column j, contiguous over k)
 template <class Mode>
 struct EpY {
   CBuf Y;
   int64_t D, ys;
-  __device__ __forceinline__ void operator()(int g, int64_t i, int64_t col, typename Mode::V a) const {
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t col, typename Mode::V a) const {
     Mode::st(Y, (int64_t)g * ys + col * D + i, Mode::renorm(a));
   }
 };
@@ -956,8 +1082,11 @@ struct LdWcol {  // operand (k, j) = Wtmp[g][j][k] (column-major, N rows)
   __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const { return Mode::ld(Wt, (int64_t)g * ws + j * N + k); }
 };
 
+constexpr int SPLIT_MAX = 16;
+
 template <class Mode, int ET>
-static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf Y, CBuf Wtmp, const int* perm_dev,
+static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf Y, CBuf Z, CBuf R, CBuf Wtmp,
+                              const int* perm_dev,
                               const double* tau_dev, const double* lam0_dev, const std::vector<int>& order,
                               cudaStream_t st) {
   const Tall& A = p->A;
@@ -969,7 +1098,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
   {
     GemmShape sh{D, K, D, 0};
     KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * K * L, (double)L * D * D * 8);
-    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, L, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
+    CK((launch_gemm_n<Mode>(sh, L, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
                                             LdCColB<Mode>{c, D, 0, nullptr}, EpInit<Mode>{U0, p->Ut, D, gs, perm_dev},
                                             st)));
   }
@@ -982,11 +1111,15 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t nold = (int64_t)std::min(i, J) * K;
     const int64_t nnew = (int64_t)std::min(i + 1, J) * K;
     const int64_t ys = nold * D;
+    const int64_t mt = (D + 63) / 64;
+    int ny = 1;
     if (pl.product == IHSBIN_PRODUCT_GRAM) {
       GemmShape sh{D, nold, D, 0};
+      sh.ksplit = ny = std::min(pick_split(mt * ((nold + tile_n(nold) - 1) / tile_n(nold)) * live, D, tile_k(nold)),
+                                SPLIT_MAX);
       KTimer kt(p, K_LOOP_Y, st, 2.0 * D * D * nold * live, (double)D * D * 8 + 16.0 * D * nold * live);
-      CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, live, LdCMatA<Mode>{p->G, D, 0, nullptr},
-                                              LdCColB<Mode>{Uin, D, gs, perm_dev}, EpY<Mode>{Y, D, ys}, st)));
+      CK((launch_gemm_n<Mode>(sh, live, LdCMatA<Mode>{p->G, D, 0, nullptr}, LdCColB<Mode>{Uin, D, gs, perm_dev},
+                              EpPartial<Mode>{Y, D, nold, live}, st)));
     } else {
       // W = A_hat U (N x nold), then Y = A_hat^T W
       const int64_t N = A.N;
@@ -1002,11 +1135,31 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     }
     GemmShape sp{D, nnew, D, 0};
     const int inew = (i < J) ? i : -1;
-    KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 32.0 * D * nnew * live);
-    CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(
-        sp, live, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
-        LdR<Mode>{Uin, Y, D, K, gs, ys, inew, perm_dev, tau_dev, lam0_dev},
-        EpUpdate<Mode>{Uin, Uout, p->Ut, D, K, gs, inew < 0 ? (1 << 30) : i, perm_dev}, st)));
+    sp.ksplit = std::min(pick_split(mt * ((nnew + tile_n(nnew) - 1) / tile_n(nnew)) * live, D, tile_k(nnew)),
+                         SPLIT_MAX);
+    {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * 8 * (ny + 3));
+      k_make_R<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
+          Y, ny, (int64_t)live * ys, Uin, live, nold, nnew, D, K, inew, perm_dev, tau_dev, lam0_dev, gs, R);
+      CK(cudaGetLastError());
+    }
+    const LdCColB<Mode> ldr{R, D, nnew * D, nullptr};
+    {
+      KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 32.0 * D * nnew * live);
+      if (sp.ksplit == 1) {
+        CK((launch_gemm_n<Mode>(sp, live, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev}, ldr,
+                                EpUpdate<Mode>{Uin, Uout, p->Ut, D, K, gs, i, perm_dev}, st)));
+      } else {
+        CK((launch_gemm_n<Mode>(sp, live, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev}, ldr,
+                                EpPartial<Mode>{Z, D, nnew, live}, st)));
+      }
+    }
+    if (sp.ksplit > 1) {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * 8 * (sp.ksplit + 3));
+      k_update<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(Z, sp.ksplit, live, nnew, D, K, i, Uin,
+                                                                            Uout, p->Ut, perm_dev, gs);
+      CK(cudaGetLastError());
+    }
     std::swap(Uin, Uout);
   }
   return cudaSuccess;
@@ -1096,12 +1249,16 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   // a3: Gram (product mode GRAM) and right-hand side
   CBuf c = cb((size_t)D * K);
   CK(err);
+  const bool csr = A.layout == IHSBIN_CSR;
   if (pl.product == IHSBIN_PRODUCT_GRAM) {
     p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
     CK(err);
-    CK((gram_dense<Mode, ET>(p, st)));
+    if (csr) CK(csr_gram(p, cm, st));
+    else CK((gram_dense<Mode, ET>(p, st)));
   }
-  if (p->dual) {
+  if (csr && !p->dual) {
+    CK(csr_rhs(p, cm, c, st));
+  } else if (p->dual) {
     KTimer kt(p, K_RHS, st, 0, (double)D * K * 16);
     k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(p->B, D, K, c);
     CK(cudaGetLastError());
@@ -1116,7 +1273,9 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   p->Ut = alloc_cbuf(p, cm, per * L, SCOPE_BASIS, &err);
   CK(err);
   const int64_t ncol_max = (int64_t)pl.jc * K;
-  CBuf Y = cb((size_t)ncol_max * D * L);
+  CBuf Y = cb((size_t)SPLIT_MAX * ncol_max * D * L);
+  CBuf Z = cb((size_t)SPLIT_MAX * ncol_max * D * L);
+  CBuf R = cb((size_t)ncol_max * D * L);
   CBuf Wtmp{};
   if (pl.product == IHSBIN_PRODUCT_ASPACE) Wtmp = cb((size_t)ncol_max * A.N * L);
   CK(err);
@@ -1124,10 +1283,14 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   if (U0.p1) CK(cudaMemsetAsync(U0.p1, 0, per * L * 4, st));
   CK(cudaMemsetAsync(p->Ut.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
   if (p->Ut.p1) CK(cudaMemsetAsync(p->Ut.p1, 0, per * L * 4, st));
-  CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Wtmp, perm_dev, tau_dev, lam0_dev, order, st)));
+  CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Z, R, Wtmp, perm_dev, tau_dev, lam0_dev, order, st)));
 
   // a5: primal image of the dual basis, W_l = A_hat utilde_l (N x jc K)
-  if (p->dual) {
+  if (p->dual && csr) {
+    p->W = alloc_cbuf(p, cm, (size_t)L * pl.jc * K * A.N, SCOPE_BASIS, &err);
+    CK(err);
+    CK(csr_dual_map(p, cm, (int64_t)pl.jc * K, st));
+  } else if (p->dual) {
     const int64_t N = A.N;
     p->W = alloc_cbuf(p, cm, (size_t)L * pl.jc * K * N, SCOPE_BASIS, &err);
     CK(err);
@@ -1142,7 +1305,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
 
 cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev) {
   const int cm = p->plan.compute, et = p->A.elem;
-  if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  if (p->A.layout == IHSBIN_CSR && p->plan.product != IHSBIN_PRODUCT_GRAM) return cudaErrorNotSupported;
   if (cm == IHSBIN_COMPUTE_F64) {
     if (et == ELEM_F64) return build_typed<F64, ELEM_F64>(p, st, ev);
     if (et == ELEM_F32) return build_typed<F64, ELEM_F32>(p, st, ev);
@@ -1190,9 +1353,5 @@ cudaError_t eval_device(ihsbin_problem* p, const double* lam_dev, int64_t T, voi
   return eval_typed<DD>(p, lam_dev, T, X, x_elem, st);
 }
 
-cudaError_t launch_csr_transpose(ihsbin_problem*, const int64_t*, const int32_t*, const void*, int, int64_t, int64_t,
-                                 int64_t, int64_t**, int32_t**, void**, cudaStream_t) {
-  return cudaErrorNotSupported;
-}
 
 }  // namespace ihsbin

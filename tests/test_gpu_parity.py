@@ -179,3 +179,45 @@ def test_call_order_enforced(ctx):
         gp.build_basis(prob.lambda_min, prob.lambda_max, k_default=3)
     assert ei.value.status == ihs.ERR_STATE
     gp.close()
+
+
+def csr_under(prob, seed=3):
+    """Under-determined CSR variant: A_u = A^T of a CSR workload, fresh b_u."""
+    t = prob.transpose()
+    rng = np.random.default_rng(seed)
+    B = rng.standard_normal((t.n, 1))
+    import dataclasses
+    return dataclasses.replace(t, B=B, x_star=np.zeros((t.d, 1)))
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32x2"])
+def test_c3_small_csr_sjlt(ctx, compute):
+    prob = small("c3_small")
+    gp, Xg, res, plan = run_both(ctx, prob, compute, k=30)
+    assert rel_err_max(Xg, res.X) <= TOL[compute]
+    gp.close()
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32x2"])
+def test_c3_small_csr_underdetermined_dual(ctx, compute):
+    prob = csr_under(small("c3_small"))
+    assert prob.n < prob.d
+    gp, Xg, res, plan = run_both(ctx, prob, compute, k=30)
+    assert res.dual and Xg.shape == (len(prob.lambdas), prob.d, 1)
+    assert rel_err_max(Xg, res.X) <= TOL[compute]
+    gp.close()
+
+
+def test_csr_countsketch_draws_bit_exact(ctx):
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small("c3_small")
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch("countsketch", prob.m, prob.s, 77)
+    idx, sign, cnt = gp.sketch_export(prob.n * prob.s)
+    rows, sg = osk.countsketch_map(prob.n, prob.m, prob.s, 77)
+    np.testing.assert_array_equal(idx[:cnt].reshape(prob.n, prob.s), rows)
+    np.testing.assert_array_equal(sign[:cnt].reshape(prob.n, prob.s).astype(float), sg)
+    SA, GS = gp.sketch_matrices(prob.m, prob.d)
+    SAo = osk.apply_countsketch(oracle_A(prob), prob.m, prob.s, 77)
+    np.testing.assert_allclose(SA, SAo, rtol=0, atol=1e-12 * np.abs(SAo).max())
+    gp.close()
