@@ -219,6 +219,30 @@ IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,
                                              double* flops, double* bytes, const char** name);
 
+/* Allocation-free variant of the sketched Gram matrix (the paper has no
+ * counterpart; this exists for callers that cannot allocate device memory).
+ *
+ * GS (D x D, row-major FP64, device) = SA^T SA for SA (m x D, row-major FP64,
+ * device) -- the same matrix ihsbin_sketch forms from its sketch.  Callers
+ * that cannot call cudaMalloc where they need it (code running under stream
+ * capture into a CUDA graph, where cudaMalloc is not capturable; latency-bound
+ * callers that cannot absorb an allocation's device synchronisation; hosts
+ * whose memory pool forbids library allocations) use this entry point: it
+ * calls no cudaMalloc, cudaFree or allocating library routine.  Its split-K
+ * partial sums live in one file-scope device array of
+ * IHSBIN_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the
+ * library holds until the process exits; D*D must fit in it (D <= 1448),
+ * otherwise IHSBIN_ERR_INVALID_ARG is returned before anything is launched.
+ * All calls share that array: calls that overlap on the GPU race, so
+ * serialise them.  The first call on a device (with that device current) looks
+ * up the array's device address and caches it; make that first call before any
+ * stream capture.  Stream-ordered on `stream` (a cudaStream_t, NULL = legacy
+ * default stream); returns after enqueueing, without synchronising.  Inputs and
+ * outputs are caller-owned. */
+#define IHSBIN_NOALLOC_SCRATCH_BYTES (16u << 20)
+IHSBIN_API ihsbin_status ihsbin_sketch_gram_noalloc(const double* SA, int64_t m, int64_t D, double* GS,
+                                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,8 @@ ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where
 
 namespace ihsbin {
 
+void set_last_error(const char* msg) { g_err = msg; }
+
 cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
   *out = nullptr;
   if (bytes == 0) bytes = 16;

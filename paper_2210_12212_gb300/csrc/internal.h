@@ -101,6 +101,9 @@ struct ihsbin_problem {
 
 namespace ihsbin {
 
+// Text returned by ihsbin_last_error() on this thread (api.cu).
+void set_last_error(const char* msg);
+
 // ----- allocation helpers (api.cu) --------------------------------------------
 // Lifetime of a device allocation: the problem, the current basis, or the current call.
 enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2 };

@@ -63,7 +63,7 @@ EXPORTED = [
     "ihsbin_problem_create", "ihsbin_problem_destroy", "ihsbin_sketch", "ihsbin_sketch_export",
     "ihsbin_sketch_matrix_export", "ihsbin_build_basis", "ihsbin_plan_export", "ihsbin_basis_export",
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
-    "ihsbin_kernel_stats",
+    "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc",
 ]
 KCAT_COUNT = 17
 
@@ -96,6 +96,7 @@ def load(path: Optional[str] = None):
         "ihsbin_set_timing": [vp, C.c_int],
         "ihsbin_reset_stats": [vp],
         "ihsbin_kernel_stats": [vp, i32, vp, vp, vp, vp, vp],
+        "ihsbin_sketch_gram_noalloc": [vp, i64, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
