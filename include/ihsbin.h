@@ -17,9 +17,13 @@
  *    kernel traps: faults detected on the device (non-positive pivot, NaN)
  *    come back through a device status word read at the call's synchronisation
  *    point;
- *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
- *    stream); every call is stream-ordered and returns after its own work on
- *    that stream has completed (the status word is read there);
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the calling thread's
+ *    default stream; the library is built with per-thread default streams, so
+ *    calls from different host threads never serialise on a shared stream);
+ *    every call is stream-ordered and returns after its own work on that
+ *    stream has completed (the status word is read there);
+ *  - device memory comes from a stream-ordered pool owned by the context
+ *    (freed blocks are kept for reuse), so no call synchronises the device;
  *  - on error, outputs are unspecified and the problem keeps its previous state;
  *  - ihsbin_last_error() returns a thread-local description of the last error.
  */
@@ -118,7 +122,13 @@ typedef struct {
  *           positive value keeps only the terms j < jmax.  The recursion for
  *           j < jmax is unchanged, so the result differs from the full basis
  *           only by the omitted high-order terms of the expansion in
- *           theta = tau (lam - lam0) / lam0. */
+ *           theta = tau (lam - lam0) / lam0.
+ *  auto_rho nonzero (with rho1/rho2 NULL): rho_l = min(d_e(lam0_l)/m, 0.95) with the
+ *           effective dimension of Section 4.2 estimated from the sketch,
+ *           d_e = tr(G_S (G_S + lam0 I)^-1) = D - lam0 tr(P_l) (taking ||D||_2 = 1).
+ *  eps      with k == NULL and k_default <= 0, k_l is Theorem 4's iteration
+ *           count for relative error eps: ceil(ln eps / ln((kt-1)/(kt+1))) with
+ *           kt = rho1 hi_l / (rho2 lo_l) (eps <= 0 selects 1e-7). */
 typedef struct {
   double lambda_min, lambda_max;
   int32_t L;
@@ -130,6 +140,8 @@ typedef struct {
   int32_t jmax;
   ihsbin_compute compute;
   ihsbin_product product;
+  double eps;
+  int32_t auto_rho;
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -219,6 +231,55 @@ IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,
                                              double* flops, double* bytes, const char** name);
 
+/* ---- Serving: a continuous-batching request loop (the library's runtime; the
+ * paper solves one problem at a time).  `slots` worker threads each own a CUDA
+ * stream; a worker admits the first queued request whose estimated device
+ * footprint (ihsbin_request_footprint) fits the budget left, runs its whole
+ * path (create, sketch, basis, evaluation, destroy) on its stream, and frees
+ * the footprint when done, so requests arriving while others run enter as
+ * slots and memory free up and their kernels overlap on the device.  Each
+ * request is an independent problem: its result does not depend on what else
+ * runs (up to the order of FP64 atomic additions in CSR Gram and CountSketch
+ * accumulation). */
+typedef struct ihsbin_server ihsbin_server;
+typedef struct {
+  int32_t slots;             /* concurrent requests; 0 selects 4                                  */
+  uint64_t hbm_budget_bytes; /* admission budget; 0 selects the context's budget (0 = unlimited)  */
+} ihsbin_serve_config;
+typedef struct {
+  ihsbin_matrix A;           /* borrowed until the request completes                               */
+  const void* B;             /* n x K, row stride ldb, borrowed until completion                   */
+  int64_t K, ldb;
+  ihsbin_dtype b_dtype;
+  int b_on_device;
+  ihsbin_sketch_desc sketch;
+  ihsbin_path_desc path;     /* its arrays (k, rho1, rho2) borrowed until completion               */
+  const double* lambdas;     /* T values, copied at submission                                     */
+  int64_t T;
+  void* X;                   /* T x d x K output (ihsbin_eval_path layout), written on completion   */
+  ihsbin_dtype x_dtype;
+  int x_on_device;
+} ihsbin_request;
+
+/* Upper estimate of the device memory the request holds at its peak. */
+IHSBIN_API ihsbin_status ihsbin_request_footprint(const ihsbin_request* q, uint64_t* bytes);
+/* Start the workers.  Release with ihsbin_serve_destroy. */
+IHSBIN_API ihsbin_status ihsbin_serve_create(ihsbin_ctx* ctx, const ihsbin_serve_config* cfg, ihsbin_server** out);
+/* Queue a request (non-blocking).  IHSBIN_ERR_ADMISSION if its footprint can never fit the budget. */
+IHSBIN_API ihsbin_status ihsbin_serve_submit(ihsbin_server* s, const ihsbin_request* q, uint64_t* ticket);
+/* Wait up to timeout_us (0 = poll) for a request: IHSBIN_ERR_TIMEOUT if it is not done (the ticket
+ * stays valid); otherwise *result is the request's status and the ticket is released.  times4 (may
+ * be NULL) receives seconds of queueing, service, submission-to-completion, and device time. */
+IHSBIN_API ihsbin_status ihsbin_serve_wait(ihsbin_server* s, uint64_t ticket, int64_t timeout_us,
+                                           ihsbin_status* result, double* times4);
+/* Finish every queued and running request, then stop the workers. */
+IHSBIN_API ihsbin_status ihsbin_serve_destroy(ihsbin_server* s);
+/* Blocking driver: submits reqs[i] at arrival_s[i] seconds after the call (NULL = all at once),
+ * waits for all, and reports each status and its latency from scheduled arrival to completion. */
+IHSBIN_API ihsbin_status ihsbin_serve(ihsbin_ctx* ctx, const ihsbin_serve_config* cfg, const ihsbin_request* reqs,
+                                      int64_t n, const double* arrival_s, ihsbin_status* results,
+                                      double* latency_s);
+
 /* Allocation-free variant of the sketched Gram matrix (the paper has no
  * counterpart; this exists for callers that cannot allocate device memory).
  *
@@ -236,8 +297,9 @@ IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int
  * All calls share that array: calls that overlap on the GPU race, so
  * serialise them.  The first call on a device (with that device current) looks
  * up the array's device address and caches it; make that first call before any
- * stream capture.  Stream-ordered on `stream` (a cudaStream_t, NULL = legacy
- * default stream); returns after enqueueing, without synchronising.  Inputs and
+ * stream capture.  Stream-ordered on `stream` (a cudaStream_t, NULL = the
+ * calling thread's default stream); returns after enqueueing, without
+ * synchronising.  Inputs and
  * outputs are caller-owned. */
 #define IHSBIN_NOALLOC_SCRATCH_BYTES (16u << 20)
 IHSBIN_API ihsbin_status ihsbin_sketch_gram_noalloc(const double* SA, int64_t m, int64_t D, double* GS,

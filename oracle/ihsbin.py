@@ -94,6 +94,38 @@ def make_plan(lmin: float, lmax: float, rho1: Sequence[float], rho2: Sequence[fl
     return Plan(lmin, lmax, L, edges, lam0, tau, kk)
 
 
+def theorem4_k(rho1: float, rho2: float, lo: float, hi: float, eps: float) -> int:
+    """Theorem 4: the error contracts by (kt-1)/(kt+1) per step, kt = rho1 hi / (rho2 lo);
+    the smallest k with ((kt-1)/(kt+1))^k <= eps (capped at 20000)."""
+    kt = rho1 * hi / (rho2 * lo)
+    rate = (kt - 1.0) / (kt + 1.0)
+    k = math.ceil(math.log(eps) / math.log(rate)) if rate > 0 else 1
+    return int(min(max(k, 1), 20000))
+
+
+def auto_plan(GS: np.ndarray, m: int, lmin: float, lmax: float, eps: float = 1e-7, L: int = 0,
+              rho_cap: float = 0.95) -> Plan:
+    """Parameters from the sketch alone: rho_l = min(d_e/m, rho_cap) with the effective dimension of
+    Section 4.2 estimated from the sketched Hessian, d_e = tr(G_S (G_S + lam0 I)^-1)
+    = D - lam0 tr((G_S + lam0 I)^-1) (||D||_2 taken as 1); rho1/rho2 by the Gaussian-sketch theorem;
+    tau by Theorem 4 (proof form); k by Theorem 4's rate for relative error eps."""
+    if L <= 0:
+        L = num_intervals(lmin, lmax)
+    edges = interval_edges(lmin, lmax, L)
+    lam0 = np.sqrt(edges[:-1] * edges[1:])
+    D = GS.shape[0]
+    r1, r2, ks = [], [], []
+    for l in range(L):
+        Pinv = np.linalg.inv(GS + lam0[l] * np.eye(D))
+        de = max(1.0, D - lam0[l] * np.trace(Pinv))
+        rho = min(de / m, rho_cap)
+        a, b = rho_gaussian(rho)
+        r1.append(a)
+        r2.append(b)
+        ks.append(theorem4_k(a, b, edges[l], edges[l + 1], eps))
+    return make_plan(lmin, lmax, r1, r2, ks, L=L)
+
+
 def interval_of(lam: float, plan: Plan) -> int:
     """Half-open [lambda^(l), lambda^(l+1)), last interval closed."""
     l = int(np.searchsorted(plan.edges, lam, side="right")) - 1

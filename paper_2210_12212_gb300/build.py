@@ -12,9 +12,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libihsbin.so")
-SOURCES = ["api.cu", "kernels.cu", "sparse.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels.cu", "sparse.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+         "--default-stream", "per-thread",
          "-Xcompiler", "-fvisibility=hidden"]
 
 
@@ -28,6 +29,7 @@ def _stale(obj, src):
         return True
     deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     deps.append(os.path.join(HERE, "..", "include", "ihsbin.h"))
+    deps.append(os.path.abspath(__file__))        # flags changed -> rebuild
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

@@ -32,7 +32,7 @@ size_t elem_size(int dt) { return dt == IHSBIN_F64 ? 8 : dt == IHSBIN_F32 ? 4 : 
 void free_list(ihsbin_problem* p, std::vector<DevBuf>& v) {
   std::lock_guard<std::mutex> g(p->ctx->mu);
   for (auto& b : v) {
-    cudaFree(b.p);
+    cudaFreeAsync(b.p, ihsbin::g_call_stream);
     p->ctx->in_use -= b.bytes;
   }
   v.clear();
@@ -69,6 +69,33 @@ ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where
 
 namespace ihsbin {
 
+thread_local cudaStream_t g_call_stream = cudaStreamPerThread;
+
+// tau from Theorem 4's proof; rho from the sketch when asked; k from Theorem 4's rate when asked.
+void finalize_plan(ihsbin_problem* p, const double* trP) {
+  Plan& pl = p->plan;
+  const double D = (double)p->A.D, m = (double)p->sk.m;
+  for (int l = 0; l < pl.L; ++l) {
+    const double lo = pl.edges[l], hi = pl.edges[l + 1];
+    if (pl.auto_rho && trP) {
+      const double de = std::max(1.0, D - pl.lam0[l] * trP[l]);
+      const double r = std::min(de / m, 0.95);
+      pl.rho1[l] = (1.0 + std::sqrt(r)) * (1.0 + std::sqrt(r));
+      pl.rho2[l] = (1.0 - std::sqrt(r)) * (1.0 - std::sqrt(r));
+    }
+    pl.tau[l] = 2.0 * pl.lam0[l] / (lo / pl.rho1[l] + hi / pl.rho2[l]);
+    if (pl.auto_k) {
+      const double kt = pl.rho1[l] * hi / (pl.rho2[l] * lo);
+      const double rate = (kt - 1.0) / (kt + 1.0);
+      double k = rate > 0 ? std::ceil(std::log(pl.eps) / std::log(rate)) : 1.0;
+      pl.k[l] = (int32_t)std::min(std::max(k, 1.0), 20000.0);
+    }
+    pl.jcount[l] = pl.jmax > 0 ? std::min(pl.k[l], pl.jmax) : pl.k[l];
+  }
+  pl.jc = *std::max_element(pl.jcount.begin(), pl.jcount.end());
+  pl.kmax = *std::max_element(pl.k.begin(), pl.k.end());
+}
+
 void set_last_error(const char* msg) { g_err = msg; }
 
 cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
@@ -82,7 +109,7 @@ cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
     }
     p->ctx->in_use += bytes;
   }
-  cudaError_t e = cudaMalloc(out, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(out, bytes, p->ctx->pool, g_call_stream);
   if (e != cudaSuccess) {
     std::lock_guard<std::mutex> g(p->ctx->mu);
     p->ctx->in_use -= bytes;
@@ -167,6 +194,16 @@ ihsbin_status ihsbin_ctx_create(int device, uint64_t budget, ihsbin_ctx** out) {
   if (!c) return fail(IHSBIN_ERR_OUT_OF_MEMORY, "ctx_create: host allocation failed");
   c->device = device;
   c->budget = budget;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if ((e = cudaMemPoolCreate(&c->pool, &props)) != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "ctx_create: memory pool");
+  }
+  uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for the next request
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   *out = c;
   return IHSBIN_OK;
 }
@@ -174,6 +211,9 @@ ihsbin_status ihsbin_ctx_create(int device, uint64_t budget, ihsbin_ctx** out) {
 ihsbin_status ihsbin_ctx_destroy(ihsbin_ctx* c) {
   if (!c) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_destroy: NULL");
   if (c->in_use) return fail(IHSBIN_ERR_STATE, "ctx_destroy: problems still hold device memory");
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(cudaStreamPerThread);
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
   return IHSBIN_OK;
 }
@@ -201,6 +241,7 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
   }
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "problem_create");
+  CallStream cs(nullptr);
   ihsbin_problem* p = new (std::nothrow) ihsbin_problem();
   if (!p) return fail(IHSBIN_ERR_OUT_OF_MEMORY, "problem_create: host allocation failed");
   p->ctx = ctx;
@@ -282,7 +323,7 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
       T.rp = trp; T.ci = tci; T.val = tval;
       T.rpT = rp; T.ciT = ci; T.valT = val;
     }
-    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "problem_create (CSR transpose)");
+    if ((e = cudaStreamSynchronize(cudaStreamPerThread)) != cudaSuccess) return bail(e, "problem_create (CSR transpose)");
   }
   // B -> device FP64, packed n x K
   if ((e = prob_alloc(p, (size_t)A->n * K * 8, (void**)&p->B, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
@@ -300,7 +341,7 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
     (void)bes;
   }
   if (e != cudaSuccess) return bail(e, "problem_create");
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e, "problem_create");
+  if ((e = cudaStreamSynchronize(cudaStreamPerThread)) != cudaSuccess) return bail(e, "problem_create");
   *out = p;
   return IHSBIN_OK;
 }
@@ -308,7 +349,7 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
 ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "problem_destroy: NULL");
   cudaSetDevice(p->ctx->device);
-  cudaDeviceSynchronize();
+  CallStream cs(nullptr);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
   prob_free_basis(p);
@@ -319,7 +360,7 @@ ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
 
 ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream) {
   if (!p || !sk) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: NULL argument");
-  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   const int64_t N = p->A.N, D = p->A.D;
   if (sk->m <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: m must be positive");
   int64_t Np = 1;
@@ -336,6 +377,7 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
   }
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "sketch");
+  CallStream cs(st);
   // discard any previous sketch and basis
   prob_free_basis(p);
   p->sketched = false;
@@ -443,6 +485,11 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.jcount.resize(L);
   double rho = d->rho;
   if (!(rho > 0)) rho = std::min((double)p->A.D / (double)p->sk.m, 0.81);
+  pl.auto_rho = d->auto_rho != 0 && !(d->rho1 && d->rho2);
+  pl.auto_k = !d->k && d->k_default <= 0;
+  pl.eps = d->eps > 0 ? d->eps : 1e-7;
+  pl.rho1.resize(L);
+  pl.rho2.resize(L);
   for (int l = 0; l < L; ++l) {
     const double lo = pl.edges[l], hi = pl.edges[l + 1];
     pl.lam0[l] = std::sqrt(lo * hi);
@@ -455,24 +502,24 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
       r2 = (1.0 - std::sqrt(rho)) * (1.0 - std::sqrt(rho));
     }
     if (!(r1 > 0) || !(r2 > 0)) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: rho1 and rho2 must be positive");
-    pl.tau[l] = 2.0 * pl.lam0[l] / (lo / r1 + hi / r2);
+    pl.rho1[l] = r1;
+    pl.rho2[l] = r2;
     const int kl = d->k ? d->k[l] : d->k_default;
-    if (kl <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: every k_l must be >= 1");
-    pl.k[l] = kl;
-    pl.jcount[l] = d->jmax > 0 ? std::min(kl, d->jmax) : kl;
+    if (!pl.auto_k && kl <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: every k_l must be >= 1");
+    pl.k[l] = pl.auto_k ? 1 : kl;
   }
   pl.jmax = d->jmax;
-  pl.jc = *std::max_element(pl.jcount.begin(), pl.jcount.end());
-  pl.kmax = *std::max_element(pl.k.begin(), pl.k.end());
   pl.compute = d->compute;
   pl.product = d->product == IHSBIN_PRODUCT_AUTO ? IHSBIN_PRODUCT_GRAM : d->product;
   if (p->A.layout == IHSBIN_CSR && pl.product != IHSBIN_PRODUCT_GRAM)
     return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: CSR data uses the Gram product");
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "build_basis");
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  CallStream cs(st);
   prob_free_basis(p);
   p->plan = pl;
-  cudaStream_t st = (cudaStream_t)stream;
+  if (!pl.auto_rho) finalize_plan(p, nullptr);
   cudaEvent_t ev[5];
   for (auto& x : ev) cudaEventCreate(&x);
   ihsbin_status s;
@@ -560,7 +607,8 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
       return fail(IHSBIN_ERR_LAMBDA_RANGE, "eval_path: lambda outside [lambda_min, lambda_max]");
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "eval_path");
-  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  CallStream cs(st);
   ScratchScope scratch(p);
   double* lam_dev = nullptr;
   if ((e = prob_alloc(p, T * 8, (void**)&lam_dev, SCOPE_SCRATCH)) != cudaSuccess) return cuda_fail(e, "eval_path");

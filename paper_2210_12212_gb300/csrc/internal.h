@@ -15,6 +15,7 @@ struct ihsbin_ctx {
   uint64_t budget = 0;
   uint64_t in_use = 0;
   std::mutex mu;
+  cudaMemPool_t pool = nullptr;  // stream-ordered pool that keeps freed memory for reuse
 };
 
 namespace ihsbin {
@@ -46,6 +47,10 @@ struct Plan {
   int kmax = 0;
   int compute = IHSBIN_COMPUTE_F64;
   int product = IHSBIN_PRODUCT_GRAM;
+  // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
+  bool auto_rho = false, auto_k = false;
+  double eps = 1e-7;
+  std::vector<double> rho1, rho2;
 };
 
 struct DevBuf {
@@ -104,6 +109,14 @@ namespace ihsbin {
 // Text returned by ihsbin_last_error() on this thread (api.cu).
 void set_last_error(const char* msg);
 
+// Stream that the current ABI call allocates and frees on (stream-ordered pool allocations).
+extern thread_local cudaStream_t g_call_stream;
+struct CallStream {
+  cudaStream_t saved;
+  explicit CallStream(cudaStream_t s) : saved(g_call_stream) { g_call_stream = s ? s : cudaStreamPerThread; }
+  ~CallStream() { g_call_stream = saved; }
+};
+
 // ----- allocation helpers (api.cu) --------------------------------------------
 // Lifetime of a device allocation: the problem, the current basis, or the current call.
 enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2 };
@@ -139,6 +152,8 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st);
 cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st);
 
 cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev);
+// Completes tau, k, jcount, jc, kmax of p->plan; trP[l] = tr(P_l) when rho comes from the sketch (api.cu).
+void finalize_plan(ihsbin_problem* p, const double* trP);
 
 // CSR data (sparse.cu)
 cudaError_t csr_gram(ihsbin_problem* p, int compute, cudaStream_t st);

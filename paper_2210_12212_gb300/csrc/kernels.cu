@@ -888,6 +888,22 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
                                              EpStoreSym<Mode>{p->Pinv, D, D * D}, st);
 }
 
+// tr(P_l) for every interval (one CTA each), for the effective dimension of the sketch
+template <class Mode>
+__global__ void k_trace(CBuf Pm, int64_t D, double* out) {
+  __shared__ double part[256];
+  const int l = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < D; i += blockDim.x) s += Mode::to_d(Mode::ld(Pm, (int64_t)l * D * D + i * D + i));
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[l] = part[0];
+}
+
 // ============================================================ a3: Gram and rhs
 template <class Mode, int ET>
 static cudaError_t gram_dense(ihsbin_problem* p, cudaStream_t st) {
@@ -1244,6 +1260,19 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
   CK(err);
   CK(factor_and_invert<Mode>(p, H, Wm, dinv, lam0_dev, st));
+  if (pl.auto_rho) {
+    double* tr_dev = nullptr;
+    CK(prob_alloc(p, L * sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH));
+    k_trace<Mode><<<L, 256, 0, st>>>(p->Pinv, D, tr_dev);
+    CK(cudaGetLastError());
+    std::vector<double> trP(L);
+    CK(cudaMemcpyAsync(trP.data(), tr_dev, L * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    finalize_plan(p, trP.data());
+    CK(cudaMemcpyAsync(tau_dev, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.k[a] > pl.k[b]; });
+    CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   CK(cudaEventRecord(ev[1], st));
 
   // a3: Gram (product mode GRAM) and right-hand side

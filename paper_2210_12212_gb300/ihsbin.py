@@ -53,7 +53,17 @@ class PathDesc(C.Structure):
     _fields_ = [("lambda_min", C.c_double), ("lambda_max", C.c_double), ("L", C.c_int32),
                 ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
-                ("compute", C.c_int), ("product", C.c_int)]
+                ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("A", Matrix), ("B", C.c_void_p), ("K", C.c_int64), ("ldb", C.c_int64), ("b_dtype", C.c_int),
+                ("b_on_device", C.c_int), ("sketch", SketchDesc), ("path", PathDesc), ("lambdas", C.c_void_p),
+                ("T", C.c_int64), ("X", C.c_void_p), ("x_dtype", C.c_int), ("x_on_device", C.c_int)]
+
+
+class ServeConfig(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("hbm_budget_bytes", C.c_uint64)]
 
 
 _lib = None
@@ -63,7 +73,8 @@ EXPORTED = [
     "ihsbin_problem_create", "ihsbin_problem_destroy", "ihsbin_sketch", "ihsbin_sketch_export",
     "ihsbin_sketch_matrix_export", "ihsbin_build_basis", "ihsbin_plan_export", "ihsbin_basis_export",
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
-    "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc",
+    "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
+    "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve",
 ]
 KCAT_COUNT = 17
 
@@ -97,6 +108,12 @@ def load(path: Optional[str] = None):
         "ihsbin_reset_stats": [vp],
         "ihsbin_kernel_stats": [vp, i32, vp, vp, vp, vp, vp],
         "ihsbin_sketch_gram_noalloc": [vp, i64, i64, vp, vp],
+        "ihsbin_request_footprint": [C.POINTER(Request), C.POINTER(C.c_uint64)],
+        "ihsbin_serve_create": [vp, C.POINTER(ServeConfig), C.POINTER(vp)],
+        "ihsbin_serve_submit": [vp, C.POINTER(Request), C.POINTER(C.c_uint64)],
+        "ihsbin_serve_wait": [vp, C.c_uint64, i64, C.POINTER(C.c_int), vp],
+        "ihsbin_serve_destroy": [vp],
+        "ihsbin_serve": [vp, C.POINTER(ServeConfig), vp, i64, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -200,7 +217,8 @@ class Problem:
                     k: Optional[Sequence[int]] = None, k_default: int = 20,
                     rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
-                    stream=None):
+                    eps: float = 0.0, auto_rho: bool = False, stream=None):
+        """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch."""
         pd = PathDesc()
         pd.lambda_min, pd.lambda_max, pd.L = lambda_min, lambda_max, L
         ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
@@ -211,6 +229,7 @@ class Problem:
         pd.rho1, pd.rho2 = _ptr(r1), _ptr(r2)
         pd.rho, pd.jmax = rho, jmax
         pd.compute, pd.product = COMPUTE[compute], PRODUCT[product]
+        pd.eps, pd.auto_rho = eps, int(auto_rho)
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def eval_path(self, lambdas, out=None, x_dtype: str = "f64", stream=None):
@@ -291,3 +310,93 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------- serving
+def _matrix(A=None, *, dtype="f32", csr=None, shape=None, keep=None):
+    m = Matrix()
+    if csr is not None:
+        rp, ci, val = csr
+        n, d = shape
+        m.n, m.d, m.layout, m.dtype = n, d, CSR, DTYPE[dtype]
+        m.values, m.row_ptr, m.col_idx, m.nnz = _ptr(val), _ptr(rp), _ptr(ci), int(len(ci))
+        m.on_device = _on_device(val)
+        keep += [rp, ci, val]
+    else:
+        n, d = A.shape
+        m.n, m.d, m.layout, m.dtype = n, d, DENSE, DTYPE[dtype]
+        m.values = _ptr(A)
+        m.ld = A.stride(0) if hasattr(A, "stride") and callable(A.stride) else A.strides[0] // A.itemsize
+        m.on_device = _on_device(A)
+        keep.append(A)
+    return m
+
+
+def make_request(A=None, B=None, lambdas=None, *, dtype="f32", csr=None, shape=None, sketch="srht", m=None,
+                 s=1, seed=0, lambda_min=None, lambda_max=None, L=0, k=None, k_default=0, eps=1e-7,
+                 auto_rho=True, jmax=32, compute="f32x2", out=None, x_dtype="f64"):
+    """Build an ihsbin_request (returns (request, keep-alive list, output array))."""
+    keep = []
+    req = Request()
+    req.A = _matrix(A, dtype=dtype, csr=csr, shape=shape, keep=keep)
+    n, d = req.A.n, req.A.d
+    if B.ndim == 1:
+        B = B.reshape(-1, 1)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    keep.append(B)
+    req.B, req.K, req.ldb, req.b_dtype, req.b_on_device = _ptr(B), B.shape[1], B.shape[1], F64, 0
+    req.sketch = SketchDesc(SKETCH_KIND[sketch], m if m else 2 * min(n, d), s, seed)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+    keep.append(lam)
+    pd = PathDesc()
+    pd.lambda_min = lambda_min if lambda_min is not None else float(lam.min())
+    pd.lambda_max = lambda_max if lambda_max is not None else float(lam.max())
+    pd.L = L
+    ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
+    keep.append(ka)
+    pd.k, pd.k_default = _ptr(ka), k_default
+    pd.jmax, pd.compute, pd.product, pd.eps, pd.auto_rho = jmax, COMPUTE[compute], PRODUCT_AUTO, eps, int(auto_rho)
+    req.path = pd
+    req.lambdas, req.T = _ptr(lam), lam.shape[0]
+    if out is None:
+        out = np.zeros((lam.shape[0], d, B.shape[1]), dtype=np.float64 if x_dtype == "f64" else np.float32)
+    keep.append(out)
+    req.X, req.x_dtype, req.x_on_device = _ptr(out), DTYPE[x_dtype], _on_device(out)
+    return req, keep, out
+
+
+def request_footprint(req) -> int:
+    v = C.c_uint64()
+    _check(_lib.ihsbin_request_footprint(C.byref(req), C.byref(v)))
+    return v.value
+
+
+class Server:
+    """ihsbin_serve_create / _submit / _wait / _destroy."""
+
+    def __init__(self, ctx: Context, slots: int = 4, hbm_budget_bytes: int = 0):
+        load()
+        cfg = ServeConfig(slots, hbm_budget_bytes)
+        h = C.c_void_p()
+        _check(_lib.ihsbin_serve_create(ctx.h, C.byref(cfg), C.byref(h)))
+        self.h = h
+        self._keep = {}
+
+    def submit(self, req, keep) -> int:
+        t = C.c_uint64()
+        _check(_lib.ihsbin_serve_submit(self.h, C.byref(req), C.byref(t)))
+        self._keep[t.value] = (req, keep)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = 60_000_000):
+        """(request status, [queue_s, service_s, total_s, device_s]); raises IhsbinError(ERR_TIMEOUT)."""
+        res = C.c_int()
+        t4 = np.zeros(4)
+        _check(_lib.ihsbin_serve_wait(self.h, ticket, timeout_us, C.byref(res), _ptr(t4)))
+        self._keep.pop(ticket, None)
+        return res.value, t4
+
+    def close(self):
+        if getattr(self, "h", None):
+            _check(_lib.ihsbin_serve_destroy(self.h))
+            self.h = None

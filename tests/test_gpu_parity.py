@@ -221,3 +221,24 @@ def test_csr_countsketch_draws_bit_exact(ctx):
     SAo = osk.apply_countsketch(oracle_A(prob), prob.m, prob.s, 77)
     np.testing.assert_allclose(SA, SAo, rtol=0, atol=1e-12 * np.abs(SAo).max())
     gp.close()
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32x2"])
+def test_auto_parameters_match_oracle(ctx, compute):
+    # rho from the sketch's effective dimension, k from Theorem 4: both sides derive them independently
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small("c2_small")
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, k=None, k_default=0, eps=1e-6, auto_rho=True,
+                   compute=compute, jmax=40)
+    Xg = gp.eval_path(prob.lambdas)
+    SA = osk.apply_srht(oracle_A(prob), prob.m, prob.sketch_seed)
+    plan = ob.auto_plan(SA.T @ SA, prob.m, prob.lambda_min, prob.lambda_max, eps=1e-6)
+    got = gp.plan()
+    np.testing.assert_allclose(got["tau"], plan.tau, rtol=1e-9)
+    assert np.abs(got["k"] - plan.k).max() <= 1
+    res = ob.ihs_bin_path(oracle_A(prob), prob.B, prob.sketch, prob.m, prob.s, prob.sketch_seed, plan,
+                          prob.lambdas)
+    assert rel_err_max(Xg, res.X) <= TOL[compute]
+    gp.close()

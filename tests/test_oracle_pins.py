@@ -329,3 +329,25 @@ def test_theorem4_contraction_bound_holds_with_exact_rhos():
         if m == 14:
             tau_printed = 2 * math.sqrt(1 / (r1 * r2)) / (math.sqrt(kt) + 1 / math.sqrt(kt))
             assert worst_ratio(GS, tau_printed) > 1.0 > bound
+
+
+def test_theorem4_k_meets_its_rate():
+    # the chosen k is the first with rate^k <= eps
+    lo, hi, r1, r2, eps = 1.0, 1.6, 2.0, 0.3, 1e-7
+    k = ob.theorem4_k(r1, r2, lo, hi, eps)
+    kt = r1 * hi / (r2 * lo)
+    rate = (kt - 1) / (kt + 1)
+    assert rate ** k <= eps < rate ** (k - 1)
+
+
+def test_auto_plan_effective_dimension_limits():
+    # d_e from the sketch tends to rank(G_S) as lam0 -> 0 and to 0 as lam0 -> inf
+    rng = np.random.default_rng(2)
+    SA = rng.standard_normal((6, 9))
+    GS = SA.T @ SA
+    p_small = ob.auto_plan(GS, 100, 1e-9, 2e-9, L=1)
+    p_large = ob.auto_plan(GS, 100, 1e9, 2e9, L=1)
+    de_small = 9 - p_small.lam0[0] * np.trace(np.linalg.inv(GS + p_small.lam0[0] * np.eye(9)))
+    de_large = 9 - p_large.lam0[0] * np.trace(np.linalg.inv(GS + p_large.lam0[0] * np.eye(9)))
+    assert abs(de_small - 6) < 1e-6 and de_large < 1e-6
+    assert p_small.k[0] > p_large.k[0] >= 1
