@@ -39,6 +39,9 @@ WORKLOADS = {
           "T=200 lambdas log-spaced in [1e-6,1]*||A||_2^2, L=27",
     "c1": "dense FP64 A 2000x100, columns (1+j)^-0.8, Gaussian sketch m=200, T=50 lambdas in "
           "[1e-4,1e2]*||A||_2^2, L=27",
+    "c5": "serving: Poisson arrivals 2000/s, n~U[4096,65536], d~U[64,1024], T~U[20,500], 50% dense FP32 "
+          "(columns (1+j)^-0.8, SRHT) / 50% CSR 1% density (CountSketch s=1), m=2d, lambda in "
+          "[1e-3,1e-1]*||A||_F^2/d, parameters from the sketch (Theorem 4, eps=1e-7), jmax=32",
 }
 # FP32 lanes per SM and SM count of GB300; max SM clock 2070 MHz
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9
@@ -57,10 +60,12 @@ def parse():
     ap.add_argument("--impl", default="ihsbin", choices=["ihsbin", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--compute", default="f32x2", choices=["f32x2", "f64"])
-    ap.add_argument("--jmax", type=int, default=32)
+    ap.add_argument("--jmax", type=int, default=20)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--requests", type=int, default=128, help="serving workload (c5): number of requests")
+    ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
     return ap.parse_args()
 
 
@@ -181,8 +186,94 @@ def reference_arm(args, prob, par):
 
 
 # ---------------------------------------------------------------------------- GPU arm
+def serving_arm(args):
+    """Serving workload: the served float-float form (`--slots` concurrent requests) against the plain
+    FP64 GPU method processing the same trace FIFO, one request at a time."""
+    import torch
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    from synthetic import serving_requests
+    from synthetic.configs import _csr_uniform
+    torch.cuda.set_device(0)
+    trace = serving_requests(args.requests)
+    rng = np.random.default_rng(12345)
+    # one device buffer of FP32 data with (1+j)^-0.8 column scales; a dense request uses its
+    # top-left n x d block in place (row stride 1024)
+    big = (rng.standard_normal((65536, 1024), dtype=np.float32)
+           * (1.0 + np.arange(1024, dtype=np.float32)) ** -0.8).astype(np.float32)
+    big_dev = torch.from_numpy(big).cuda()
+    colsq = np.cumsum(np.cumsum(big.astype(np.float64) ** 2, axis=0), axis=1)  # prefix sums for ||A||_F^2
+    reqs = []
+    for r in trace:
+        n, d, T = r["n"], r["d"], r["T"]
+        rr = np.random.default_rng(1000 + r["seed"])
+        b = rr.standard_normal(n)
+        if r["layout"] == "dense":
+            fro2 = colsq[n - 1, d - 1]
+            entry = dict(kind="dense", n=n, d=d, T=T, b=b, fro2=fro2)
+        else:
+            per = max(1, int(round(0.01 * d)))
+            rp, cols, vals = _csr_uniform(rr, n, d, per)
+            entry = dict(kind="csr", n=n, d=d, T=T, b=b, csr=(rp, cols, vals),
+                         fro2=float(np.sum(vals.astype(np.float64) ** 2)))
+        scale = entry["fro2"] / d
+        entry["lambdas"] = np.geomspace(1e-3 * scale, 1e-1 * scale, T)
+        entry["arrival"] = r["arrival_s"]
+        reqs.append(entry)
+    arrivals = np.array([e["arrival"] for e in reqs])
+
+    def build(compute):
+        built = []
+        for e in reqs:
+            kw = dict(m=2 * min(e["n"], e["d"]), seed=7, eps=1e-7, auto_rho=True, jmax=32, compute=compute)
+            if e["kind"] == "dense":
+                A = big_dev[:e["n"], :e["d"]]
+                built.append(ihs.make_request(A, e["b"], e["lambdas"], dtype="f32", sketch="srht", **kw))
+            else:
+                built.append(ihs.make_request(B=e["b"], lambdas=e["lambdas"], dtype="f32", csr=e["csr"],
+                                              shape=(e["n"], e["d"]), sketch="countsketch", s=1, **kw))
+        return built
+
+    ctx = ihs.Context(0)
+
+    def run(compute, slots):
+        built = build(compute)
+        arr = (ihs.Request * len(built))(*[b[0] for b in built])
+        res = np.zeros(len(built), dtype=np.int32)
+        lat = np.zeros(len(built))
+        cfg = ihs.ServeConfig(slots, 120 << 30)
+        t0 = time.perf_counter()
+        ihs._check(ihs._lib.ihsbin_serve(ctx.h, ihs.C.byref(cfg), ihs.C.cast(arr, ihs.C.c_void_p), len(built),
+                                         ihs._ptr(arrivals), ihs._ptr(res), ihs._ptr(lat)))
+        wall = time.perf_counter() - t0
+        outs = [b[2] for b in built]
+        return dict(wall=wall, lat=lat, res=res, outs=outs)
+
+    served = run("f32x2", args.slots)
+    fifo = run("f64", 1)
+    errs = [float(np.max(np.linalg.norm((a - b).reshape(len(a), -1), axis=1)
+                         / np.maximum(np.linalg.norm(b.reshape(len(b), -1), axis=1), 1e-300)))
+            for a, b in zip(served["outs"], fifo["outs"])]
+
+    def summary(r):
+        lat = np.sort(r["lat"])
+        return {"paths_per_s": len(lat) / r["wall"], "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "wall_s": r["wall"],
+                "failed": int(np.sum(r["res"] != 0))}
+    line = {"metric": METRIC, "value": summary(served)["paths_per_s"], "unit": "paths/s", "n_gpus": 1,
+            "steps": args.requests, "warmup": 0, "ms_per_step": 1e3 * served["wall"] / args.requests,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32x2",
+            "data": "synthetic", "config": {"workload": WORKLOADS["c5"], "requests": args.requests,
+                                            "slots": args.slots, "budget_gb": 120},
+            "served_f32x2": summary(served), "fifo_f64": summary(fifo),
+            "max_rel_err_served_vs_fp64": max(errs)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.config == "c5":
+        serving_arm(args)
+        return
     from synthetic import make_problem
     prob = make_problem(args.config, seed=0)
     par = load_params(args.config)

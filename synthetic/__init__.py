@@ -18,4 +18,5 @@ from .configs import (  # noqa: F401
     lambda_grid,
     to_bf16_bits,
     bf16_bits_to_f32,
+    serving_requests,
 )
