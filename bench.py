@@ -185,6 +185,22 @@ def reference_arm(args, prob, par):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------------ multi-rank
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's time (replicas: the job is done when the last rank is)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job rate: units processed by all ranks / the max-over-ranks time."""
+    return world * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def serving_arm(args):
     """Serving workload: the served float-float form (`--slots` concurrent requests) against the plain
@@ -331,11 +347,7 @@ def main():
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    elapsed_ms = e_start.elapsed_time(e_stop)
-    if dist:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(e_start.elapsed_time(e_stop), dist, "cuda")
     lat = sorted(a.elapsed_time(b) for a, b in evs)
     stats = p.kernel_stats()
     p.set_timing(False)
@@ -359,12 +371,8 @@ def main():
             Xh = step(q)
             q.close()
         torch.cuda.synchronize()
-        te = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([te], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        e2e = {"value": world * ke / te, "unit": "paths/s",
+        te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": job_throughput(world, ke, te), "unit": "paths/s",
                "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size() + B_host.nbytes
                                          + prob.lambdas.nbytes),
                "d2h_bytes_per_step": int(Xh.nbytes)}
@@ -397,7 +405,7 @@ def main():
         cpu = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     gpu_launches = int(sum(v[0] for v in stats.values()))
-    value = world * args.steps / (elapsed_ms * 1e-3)
+    value = job_throughput(world, args.steps, elapsed_ms * 1e-3)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,

@@ -150,6 +150,20 @@ struct LdCColB {
   }
 };
 
+// the old columns of every live interval side by side: column c -> (group c / ncol, column c % ncol)
+template <class Mode>
+struct LdUcat {
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf U;
+  int64_t D, gs, ncol;
+  const int* perm;
+  __device__ __forceinline__ T operator()(int, int64_t k, int64_t c) const {
+    const int64_t g = c / ncol, col = c - g * ncol;
+    return Mode::ld(U, (int64_t)perm[g] * gs + col * D + k);
+  }
+};
+
 // ============================================================ epilogues
 template <class Mode>
 struct EpStoreSym {  // symmetric result: write (i, j) and (j, i) into a D x D matrix (group stride gs)
@@ -1130,12 +1144,21 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t mt = (D + 63) / 64;
     int ny = 1;
     if (pl.product == IHSBIN_PRODUCT_GRAM) {
-      GemmShape sh{D, nold, D, 0};
-      sh.ksplit = ny = std::min(pick_split(mt * ((nold + tile_n(nold) - 1) / tile_n(nold)) * live, D, tile_k(nold)),
-                                SPLIT_MAX);
-      KTimer kt(p, K_LOOP_Y, st, 2.0 * D * D * nold * live, (double)D * D * 8 + 16.0 * D * nold * live);
-      CK((launch_gemm_n<Mode>(sh, live, LdCMatA<Mode>{p->G, D, 0, nullptr}, LdCColB<Mode>{Uin, D, gs, perm_dev},
-                              EpPartial<Mode>{Y, D, nold, live}, st)));
+      // every live interval multiplies the same G: one contraction over their concatenated columns
+      const int64_t ncat = nold * live;
+      GemmShape sh{D, ncat, D, 0};
+      KTimer kt(p, K_LOOP_Y, st, 2.0 * D * D * ncat, (double)D * D * 8 + 16.0 * D * ncat);
+      if (ncat > 32) {
+        sh.ksplit = ny = std::min(pick_split(mt * ((ncat + 63) / 64), D, 16), SPLIT_MAX);
+        CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(sh, 1, LdCMatA<Mode>{p->G, D, 0, nullptr},
+                                                LdUcat<Mode>{Uin, D, gs, nold, perm_dev},
+                                                EpPartial<Mode>{Y, D, ncat, 1}, st)));
+      } else {
+        sh.ksplit = ny = std::min(pick_split(mt * ((ncat + tile_n(ncat) - 1) / tile_n(ncat)), D, tile_k(ncat)),
+                                  SPLIT_MAX);
+        CK((launch_gemm_n<Mode>(sh, 1, LdCMatA<Mode>{p->G, D, 0, nullptr}, LdUcat<Mode>{Uin, D, gs, nold, perm_dev},
+                                EpPartial<Mode>{Y, D, ncat, 1}, st)));
+      }
     } else {
       // W = A_hat U (N x nold), then Y = A_hat^T W
       const int64_t N = A.N;
