@@ -39,6 +39,12 @@ WORKLOADS = {
           "T=200 lambdas log-spaced in [1e-6,1]*||A||_2^2, L=27",
     "c1": "dense FP64 A 2000x100, columns (1+j)^-0.8, Gaussian sketch m=200, T=50 lambdas in "
           "[1e-4,1e2]*||A||_2^2, L=27",
+    "c3": "CSR A 1048576x4096, 40 distinct uniform columns/row, N(0,1) FP32 values, b=Ax*+0.1z, SJLT s=8 "
+          "m=8192, T=1000 lambdas in [1e-4,1e-2]*||A||_2^2, L=9",
+    "c3t": "under-determined CSR A 4096x1048576 (transpose of c3), through the dual, SJLT s=8 m=8192, "
+           "T=1000 lambdas in [1e-4,1e-2]*||A||_2^2, L=9",
+    "c4": "dense BF16 A 262144x2048, columns (1+j)^-1, B 262144x64 from a planted X* + 1% noise, Gaussian "
+          "sketch m=4096 with BF16 entries, T=500 lambdas in [1e-4,1e-2]*||A||_2^2, L=9",
     "c5": "serving: Poisson arrivals 2000/s, n~U[4096,65536], d~U[64,1024], T~U[20,500], 50% dense FP32 "
           "(columns (1+j)^-0.8, SRHT) / 50% CSR 1% density (CountSketch s=1), m=2d, lambda in "
           "[1e-3,1e-1]*||A||_F^2/d, parameters from the sketch (Theorem 4, eps=1e-7), jmax=32",
@@ -60,7 +66,7 @@ def parse():
     ap.add_argument("--impl", default="ihsbin", choices=["ihsbin", "reference"])
     ap.add_argument("--config", default="c2")
     ap.add_argument("--compute", default="f32x2", choices=["f32x2", "f64"])
-    ap.add_argument("--jmax", type=int, default=20)
+    ap.add_argument("--jmax", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -130,13 +136,14 @@ def oracle_sample(prob, par, reps=1):
     evaluation of its lambdas.  Per-path time = fixed part + per-column time x all basis columns."""
     from oracle import ihsbin as ob
     from oracle import sketch as osk
-    A = prob.dense_f64()
+    A = oracle_matrix(prob)
     plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
     t0 = time.perf_counter()
-    SA = osk.apply(prob.sketch, A, prob.m, prob.s, prob.sketch_seed)
+    Ahat, c, _ = ob.tall_form(A, prob.B)
+    SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
     GS = SA.T @ SA
-    G = A.T @ A
-    c = A.T @ prob.B
+    G = Ahat.T @ Ahat
+    G = np.asarray(G.todense()) if hasattr(G, "todense") else G
     t_fixed = time.perf_counter() - t0
     ks = np.array(par["k"])
     l = int(np.argsort(ks)[len(ks) // 2])          # the median-k interval
@@ -156,6 +163,14 @@ def oracle_sample(prob, par, reps=1):
                 sample=f"FP64 numpy oracle: sketch+Gram+rhs ({t_fixed:.2f}s) and interval {l} "
                        f"(k={int(ks[l])}, {t_int:.2f}s) of the {prob.name} path; per-path time "
                        f"extrapolated by basis columns sum_l k_l(k_l+1)/2", t_fixed=t_fixed, t_interval=t_int)
+
+
+def oracle_matrix(prob):
+    """A as the oracle consumes it: FP64 dense, or scipy CSR for sparse workloads."""
+    if prob.layout == "csr":
+        import scipy.sparse as sp
+        return sp.csr_matrix((prob.val.astype(np.float64), prob.col_idx, prob.row_ptr), shape=(prob.n, prob.d))
+    return prob.dense_f64()
 
 
 def reference_arm(args, prob, par):
@@ -292,7 +307,7 @@ def main():
         return
     from synthetic import make_problem
     prob = make_problem(args.config, seed=0)
-    par = load_params(args.config)
+    par = load_params(args.config[:-1] if args.config == "c3t" else args.config)
     if args.impl == "reference":
         reference_arm(args, prob, par)
         return
@@ -309,18 +324,31 @@ def main():
     from paper_2210_12212_gb300 import ihsbin as ihs
 
     ctx = ihs.Context(local)
-    es = {"f64": np.float64, "f32": np.float32}
-    A_dev = torch.from_numpy(np.ascontiguousarray(prob.A)).cuda()
     B_dev = torch.from_numpy(np.ascontiguousarray(prob.B)).cuda()
     T = len(prob.lambdas)
     X_dev = torch.empty((T, prob.d, prob.K), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
                compute=args.compute)
-    p = ihs.Problem(ctx, A_dev, B_dev, dtype=prob.storage)
+    entries = "bf16" if prob.storage == "bf16" else "f64"
+    if prob.layout == "csr":
+        csr_dev = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda()
+                        for a in (prob.row_ptr, prob.col_idx, prob.val))
+        make_dev = lambda: ihs.Problem(ctx, B=B_dev, dtype=prob.storage, csr=csr_dev, shape=(prob.n, prob.d))
+        make_host = lambda: ihs.Problem(ctx, B=np.ascontiguousarray(prob.B), dtype=prob.storage,
+                                        csr=(prob.row_ptr, prob.col_idx, prob.val), shape=(prob.n, prob.d))
+        host_bytes = prob.row_ptr.nbytes + prob.col_idx.nbytes + prob.val.nbytes
+    else:
+        A_np = np.ascontiguousarray(prob.A)
+        A_dev = torch.from_numpy(A_np.view(np.int16) if prob.storage == "bf16" else A_np).cuda()
+        A_pin = torch.from_numpy(A_np.view(np.int16) if prob.storage == "bf16" else A_np).pin_memory()
+        make_dev = lambda: ihs.Problem(ctx, A_dev, B_dev, dtype=prob.storage)
+        make_host = lambda: ihs.Problem(ctx, A_pin, np.ascontiguousarray(prob.B), dtype=prob.storage)
+        host_bytes = A_pin.numel() * A_pin.element_size()
+    p = make_dev()
 
     def step(pp, out=None):
-        pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, stream=stream)
+        pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, entries=entries, stream=stream)
         pp.build_basis(prob.lambda_min, prob.lambda_max, stream=stream, **bkw)
         return pp.eval_path(prob.lambdas, out=out, stream=stream)
 
@@ -356,10 +384,8 @@ def main():
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
-        A_pin = torch.from_numpy(np.ascontiguousarray(prob.A)).pin_memory()
-        B_host = np.ascontiguousarray(prob.B)
         ke = max(1, min(args.steps, 5))
-        q = ihs.Problem(ctx, A_pin, B_host, dtype=prob.storage)   # warm the host path once
+        q = make_host()   # warm the host path once
         step(q)
         q.close()
         torch.cuda.synchronize()
@@ -367,20 +393,19 @@ def main():
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(ke):
-            q = ihs.Problem(ctx, A_pin, B_host, dtype=prob.storage)
+            q = make_host()
             Xh = step(q)
             q.close()
         torch.cuda.synchronize()
         te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": job_throughput(world, ke, te), "unit": "paths/s",
-               "h2d_bytes_per_step": int(A_pin.numel() * A_pin.element_size() + B_host.nbytes
-                                         + prob.lambdas.nbytes),
+               "h2d_bytes_per_step": int(host_bytes + prob.B.nbytes + prob.lambdas.nbytes),
                "d2h_bytes_per_step": int(Xh.nbytes)}
 
     # ---- parity of the timed result against the FP64 oracle (sampled lambdas, rank 0)
     check = None
     if rank == 0 and not args.no_check:
-        check = parity_sample(prob, par, X_dev.cpu().numpy())
+        check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
@@ -412,7 +437,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
             "config": {"workload": WORKLOADS.get(args.config, args.config), "jmax": args.jmax,
-                       "storage": prob.storage, "l2": "inputs larger than L2 (A is 256 MiB)",
+                       "storage": prob.storage, "l2": ("inputs larger than L2 (A is 256 MiB)" if args.config == "c2"
+                                                       else "see workload"),
                        "params": f"tests/golden/{args.config}_params.json",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
@@ -428,23 +454,27 @@ def main():
         dist.destroy_process_group()
 
 
-def parity_sample(prob, par, X):
+def parity_sample(prob, par, X, tol=1e-6):
     """Max relative error of the GPU path against the oracle's k_l-step IHS (Gram space) at 9 lambdas
     (the endpoints and 7 interior grid points), plus the distance of the oracle to x*(lambda)."""
     from oracle import ihsbin as ob
     from oracle import sketch as osk
-    A = prob.dense_f64()
+    A = oracle_matrix(prob)
     plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
     idx = np.unique(np.linspace(0, len(prob.lambdas) - 1, 9).round().astype(int))
     lams = prob.lambdas[idx]
-    SA = osk.apply(prob.sketch, A, prob.m, prob.s, prob.sketch_seed)
+    Ahat, c, dual = ob.tall_form(A, prob.B)
+    SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
     ref = ob.direct_path(A, prob.B, SA.T @ SA, plan, lams)
     err = [float(np.linalg.norm(X[i] - ref[t]) / np.linalg.norm(ref[t])) for t, i in enumerate(idx)]
-    G = A.T @ A
-    c = A.T @ prob.B
-    conv = [float(np.linalg.norm(ref[t] - np.linalg.solve(G + lam * np.eye(G.shape[0]), c))
-                  / np.linalg.norm(ref[t])) for t, lam in enumerate(lams)]
-    return {"max_rel_err_vs_oracle": max(err), "lambdas_checked": len(idx), "pass": max(err) <= 1e-6,
+    G = Ahat.T @ Ahat
+    G = np.asarray(G.todense()) if hasattr(G, "todense") else G
+    conv = []
+    for t, lam in enumerate(lams):
+        z = np.linalg.solve(G + lam * np.eye(G.shape[0]), c)
+        xs = Ahat @ z if dual else z
+        conv.append(float(np.linalg.norm(ref[t] - xs) / np.linalg.norm(ref[t])))
+    return {"max_rel_err_vs_oracle": max(err), "lambdas_checked": len(idx), "pass": max(err) <= tol,
             "oracle_max_rel_dist_to_exact_ridge": max(conv)}
 
 

@@ -106,6 +106,10 @@ typedef struct {
   int64_t m;     /* sketch rows (m % s == 0 for CountSketch/SJLT)           */
   int32_t s;     /* SJLT sparsity; 1 = CountSketch; ignored for other kinds */
   uint64_t seed; /* Philox4x32-10 key                                       */
+  ihsbin_dtype entries; /* Gaussian only: IHSBIN_F64 (default) keeps the FP64 entries z/sqrt(m);
+                         * IHSBIN_BF16 rounds them (FP64 -> FP32 -> BF16, to nearest even), and with
+                         * FP32/BF16 data every product of the sketch is then exact in FP32 and is
+                         * accumulated in float-float (about 8x the FP64 rate on GB300) */
 } ihsbin_sketch_desc;
 
 /* Interval plan and iteration parameters (Section 4.2, Theorem 4).
@@ -169,8 +173,10 @@ IHSBIN_API ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p);
 
 /* Step a1 of the hot path: S A_hat (m x D) for the sketch of Section 3 and
  * its Gram (S A_hat)^T (S A_hat), where A_hat = A (over-determined) or A^T
- * (under-determined).  Re-sketching an already sketched problem discards the
- * basis. */
+ * (under-determined).  S A_hat is formed in FP64 (exact for the SRHT of FP32
+ * data; FP64 accumulation otherwise); its Gram is accumulated in FP64 for FP64
+ * data and in float-float (about 44 significant bits) for FP32/BF16 data.
+ * Re-sketching an already sketched problem discards the basis. */
 IHSBIN_API ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream);
 
 /* Bit-exact export of the sketch's integer draws, for tests.

@@ -77,13 +77,19 @@ def tune(prob, eps: float = 1e-7, kmax: int = 3000, rho_cap: float = 0.95, bf16_
         lams = np.array(sorted(set(lams)))
         P = ob.precond(GS, lam0[l])
         Xs = np.stack([sla.cho_solve(sla.cho_factor(G + lam * np.eye(D), lower=True), c) for lam in lams])
-        X = np.zeros_like(Xs)
+        K = c.shape[1]
+        # all lambdas of the interval side by side: column block t holds x(lams[t]) (D x K)
+        Xs_cat = np.concatenate(list(Xs), axis=1)
+        C_cat = np.tile(c, (1, len(lams)))
+        lam_cols = np.repeat(lams, K)[None, :]
+        nrm = np.array([np.linalg.norm(Xs[t]) for t in range(len(lams))])
+        X = np.zeros_like(Xs_cat)
         k_need = kmax
         err = np.inf
         for k in range(1, kmax + 1):
-            for t, lam in enumerate(lams):
-                X[t] = X[t] - tau * P.solve(G @ X[t] - c + lam * X[t])
-            err = max(np.linalg.norm(X[t] - Xs[t]) / np.linalg.norm(Xs[t]) for t in range(len(lams)))
+            X = X - tau * P.solve(G @ X - C_cat + lam_cols * X)      # one IHS step for every lambda
+            diff = (X - Xs_cat).reshape(D, len(lams), K)
+            err = float(np.max(np.linalg.norm(diff, axis=(0, 2)) / nrm))
             if err <= eps:
                 k_need = k
                 break

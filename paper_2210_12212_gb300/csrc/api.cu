@@ -363,6 +363,8 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   const int64_t N = p->A.N, D = p->A.D;
   if (sk->m <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: m must be positive");
+  if (sk->entries != IHSBIN_F64 && sk->entries != IHSBIN_BF16)
+    return fail(IHSBIN_ERR_INVALID_ARG, "sketch: entries must be IHSBIN_F64 or IHSBIN_BF16");
   int64_t Np = 1;
   while (Np < N) Np <<= 1;
   if (sk->kind == IHSBIN_SK_COUNTSKETCH) {

@@ -232,6 +232,19 @@ __global__ void k_reduce_sym(CBuf part, int S, int64_t D, CBuf out) {
   Mode::st(out, i * D + j, v);
   Mode::st(out, j * D + i, v);
 }
+// float-float partials of a symmetric D x D result into an FP64 matrix
+__global__ void k_reduce_sym_to_f64(CBuf part, int S, int64_t D, double* out) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D * D) return;
+  int64_t i = e / D, j = e % D;
+  if (i > j) return;
+  dd v = DD::ld(part, j * D + i);
+  for (int s = 1; s < S; ++s) v = dd_add(v, DD::ld(part, ((int64_t)s * D + j) * D + i));
+  const double x = dd_to_double(v);
+  out[i * D + j] = x;
+  out[j * D + i] = x;
+}
+
 // column-major M x N result (one group) from S partials
 template <class Mode>
 __global__ void k_reduce_cols(CBuf part, int S, int64_t M, int64_t N, CBuf out) {
@@ -266,6 +279,29 @@ __global__ void k_gauss_fill(double* S, int64_t m, int64_t N, int64_t j0, int64_
   double z = sqrt(-2.0 * log(u0)) * cospi(2.0 * u1);
   S[e] = z * inv_sqrt_m;
 }
+
+// The same entries rounded to BF16 (FP64 -> FP32 -> BF16, round to nearest even), stored as floats.
+__global__ void k_gauss_fill_bf16(float* S, int64_t m, int64_t N, int64_t j0, int64_t nc, uint64_t seed,
+                                  double inv_sqrt_m) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m * nc) return;
+  int64_t i = e / nc, jj = e % nc;
+  u32x4 w = rng_draw(seed, STREAM_GAUSSIAN, (uint64_t)i * (uint64_t)N + (uint64_t)(j0 + jj));
+  double u0 = ((double)w.x + 0.5) * 2.3283064365386963e-10;
+  double u1 = ((double)w.y + 0.5) * 2.3283064365386963e-10;
+  double z = sqrt(-2.0 * log(u0)) * cospi(2.0 * u1);
+  float f = __double2float_rn(z * inv_sqrt_m);
+  uint32_t b = __float_as_uint(f);
+  b = (b + 0x7FFFu + ((b >> 16) & 1u)) & 0xFFFF0000u;
+  S[e] = __uint_as_float(b);
+}
+struct LdGaussSf {  // float S block (m x nc) as the A operand (exact floats)
+  using T = float;
+  static constexpr bool k_contig = true;
+  const float* S;
+  int64_t nc;
+  __device__ __forceinline__ T operator()(int, int64_t i, int64_t k) const { return S[i * nc + k]; }
+};
 
 template <class Mode>
 struct LdGaussS {  // S block (m x nc, row-major FP64) as the A operand
@@ -316,9 +352,39 @@ static cudaError_t gauss_apply(ihsbin_problem* p, double* Sbuf, int64_t chunk, c
   return cudaSuccess;
 }
 
+// BF16 entries with FP32/BF16 data: exact float x float products accumulated in float-float
+template <int ET>
+static cudaError_t gauss_apply_bf16(ihsbin_problem* p, float* Sbuf, int64_t chunk, cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t m = p->sk.m, N = A.N, D = A.D;
+  const double ism = 1.0 / std::sqrt((double)m);
+  for (int64_t j0 = 0; j0 < N; j0 += chunk) {
+    int64_t nc = std::min(chunk, N - j0);
+    {
+      KTimer kt(p, K_SKETCH_DRAW, st, 0, (double)m * nc * 4);
+      k_gauss_fill_bf16<<<nblocks(m * nc, 256), 256, 0, st>>>(Sbuf, m, N, j0, nc, p->sk.seed, ism);
+    }
+    CK(cudaGetLastError());
+    GemmShape sh{m, D, nc, 0};
+    KTimer kt(p, K_SKETCH_APPLY, st, 2.0 * m * D * nc, (double)nc * D * (ET == ELEM_F32 ? 4 : 2));
+    CK((launch_gemm<DD, 64, 64, 16, 4, 4>(sh, 1, LdGaussSf{Sbuf, nc}, LdRowsB<DD, ET>{A.A, A.ld, j0},
+                                          EpAccumF64{p->SA, D}, st)));
+  }
+  return cudaSuccess;
+}
+
 cudaError_t sketch_gaussian(ihsbin_problem* p, cudaStream_t st) {
   const Tall& A = p->A;
   if (A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  if (p->sk.entries == IHSBIN_BF16 && A.elem != ELEM_F64) {
+    const int64_t m = p->sk.m, N = A.N;
+    int64_t chunk = std::max<int64_t>(16, std::min<int64_t>(N, (int64_t)((256ll << 20) / (4 * m))));
+    float* Sbuf = nullptr;
+    CK(ihsbin::prob_alloc(p, (size_t)m * chunk * sizeof(float), (void**)&Sbuf, SCOPE_SCRATCH));
+    CK(cudaMemsetAsync(p->SA, 0, (size_t)m * A.D * sizeof(double), st));
+    if (A.elem == ELEM_F32) return gauss_apply_bf16<ELEM_F32>(p, Sbuf, chunk, st);
+    return gauss_apply_bf16<ELEM_BF16>(p, Sbuf, chunk, st);
+  }
   const int64_t m = p->sk.m, N = A.N;
   int64_t chunk = std::max<int64_t>(16, std::min<int64_t>(N, (int64_t)((256ll << 20) / (8 * m))));
   double* Sbuf = nullptr;
@@ -632,6 +698,16 @@ cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) {
   if (sh.ksplit == 1)
     return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
                                                EpStoreSymF64{p->GS, D}, st);
+  if (p->A.elem != ELEM_F64) {
+    // float-float: SA split exactly into hi + lo floats, products and sums at ~44 bits
+    cudaError_t err = cudaSuccess;
+    CBuf part = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)sh.ksplit * D * D, SCOPE_SCRATCH, &err);
+    CK(err);
+    CK((launch_gemm<DD, 64, 64, 16, 4, 4>(sh, 1, LdTrans<DD, ELEM_F64>{p->SA, D}, LdRowB<DD, ELEM_F64>{p->SA, D},
+                                          EpPartial<DD>{part, D, D, 1}, st)));
+    k_reduce_sym_to_f64<<<nblocks(D * D, 256), 256, 0, st>>>(part, sh.ksplit, D, p->GS);
+    return cudaGetLastError();
+  }
   CBuf part;
   CK(prob_alloc(p, (size_t)sh.ksplit * D * D * 8, &part.p0, SCOPE_SCRATCH));
   CK((launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},

@@ -46,7 +46,7 @@ class Matrix(C.Structure):
 
 
 class SketchDesc(C.Structure):
-    _fields_ = [("kind", C.c_int), ("m", C.c_int64), ("s", C.c_int32), ("seed", C.c_uint64)]
+    _fields_ = [("kind", C.c_int), ("m", C.c_int64), ("s", C.c_int32), ("seed", C.c_uint64), ("entries", C.c_int)]
 
 
 class PathDesc(C.Structure):
@@ -209,8 +209,8 @@ class Problem:
         self.n, self.d, self.K = n, d, K
 
     # -- hot path -------------------------------------------------------------------------
-    def sketch(self, kind: str, m: int, s: int = 1, seed: int = 0, stream=None):
-        sd = SketchDesc(SKETCH_KIND[kind], m, s, seed)
+    def sketch(self, kind: str, m: int, s: int = 1, seed: int = 0, entries: str = "f64", stream=None):
+        sd = SketchDesc(SKETCH_KIND[kind], m, s, seed, DTYPE[entries])
         _check(_lib.ihsbin_sketch(self.h, C.byref(sd), _stream(stream)))
 
     def build_basis(self, lambda_min: float, lambda_max: float, *, L: int = 0,
@@ -345,7 +345,7 @@ def make_request(A=None, B=None, lambdas=None, *, dtype="f32", csr=None, shape=N
     B = np.ascontiguousarray(B, dtype=np.float64)
     keep.append(B)
     req.B, req.K, req.ldb, req.b_dtype, req.b_on_device = _ptr(B), B.shape[1], B.shape[1], F64, 0
-    req.sketch = SketchDesc(SKETCH_KIND[sketch], m if m else 2 * min(n, d), s, seed)
+    req.sketch = SketchDesc(SKETCH_KIND[sketch], m if m else 2 * min(n, d), s, seed, F64)
     lam = np.ascontiguousarray(lambdas, dtype=np.float64)
     keep.append(lam)
     pd = PathDesc()

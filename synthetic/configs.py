@@ -209,12 +209,26 @@ CONFIGS = {
 }
 
 
+def make_transposed(name: str, seed: int = 0, **overrides) -> Problem:
+    """Under-determined variant of a CSR workload: A_u = A^T (d x n), with its own planted x*_u and
+    b_u = A_u x*_u + 0.1 z; the lambda range keeps the base workload's fractions of ||A||_2^2."""
+    base = make_problem(name, seed=seed, **overrides)
+    t = base.transpose()
+    rng = np.random.default_rng(seed + 31337)
+    x_u = rng.standard_normal((t.d, base.K))
+    mv, _ = _csr_matvec(t.row_ptr, t.col_idx, t.val, t.n, t.d)
+    B = np.stack([mv(x_u[:, r]) for r in range(base.K)], axis=1) + 0.1 * rng.standard_normal((t.n, base.K))
+    return dataclasses.replace(t, name=name + "t", B=B, x_star=x_u)
+
+
 def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
     """Build the named workload deterministically from `seed`.
 
     `overrides` may replace any entry of the config table (n, d, m, T, lrange, ...).
     Set IHSBIN_DATA_CACHE to a directory to cache large generated inputs.
     """
+    if name.endswith("t") and name[:-1] in CONFIGS and CONFIGS[name[:-1]]["kind"] == "csr":
+        return make_transposed(name[:-1], seed=seed, **overrides)
     cfg = dict(CONFIGS[name])
     cfg.update(overrides)
     key = f"{name}_s{seed}_" + "_".join(f"{k}{cfg[k]}" for k in sorted(cfg))

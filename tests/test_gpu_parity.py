@@ -242,3 +242,23 @@ def test_auto_parameters_match_oracle(ctx, compute):
                           prob.lambdas)
     assert rel_err_max(Xg, res.X) <= TOL[compute]
     gp.close()
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32x2"])
+def test_bf16_gaussian_sketch_entries(ctx, compute):
+    # BF16 data with BF16 sketch entries: exact products, float-float accumulation of S A
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small("c4_small")
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch("gaussian", prob.m, 1, 21, entries="bf16")
+    SA, GS = gp.sketch_matrices(prob.m, prob.d)
+    SAo = osk.apply_gaussian(oracle_A(prob), prob.m, 21, bf16_entries=True)
+    np.testing.assert_allclose(SA, SAo, rtol=0, atol=1e-13 * np.abs(SAo).max())
+    L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
+    r1, r2, kk = default_params(prob, L, 16)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute=compute)
+    Xg = gp.eval_path(prob.lambdas)
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L)
+    res = ob.ihs_bin_path(oracle_A(prob), prob.B, "gaussian", prob.m, 1, 21, plan, prob.lambdas, bf16_sketch=True)
+    assert rel_err_max(Xg, res.X) <= TOL[compute]
+    gp.close()
