@@ -110,6 +110,7 @@ struct F64 {
   __device__ __forceinline__ static V from_d(double x) { return x; }
   __device__ __forceinline__ static double to_d(V v) { return v; }
   __device__ __forceinline__ static V renorm(V v) { return v; }
+  __device__ __forceinline__ static V neg_(V v) { return -v; }
   __device__ __forceinline__ static void mac(V& acc, V a, V b) { acc = fma(a, b, acc); }
   __device__ __forceinline__ static void mac(V& acc, float a, float b) {
     acc = fma((double)a, (double)b, acc);
@@ -135,6 +136,7 @@ struct DD {
   __device__ __forceinline__ static V from_d(double x) { return dd_from_double(x); }
   __device__ __forceinline__ static double to_d(V v) { return dd_to_double(v); }
   __device__ __forceinline__ static V renorm(V v) { return dd_renorm(v); }
+  __device__ __forceinline__ static V neg_(V v) { return dd_neg(v); }
   // acc += a * b with both operands float-float: the exact product of the high
   // parts plus the two cross terms, added to the accumulator by TwoSum; the
   // low word is left unnormalised (callers renormalise every few steps).

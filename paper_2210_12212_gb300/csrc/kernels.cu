@@ -843,70 +843,114 @@ struct EpTrailing {  // H[r0+i][r0+j] -= acc on the lower triangle
   }
 };
 
-// W = L^-1 (lower triangular) by block forward substitution; one CTA per
-// (column block cb, interval).  W[rb][cb] = Linv_rb (delta_{rb,cb} I - sum_{kb<rb} L[rb][kb] W[kb][cb]).
+// ---- W = L^-1 by recursive doubling of the inverted diagonal blocks:
+//   inv([A 0; B C]) = [A^-1 0; -C^-1 (B A^-1)  C^-1]
+// Level s (block size s = 32, 64, ...): for every pair of s-blocks starting at r0 = 2 s p, the
+// off-diagonal block W[r0+s:r0+2s, r0:r0+s] = -W_C (L_B W_A).  Groups are (interval, pair).
 template <class Mode>
-__global__ void __launch_bounds__(256) k_trtri(CBuf H, CBuf dinv, CBuf Wm, int64_t D) {
-  using V = typename Mode::V;
-  const int cb = blockIdx.x, l = blockIdx.y;
-  const int64_t nblk = (D + NB - 1) / NB;
-  const int64_t off = (int64_t)l * D * D;
-  __shared__ V Lt[NB][NB + 1];
-  __shared__ V Wt[NB][NB + 1];
-  __shared__ V T[NB][NB + 1];
-  const int tid = threadIdx.x;
-  // zero the strictly-upper blocks of this column block
-  for (int64_t rb = 0; rb < cb; ++rb)
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int64_t i = rb * NB + e / NB, j = (int64_t)cb * NB + e % NB;
-      if (i < D && j < D) Mode::st(Wm, off + i * D + j, Mode::zero());
+__global__ void k_wdiag(CBuf dinv, int64_t D, CBuf Wm) {  // W <- block diagonal of the 32x32 inverses, 0 elsewhere
+  const int l = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= D * D) return;
+  const int64_t i = e / D, j = e % D, nblk = (D + NB - 1) / NB;
+  typename Mode::V v = Mode::zero();
+  if (i / NB == j / NB) v = Mode::ld(dinv, ((int64_t)l * nblk + i / NB) * NB * NB + (i % NB) * NB + (j % NB));
+  Mode::st(Wm, (int64_t)l * D * D + e, v);
+}
+template <class Mode>
+struct LdPairB {  // operand (i, k) = L[r0 + s + i][r0 + k]  (the lower-left block B of the pair)
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf H;
+  int64_t D, s;
+  int npairs;
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    const int64_t l = g / npairs, r0 = 2 * s * (g % npairs);
+    const int64_t r = r0 + s + i;
+    return r < D ? Mode::ld(H, l * D * D + r * D + r0 + k) : Mode::zero();
+  }
+};
+template <class Mode>
+struct LdPairWA {  // operand (k, j) = W[r0 + k][r0 + j]  (the inverted upper-left block)
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  CBuf Wm;
+  int64_t D, s;
+  int npairs;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    const int64_t l = g / npairs, r0 = 2 * s * (g % npairs);
+    const int64_t r = r0 + k, c = r0 + j;
+    return (r < D && c < D) ? Mode::ld(Wm, l * D * D + r * D + c) : Mode::zero();
+  }
+};
+template <class Mode>
+struct EpPairT {  // T[g][i][j] (s x s scratch per group)
+  CBuf Tm;
+  int64_t s;
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
+    Mode::st(Tm, ((int64_t)g * s + i) * s + j, Mode::renorm(a));
+  }
+};
+template <class Mode>
+struct LdPairWC {  // operand (i, k) = W[r0 + s + i][r0 + s + k]  (the inverted lower-right block)
+  using T = typename Mode::V;
+  static constexpr bool k_contig = true;
+  CBuf Wm;
+  int64_t D, s;
+  int npairs;
+  __device__ __forceinline__ T operator()(int g, int64_t i, int64_t k) const {
+    const int64_t l = g / npairs, r0 = 2 * s * (g % npairs);
+    const int64_t r = r0 + s + i, c = r0 + s + k;
+    return (r < D && c < D) ? Mode::ld(Wm, l * D * D + r * D + c) : Mode::zero();
+  }
+};
+template <class Mode>
+struct LdPairT {  // operand (k, j) = T[g][k][j]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  CBuf Tm;
+  int64_t s;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    return Mode::ld(Tm, ((int64_t)g * s + k) * s + j);
+  }
+};
+template <class Mode>
+struct EpPairOff {  // W[r0 + s + i][r0 + j] = -acc
+  CBuf Wm;
+  int64_t D, s;
+  int npairs;
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
+    const int64_t l = g / npairs, r0 = 2 * s * (g % npairs);
+    const int64_t r = r0 + s + i;
+    if (r < D) Mode::st(Wm, l * D * D + r * D + r0 + j, Mode::neg_(Mode::renorm(a)));
+  }
+};
+
+template <class Mode>
+static cudaError_t trtri_doubling(ihsbin_problem* p, CBuf H, CBuf dinv, CBuf Wm, CBuf Tm, int L, cudaStream_t st) {
+  const int64_t D = p->A.D;
+  {
+    KTimer kt(p, K_TRTRI, st, 0, (double)L * D * D * 8);
+    k_wdiag<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(dinv, D, Wm);
+    CK(cudaGetLastError());
+  }
+  for (int64_t s = NB; s < D; s *= 2) {
+    const int npairs = (int)((D + 2 * s - 1) / (2 * s));
+    // pairs whose lower block starts beyond D contribute nothing (loaders return zeros, stores are skipped)
+    const int groups = npairs * L;
+    GemmShape s1{s, s, s, 0};
+    {
+      KTimer kt(p, K_TRTRI, st, 2.0 * groups * s * s * s / 2, (double)groups * s * s * 8 * 3);
+      CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(s1, groups, LdPairB<Mode>{H, D, s, npairs},
+                                              LdPairWA<Mode>{Wm, D, s, npairs}, EpPairT<Mode>{Tm, s}, st)));
     }
-  for (int64_t rb = cb; rb < nblk; ++rb) {
-    // T = delta I - sum_kb L[rb][kb] W[kb][cb]
-    V acc[4];
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + q * 256;
-      int i = e / NB, j = e % NB;
-      acc[q] = (rb == cb && i == j) ? Mode::from_d(1.0) : Mode::zero();
-    }
-    for (int64_t kb = cb; kb < rb; ++kb) {
-      __syncthreads();
-      for (int e = tid; e < NB * NB; e += blockDim.x) {
-        int i = e / NB, j = e % NB;
-        int64_t gi = rb * NB + i, gk = kb * NB + j, gj = (int64_t)cb * NB + i;
-        Lt[i][j] = (gi < D && gk < D) ? Mode::ld(H, off + gi * D + gk) : Mode::zero();
-        int64_t wk = kb * NB + i, wj = (int64_t)cb * NB + j;
-        Wt[i][j] = (wk < D && wj < D) ? Mode::ld(Wm, off + wk * D + wj) : Mode::zero();
-        (void)gj;
-      }
-      __syncthreads();
-      for (int q = 0; q < 4; ++q) {
-        int e = tid + q * 256;
-        int i = e / NB, j = e % NB;
-        V s = Mode::zero();
-        for (int k = 0; k < NB; ++k) Mode::mac(s, Lt[i][k], Wt[k][j]);
-        acc[q] = Mode::sub(acc[q], Mode::renorm(s));
-      }
-    }
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + q * 256;
-      T[e / NB][e % NB] = acc[q];
-    }
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      int i = e / NB, j = e % NB;
-      Lt[i][j] = Mode::ld(dinv, ((int64_t)l * nblk + rb) * NB * NB + i * NB + j);
-    }
-    __syncthreads();
-    for (int q = 0; q < 4; ++q) {
-      int e = tid + q * 256;
-      int i = e / NB, j = e % NB;
-      V s = Mode::zero();
-      for (int k = 0; k < NB; ++k) Mode::mac(s, Lt[i][k], T[k][j]);
-      int64_t gi = rb * NB + i, gj = (int64_t)cb * NB + j;
-      if (gi < D && gj < D) Mode::st(Wm, off + gi * D + gj, Mode::renorm(s));
+    {
+      KTimer kt(p, K_TRTRI, st, 2.0 * groups * s * s * s / 2, (double)groups * s * s * 8 * 3);
+      CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(s1, groups, LdPairWC<Mode>{Wm, D, s, npairs},
+                                              LdPairT<Mode>{Tm, s}, EpPairOff<Mode>{Wm, D, s, npairs}, st)));
     }
   }
+  return cudaSuccess;
 }
 
 template <class Mode>
@@ -966,10 +1010,14 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
     }
   }
   {
-    KTimer kt(p, K_TRTRI, st, (double)L * D * D * D / 3.0, (double)L * D * D * cs);
-    k_trtri<Mode><<<dim3((unsigned)nblk, L), 256, 0, st>>>(H, dinv, Wm, D);
+    cudaError_t err = cudaSuccess;
+    size_t tmax = 1;  // the largest per-level scratch: (pairs x s x s) per interval
+    for (int64_t sz = NB; sz < D; sz *= 2) tmax = std::max(tmax, (size_t)((D + 2 * sz - 1) / (2 * sz)) * sz * sz);
+    CBuf Tm = alloc_cbuf(p, Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2, (size_t)L * tmax,
+                         SCOPE_SCRATCH, &err);
+    CK(err);
+    CK(trtri_doubling<Mode>(p, H, dinv, Wm, Tm, L, st));
   }
-  CK(cudaGetLastError());
   // P_l = W^T W  (W lower triangular: the sum starts at k = max(i, j))
   GemmShape sh{D, D, D, 1};
   sh.kdiag = 1;
