@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--auto", action="store_true",
+                    help="parameters from the sketch (rho from d_e, k from Theorem 4 at --eps) on both sides")
+    ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--requests", type=int, default=128, help="serving workload (c5): number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
     return ap.parse_args()
@@ -137,7 +140,11 @@ def oracle_sample(prob, par, reps=1):
     from oracle import ihsbin as ob
     from oracle import sketch as osk
     A = oracle_matrix(prob)
-    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
+    if "tau" in par:   # the library's own plan (sketch-derived parameters)
+        plan = ob.Plan(prob.lambda_min, prob.lambda_max, par["L"], np.array(par["edges"]), np.array(par["lam0"]),
+                       np.array(par["tau"]), np.array(par["k"]))
+    else:
+        plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
     t0 = time.perf_counter()
     Ahat, c, _ = ob.tall_form(A, prob.B)
     SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
@@ -307,7 +314,7 @@ def main():
         return
     from synthetic import make_problem
     prob = make_problem(args.config, seed=0)
-    par = load_params(args.config[:-1] if args.config == "c3t" else args.config)
+    par = None if args.auto else load_params(args.config[:-1] if args.config == "c3t" else args.config)
     if args.impl == "reference":
         reference_arm(args, prob, par)
         return
@@ -328,8 +335,11 @@ def main():
     T = len(prob.lambdas)
     X_dev = torch.empty((T, prob.d, prob.K), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
-               compute=args.compute)
+    if par is None:
+        bkw = dict(k=None, k_default=0, eps=args.eps, auto_rho=True, jmax=args.jmax, compute=args.compute)
+    else:
+        bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
+                   compute=args.compute)
     entries = "bf16" if prob.storage == "bf16" else "f64"
     if prob.layout == "csr":
         csr_dev = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -405,7 +415,8 @@ def main():
     # ---- parity of the timed result against the FP64 oracle (sampled lambdas, rank 0)
     check = None
     if rank == 0 and not args.no_check:
-        check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6)
+        check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6,
+                              eps=args.eps)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
@@ -426,7 +437,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu and world == 1:
-        info = oracle_sample(prob, par)
+        info = oracle_sample(prob, par if par is not None else p.plan_dict_for_oracle())
         cpu = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     gpu_launches = int(sum(v[0] for v in stats.values()))
@@ -454,18 +465,23 @@ def main():
         dist.destroy_process_group()
 
 
-def parity_sample(prob, par, X, tol=1e-6):
+def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
     """Max relative error of the GPU path against the oracle's k_l-step IHS (Gram space) at 9 lambdas
-    (the endpoints and 7 interior grid points), plus the distance of the oracle to x*(lambda)."""
+    (the endpoints and 7 interior grid points), plus the distance of the oracle to x*(lambda).
+    With par None the oracle derives its own plan from its sketch (oracle.ihsbin.auto_plan)."""
     from oracle import ihsbin as ob
     from oracle import sketch as osk
     A = oracle_matrix(prob)
-    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
     idx = np.unique(np.linspace(0, len(prob.lambdas) - 1, 9).round().astype(int))
     lams = prob.lambdas[idx]
     Ahat, c, dual = ob.tall_form(A, prob.B)
     SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
-    ref = ob.direct_path(A, prob.B, SA.T @ SA, plan, lams)
+    GS = SA.T @ SA
+    if par is None:
+        plan = ob.auto_plan(GS, prob.m, prob.lambda_min, prob.lambda_max, eps=eps)
+    else:
+        plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
+    ref = ob.direct_path(A, prob.B, GS, plan, lams)
     err = [float(np.linalg.norm(X[i] - ref[t]) / np.linalg.norm(ref[t])) for t, i in enumerate(idx)]
     G = Ahat.T @ Ahat
     G = np.asarray(G.todense()) if hasattr(G, "todense") else G

@@ -270,6 +270,13 @@ class Problem:
                                        L + 1, C.byref(Lv)))
         return dict(L=L, edges=edges, lam0=lam0, tau=tau, k=k, jcount=jc)
 
+    def plan_dict_for_oracle(self):
+        """The library's plan as (L, rho1, rho2, k) arrays, for timing the oracle on the same plan."""
+        p = self.plan()
+        # tau = 2 lam0 / (lo/rho1 + hi/rho2): report rho via the oracle-compatible fields the library used
+        return dict(L=p["L"], k=p["k"].tolist(), tau=p["tau"].tolist(), lam0=p["lam0"].tolist(),
+                    edges=p["edges"].tolist())
+
     def basis(self, l: int, D: int):
         need = C.c_int64()
         _check(_lib.ihsbin_basis_export(self.h, l, None, 0, C.byref(need)))
