@@ -133,6 +133,18 @@ typedef struct {
  *  eps      with k == NULL and k_default <= 0, k_l is Theorem 4's iteration
  *           count for relative error eps: ceil(ln eps / ln((kt-1)/(kt+1))) with
  *           kt = rho1 hi_l / (rho2 lo_l) (eps <= 0 selects 1e-7). */
+/* Kernel for the Gram A_hat^T A_hat of the Gram product mode.
+ *  AUTO   : SLICES for dense FP32/BF16 data, FMA otherwise.
+ *  SLICES : dense FP32/BF16 data only.  Every column is scaled by a power of two
+ *           and cut into 6 integer slices exact in BF16; the slice products run
+ *           on the tensor cores (tcgen05, FP32 accumulation of integer products,
+ *           exact in chunks of 512 rows, drained into int32), and the pairs are
+ *           combined in FP64.  The result matches the exact Gram to about FP64
+ *           rounding (entries within 2^-17 of their column's largest magnitude
+ *           are represented exactly; smaller ones to 2^-41 of that maximum).
+ *  FMA    : CUDA-core contraction in FP64 (F64 compute) or float-float (F32X2). */
+typedef enum { IHSBIN_GRAM_AUTO = 0, IHSBIN_GRAM_SLICES = 1, IHSBIN_GRAM_FMA = 2 } ihsbin_gram;
+
 typedef struct {
   double lambda_min, lambda_max;
   int32_t L;
@@ -146,6 +158,7 @@ typedef struct {
   ihsbin_product product;
   double eps;
   int32_t auto_rho;
+  ihsbin_gram gram;
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -200,6 +213,12 @@ IHSBIN_API ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* 
  * The bases stay resident on the device until the problem is destroyed. */
 IHSBIN_API ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* desc, void* stream);
 
+/* Copy the Gram G = A_hat^T A_hat (D x D, row-major) built by the last
+ * ihsbin_build_basis in the Gram product mode to a host FP64 array, for tests.
+ * Fails with IHSBIN_ERR_STATE when there is no basis or the product mode was
+ * A-space (no Gram is formed). */
+IHSBIN_API ihsbin_status ihsbin_gram_export(ihsbin_problem* p, double* G);
+
 /* The plan the library derived from the descriptor: arrays of L (edges: L+1),
  * any may be NULL; *L_out receives L.  Fails with INVALID_ARG if cap_L < L. */
 IHSBIN_API ihsbin_status ihsbin_plan_export(ihsbin_problem* p, double* edges, double* lam0, double* tau,
@@ -231,7 +250,7 @@ IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
  * is also bracketed by CUDA events on the stream it runs on and its device
  * time is added at the call's synchronisation point.  Categories 0 ..
  * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 17
+#define IHSBIN_KCAT_COUNT 20
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,

@@ -139,6 +139,23 @@ def gram_operator(Ahat) -> Callable[[np.ndarray], np.ndarray]:
     return lambda V: G @ V
 
 
+def gram_extended(Ahat) -> np.ndarray:
+    """G = A^T A (the Hessian of the least-squares term, Section 2) with every sum
+    accumulated in numpy's extended precision (longdouble: a 64-bit significand on
+    x86-64, 113 bits on AArch64) and rounded once to FP64.  For data stored in
+    FP32/BF16 every product is exact there, so the result is the exact Gram up to
+    the final rounding and the extended accumulation; it checks Gram kernels whose
+    error is below that of an FP64 GEMM."""
+    A = np.asarray(Ahat.todense() if hasattr(Ahat, "todense") else Ahat, dtype=np.longdouble)
+    return (A.T @ A).astype(np.float64)
+
+
+def gram_entries_extended(Ahat, rows, cols) -> np.ndarray:
+    """Entries G[rows[q], cols[q]] of A^T A, accumulated as in gram_extended."""
+    A = np.asarray(Ahat, dtype=np.longdouble)
+    return (A[:, rows] * A[:, cols]).sum(axis=0).astype(np.float64)
+
+
 def aspace_operator(Ahat) -> Callable[[np.ndarray], np.ndarray]:
     """v -> A^T (A v), the two products of Algorithm 2 line 'tau A^T A u_j'."""
     return lambda V: Ahat.T @ (Ahat @ V)

@@ -60,6 +60,8 @@ ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where
     cudaMemset(p->status, 0, sizeof(int));
     if (s == DEV_NOT_SPD) return fail(IHSBIN_ERR_NOT_SPD, std::string(where) + ": non-positive pivot in a factor of (SA)^T SA + lam0 I");
     if (s == DEV_NAN) return fail(IHSBIN_ERR_NAN, std::string(where) + ": non-finite value on the device");
+    if (s == DEV_TIMEOUT)
+      return fail(IHSBIN_ERR_TIMEOUT, std::string(where) + ": a tensor-core pipeline wait expired (the kernel gave up)");
     return fail(IHSBIN_ERR_CUDA, std::string(where) + ": device status " + std::to_string(s));
   }
   return IHSBIN_OK;
@@ -515,6 +517,16 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.product = d->product == IHSBIN_PRODUCT_AUTO ? IHSBIN_PRODUCT_GRAM : d->product;
   if (p->A.layout == IHSBIN_CSR && pl.product != IHSBIN_PRODUCT_GRAM)
     return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: CSR data uses the Gram product");
+  if (d->gram != IHSBIN_GRAM_AUTO && d->gram != IHSBIN_GRAM_SLICES && d->gram != IHSBIN_GRAM_FMA)
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown Gram kernel");
+  {
+    const bool sliceable = p->A.layout == IHSBIN_DENSE_ROWMAJOR && p->A.elem != ELEM_F64;
+    if (d->gram == IHSBIN_GRAM_SLICES && !sliceable)
+      return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: the sliced tensor-core Gram takes dense FP32/BF16 data");
+    pl.gram = d->gram == IHSBIN_GRAM_FMA ? IHSBIN_GRAM_FMA
+              : d->gram == IHSBIN_GRAM_SLICES ? IHSBIN_GRAM_SLICES
+              : (sliceable ? IHSBIN_GRAM_SLICES : IHSBIN_GRAM_FMA);
+  }
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "build_basis");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
@@ -597,6 +609,24 @@ ihsbin_status ihsbin_basis_export(ihsbin_problem* p, int32_t l, double* buf, int
   return IHSBIN_OK;
 }
 
+ihsbin_status ihsbin_gram_export(ihsbin_problem* p, double* G) {
+  if (!p || !G) return fail(IHSBIN_ERR_INVALID_ARG, "gram_export: NULL argument");
+  if (!p->built) return fail(IHSBIN_ERR_STATE, "gram_export: no basis");
+  if (p->plan.product != IHSBIN_PRODUCT_GRAM || !p->G.p0) return fail(IHSBIN_ERR_STATE, "gram_export: no Gram (A-space product)");
+  const int64_t cnt = p->A.D * p->A.D;
+  if (p->plan.compute == IHSBIN_COMPUTE_F64) {
+    if (cudaMemcpy(G, p->G.p0, cnt * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "gram_export: copy failed");
+  } else {
+    std::vector<float> hi(cnt), lo(cnt);
+    if (cudaMemcpy(hi.data(), p->G.p0, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(lo.data(), p->G.p1, cnt * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(IHSBIN_ERR_CUDA, "gram_export: copy failed");
+    for (int64_t i = 0; i < cnt; ++i) G[i] = (double)hi[i] + (double)lo[i];
+  }
+  return IHSBIN_OK;
+}
+
 ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t T, void* X, ihsbin_dtype x_dtype,
                                int x_on_device, void* stream) {
   if (!p || !lambdas || !X) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: NULL argument");
@@ -644,7 +674,7 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
 static const char* kcat_names[K_NCAT] = {
     "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
-    "eval_coef", "eval", "sparse"};
+    "eval_coef", "eval", "sparse", "gram_slice", "gram_tc_mma", "gram_combine"};
 
 ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");

@@ -20,7 +20,7 @@ namespace ihsbin {
 // ----------------------------------------------------------------- status word
 // Device kernels never trap: they record the first fault in a status word the
 // host reads at the next synchronisation point.
-enum DevStatus : int { DEV_OK = 0, DEV_NOT_SPD = 4, DEV_NAN = 11, DEV_BOUNDS = 12 };
+enum DevStatus : int { DEV_OK = 0, DEV_NOT_SPD = 4, DEV_NAN = 11, DEV_BOUNDS = 12, DEV_TIMEOUT = 13 };
 
 __device__ __forceinline__ void dev_fail(int* status, int code) {
   if (status) atomicCAS(status, 0, code);

@@ -47,6 +47,7 @@ struct Plan {
   int kmax = 0;
   int compute = IHSBIN_COMPUTE_F64;
   int product = IHSBIN_PRODUCT_GRAM;
+  int gram = IHSBIN_GRAM_FMA;   // resolved Gram kernel (never AUTO)
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
@@ -62,7 +63,7 @@ struct DevBuf {
 enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
-  K_SPARSE, K_NCAT
+  K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -157,6 +158,12 @@ void finalize_plan(ihsbin_problem* p, const double* trP);
 
 // CSR data (sparse.cu)
 cudaError_t csr_gram(ihsbin_problem* p, int compute, cudaStream_t st);
+
+// Dense FP32/BF16 Gram on the tensor cores from exact integer slices (tc_gram.cu)
+constexpr int kGramSlices = 6;     // BF16 slices per entry
+constexpr int kGramMaxWeight = 6;  // slice pairs (s, t) kept: s + t <= kGramMaxWeight
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st);
+uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
 cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,

@@ -1430,6 +1430,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
     CK(err);
     if (csr) CK(csr_gram(p, cm, st));
+    else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, st));
     else CK((gram_dense<Mode, ET>(p, st)));
   }
   if (csr && !p->dual) {

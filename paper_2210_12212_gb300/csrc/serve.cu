@@ -90,6 +90,10 @@ uint64_t request_footprint(const ihsbin_request* q) {
   if (pd.k) for (int l = 0; l < (int)L; ++l) kmax = std::max(kmax, (double)pd.k[l]);
   const double jc = pd.jmax > 0 ? std::min((double)pd.jmax, kmax) : kmax;
   bytes += 3 * L * D * D * 8 + D * D * 8 * 9;
+  // integer slices and tiles of the tensor-core Gram (dense FP32/BF16 data)
+  if (A.layout == IHSBIN_DENSE_ROWMAJOR && A.dtype != IHSBIN_F64 && pd.gram != IHSBIN_GRAM_FMA &&
+      pd.product != IHSBIN_PRODUCT_ASPACE)
+    bytes += (double)gram_slices_scratch_bytes((int64_t)N, (int64_t)D);
   // recursion buffers: U (2), utilde, R, and the split partials of Y and Z (16 each)
   bytes += (4 + 32) * L * jc * K * D * 8;
   if (A.n < A.d) bytes += L * jc * K * N * 8;                   // dual map

@@ -1,0 +1,414 @@
+// Step a3 (the Gram G = A_hat^T A_hat of the Gram product mode) for dense FP32 /
+// BF16 data on the 5th-generation tensor cores, with an exactly rounded-once
+// FP64 result.
+//
+// Method (error-free splitting of the data, as in Ozaki-style exact products):
+//  * each column j is scaled by the power of two 2^(7 - e_j), e_j the exponent of
+//    its largest magnitude, so that every scaled entry v satisfies |v| < 2^7;
+//  * v is cut into `ns` integer slices a_0 + a_1 2^-8 + a_2 2^-16 + ...,
+//    |a_t| <= 128, every one exact in BF16 (8 significant bits);
+//  * G_ij = 2^(e_i + e_j - 14) sum_{s,t} 2^(-8(s+t)) sum_k a_s(k,i) a_t(k,j).
+//    Every product a_s a_t is an integer of magnitude <= 2^14, so a tensor-core
+//    sum of 512 of them (|sum| <= 2^23) is exact in its FP32 accumulator; each
+//    such chunk is drained from Tensor Memory into int32 registers, and a work
+//    item covers at most 65536 rows (|int32 sum| <= 2^30);
+//  * a combine pass adds the integer tiles of all slice pairs in FP64 from the
+//    smallest weight up and applies the power-of-two scales.
+// For FP32 data six slices represent every entry within a factor 2^-17 of its
+// column's maximum exactly (smaller entries to 2^-41 of that maximum), and
+// pairs with s + t <= 6 are kept (the rest weigh below 2^-56 of the leading
+// term), so the result agrees with the exact Gram to about FP64 rounding.
+// Symmetry: the pair (s, t), s < t, is computed for all tile pairs (I, J) and
+// enters G_IJ and G_JI; the pair (s, s) only for I <= J.
+//
+// Tensor-core kernel (one CTA per 128 x 128 output tile, pair and row range):
+//  * slices are written by the slicing kernel directly in the shared-memory
+//    image the MMA reads (K-major 8 x 16-byte core matrices, 128 rows x 64 k
+//    per 16 KiB block), so one pipeline stage is two 16 KiB bulk copies;
+//  * warp 0 (one lane) issues the bulk copies into a 6-stage ring; warp 1
+//    owns the Tensor Memory (256 columns: two 128-column FP32 accumulators)
+//    and one lane issues tcgen05.mma (M = N = 128, K = 16; 4 per stage);
+//  * warps 2..5 drain a finished accumulator (tcgen05.ld) into int32 while the
+//    MMAs of the next chunk run into the other one;
+//  * every wait is bounded in time: a pipeline that cannot progress records
+//    DEV_TIMEOUT in the status word, lets its copies and MMAs land, frees its
+//    Tensor Memory and returns.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace ihsbin {
+namespace {
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e__ = (x);                 \
+    if (e__ != cudaSuccess) return e__;    \
+  } while (0)
+
+constexpr int SL_STAGES = 6;
+constexpr int SL_STAGE_BYTES = 32768;    // A block + B block
+constexpr int SL_BLOCK_ELEMS = 8192;     // 128 rows x 64 k (BF16)
+constexpr int SL_CHUNK = 8;              // K-blocks per exact Tensor Memory chunk (512 k)
+constexpr int SL_KB_MAX = 1024;          // K-blocks per work item (65536 k)
+constexpr int SL_MAX_PAIRS = 36;
+constexpr int SL_NONFINITE = 1 << 20;    // column exponent marking a column holding Inf/NaN
+constexpr int SL_THREADS = 192;
+
+struct SlicePlan {
+  int ns, np, T, RB, KB, nsplit, kbper, D;
+  int8_t ps[SL_MAX_PAIRS], pt[SL_MAX_PAIRS];
+  int base[SL_MAX_PAIRS + 1];  // first work item of each pair; base[np] = item count
+};
+
+__host__ __device__ __forceinline__ int tile_index(bool diag_pair, int T, int I, int J) {
+  return diag_pair ? I * T - I * (I - 1) / 2 + (J - I) : I * T + J;
+}
+
+__device__ __forceinline__ int col_exp(unsigned mbits) {
+  if (mbits >= 0x7f800000u) return SL_NONFINITE;
+  if (mbits == 0u) return 0;
+  int e;
+  frexpf(__uint_as_float(mbits), &e);  // max |a| = f 2^e with f in [0.5, 1)
+  return e;
+}
+
+template <int ET>
+__device__ __forceinline__ float load_f(const void* X, int64_t i) {
+  if (ET == ELEM_F32) return ((const float*)X)[i];
+  return __uint_as_float((uint32_t)((const uint16_t*)X)[i] << 16);
+}
+
+// cmax[j] = bits of max_k |A[k][j]| (Inf bits when the column holds Inf or NaN)
+template <int ET>
+__global__ void k_col_absmax(const void* A, int64_t ld, int64_t N, int64_t D, unsigned* cmax) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= D) return;
+  float m = 0.f;
+  bool bad = false;
+  for (int64_t k = blockIdx.y; k < N; k += gridDim.y) {
+    const float a = fabsf(load_f<ET>(A, k * ld + j));
+    bad |= !(a <= 3.402823466e38f);
+    m = fmaxf(m, a);
+  }
+  atomicMax(&cmax[j], bad ? 0x7f800000u : __float_as_uint(m));
+}
+
+// Thread (j, k8): rows 8 k8 .. 8 k8 + 7 of column j -> one 16-byte run per slice.
+// Block (t, rb, kb) of S holds slice t of columns 128 rb .. +127, rows 64 kb .. +63,
+// element (r, kk) at byte (r/8)*1024 + (kk/8)*128 + (r%8)*16 + (kk%8)*2.
+template <int ET>
+__global__ void k_slice(const void* A, int64_t ld, int64_t N, int64_t D, const unsigned* cmax, int ns, int RB,
+                        int KB, __nv_bfloat16* S) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= (int64_t)RB * 128) return;
+  int e = j < D ? col_exp(cmax[j]) : 0;
+  const bool live = j < D && e != SL_NONFINITE;
+  if (!live) e = 0;
+  const int r = (int)(j & 127), rb = (int)(j >> 7);
+  for (int64_t k8 = blockIdx.y; k8 < (int64_t)KB * 8; k8 += gridDim.y) {
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = k8 * 8 + q;
+      v[q] = (live && k < N) ? ldexpf(load_f<ET>(A, k * ld + j), 7 - e) : 0.f;  // exact, |v| < 2^7
+    }
+    const int64_t kb = k8 >> 3, kc = k8 & 7;
+    const int64_t off = ((r >> 3) * 1024 + kc * 128 + (r & 7) * 16) / 2;
+    for (int t = 0; t < ns; ++t) {
+      __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float a = rintf(v[q]);  // |a| <= 128: exact in BF16
+        h[q] = __float2bfloat16_rn(a);
+        v[q] = (v[q] - a) * 256.f;    // exact: |v - a| <= 1/2
+      }
+      *reinterpret_cast<uint4*>(S + (((int64_t)t * RB + rb) * KB + kb) * SL_BLOCK_ELEMS + off) =
+          *reinterpret_cast<const uint4*>(h);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(SL_THREADS, 1)
+    k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, SlicePlan pl, int* __restrict__ out, int* status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[SL_STAGES], empty[SL_STAGES], tfull[2], tempty[2], drained;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // work item -> pair, tile (I, J), row range
+  const int item = blockIdx.x;
+  int p = 0;
+  while (p + 1 < pl.np && pl.base[p + 1] <= item) ++p;
+  const int s = pl.ps[p], t = pl.pt[p];
+  const int rel = item - pl.base[p], tile = rel / pl.nsplit, q = rel - tile * pl.nsplit;
+  int I, J;
+  if (s == t) {
+    I = 0;
+    int rest = tile;
+    while (rest >= pl.T - I) { rest -= pl.T - I; ++I; }
+    J = I + rest;
+  } else {
+    I = tile / pl.T;
+    J = tile - I * pl.T;
+  }
+  const int kb0 = q * pl.kbper, kb1 = min(pl.KB, kb0 + pl.kbper);
+  const int nkb = kb1 - kb0, nch = (nkb + SL_CHUNK - 1) / SL_CHUNK;
+
+  if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_base), 256);
+  if (tid == 0) {
+    for (int i = 0; i < SL_STAGES; ++i) {
+      tc::bar_init(tc::smem_addr(&full[i]), 1);
+      tc::bar_init(tc::smem_addr(&empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::bar_init(tc::smem_addr(&tfull[i]), 1);
+      tc::bar_init(tc::smem_addr(&tempty[i]), 4);
+    }
+    tc::bar_init(tc::smem_addr(&drained), 1);
+    abort_flag = 0;
+    tc::bar_init_fence();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const __nv_bfloat16* gA = S + (((int64_t)s * pl.RB + I) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  const __nv_bfloat16* gB = S + (((int64_t)t * pl.RB + J) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer: bulk copies into the stage ring
+      int issued = 0;
+      for (int it = 0; it < nkb; ++it) {
+        const int st = it % SL_STAGES, rnd = it / SL_STAGES;
+        if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
+          dev_fail(status, DEV_TIMEOUT);
+          *abort_v = 1;
+          break;
+        }
+        if (*abort_v) break;
+        const uint32_t sa = tc::smem_addr(smem + st * SL_STAGE_BYTES), fb = tc::smem_addr(&full[st]);
+        tc::bar_arrive_tx(fb, SL_STAGE_BYTES);
+        tc::bulk_load(sa, gA + (int64_t)it * SL_BLOCK_ELEMS, SL_STAGE_BYTES / 2, fb);
+        tc::bulk_load(sa + SL_STAGE_BYTES / 2, gB + (int64_t)it * SL_BLOCK_ELEMS, SL_STAGE_BYTES / 2, fb);
+        issued = it + 1;
+      }
+      // the copies of the last stages land before the CTA may leave
+      for (int it = issued > SL_STAGES ? issued - SL_STAGES : 0; it < issued; ++it)
+        tc::bar_wait(tc::smem_addr(&full[it % SL_STAGES]), (it / SL_STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int h = c & 1;
+        if (c >= 2 && !tc::bar_wait(tc::smem_addr(&tempty[h]), ((c >> 1) - 1) & 1)) {
+          dev_fail(status, DEV_TIMEOUT);
+          *abort_v = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(h * 128);
+        const int i0 = c * SL_CHUNK, i1 = min(nkb, i0 + SL_CHUNK);
+        for (int it = i0; it < i1; ++it) {
+          const int st = it % SL_STAGES, rnd = it / SL_STAGES;
+          if (!tc::bar_wait(tc::smem_addr(&full[st]), rnd & 1) || *abort_v) {
+            dev_fail(status, DEV_TIMEOUT);
+            *abort_v = 1;
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_addr(smem + st * SL_STAGE_BYTES);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)  // K = 16 per MMA: two core matrices (256 bytes) along K
+            tc::mma_bf16(d, tc::smem_desc(sa + ks * 256, 128, 1024),
+                         tc::smem_desc(sa + SL_STAGE_BYTES / 2 + ks * 256, 128, 1024), idesc,
+                         (it > i0 || ks > 0) ? 1u : 0u);
+          tc::commit(tc::smem_addr(&empty[st]));
+        }
+        if (ok) tc::commit(tc::smem_addr(&tfull[h]));
+      }
+      tc::commit(tc::smem_addr(&drained));  // every MMA of this CTA has completed
+      tc::bar_wait(tc::smem_addr(&drained), 0);
+    }
+  } else {  // warps 2..5: Tensor Memory lanes 32 (warp % 4) .. +31 are this thread's rows
+    const int qd = warp & 3;
+    int acc[128];
+#pragma unroll
+    for (int c = 0; c < 128; ++c) acc[c] = 0;
+    bool ok = true;
+    for (int c = 0; c < nch; ++c) {
+      const int h = c & 1;
+      if (!tc::bar_wait(tc::smem_addr(&tfull[h]), (c >> 1) & 1) || *abort_v) {
+        if (lane == 0) dev_fail(status, DEV_TIMEOUT);
+        *abort_v = 1;
+        ok = false;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int cc = 0; cc < 128; cc += 32) {
+        uint32_t r[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * 128 + cc), r);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int x = 0; x < 32; ++x) acc[cc + x] += __float2int_rn(__uint_as_float(r[x]));  // integer-valued
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::bar_arrive(tc::smem_addr(&tempty[h]));
+    }
+    if (ok) {  // tile stored column-major: out[item][col][row]
+      int* o = out + (int64_t)item * 16384 + qd * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < 128; ++c) o[c * 128] = acc[c];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, 256);
+}
+
+// G[i][j] = G[j][i] for i <= j from the integer tiles (pairs ordered by weight, largest first)
+template <class Mode>
+__global__ void k_gram_combine(const int* __restrict__ out, SlicePlan pl, const unsigned* __restrict__ cmax, CBuf G) {
+  const int64_t D = pl.D;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D) return;
+  const int I = (int)(i >> 7), ri = (int)(i & 127);
+  const int ei = col_exp(cmax[i]);
+  for (int64_t j = i + blockIdx.y; j < D; j += gridDim.y) {
+    if (j < i) continue;
+    const int J = (int)(j >> 7), rj = (int)(j & 127);
+    const int ej = col_exp(cmax[j]);
+    double g;
+    if (ei == SL_NONFINITE || ej == SL_NONFINITE) {
+      g = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+      double sum = 0.0;
+      int w = pl.ps[0] + pl.pt[0];
+      long long v = 0;
+      for (int p = 0; p < pl.np; ++p) {
+        const int s = pl.ps[p], t = pl.pt[p];
+        if (s + t != w) {
+          sum += ldexp((double)v, -8 * w);
+          v = 0;
+          w = s + t;
+        }
+        const int a = pl.base[p] + tile_index(s == t, pl.T, I, J) * pl.nsplit;
+        for (int q = 0; q < pl.nsplit; ++q) v += out[(int64_t)(a + q) * 16384 + rj * 128 + ri];
+        if (s != t) {
+          const int b = pl.base[p] + tile_index(false, pl.T, J, I) * pl.nsplit;
+          for (int q = 0; q < pl.nsplit; ++q) v += out[(int64_t)(b + q) * 16384 + ri * 128 + rj];
+        }
+      }
+      sum += ldexp((double)v, -8 * w);
+      g = ldexp(sum, ei + ej - 14);
+    }
+    Mode::st(G, i * D + j, Mode::from_d(g));
+    Mode::st(G, j * D + i, Mode::from_d(g));
+  }
+}
+
+SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
+  SlicePlan pl{};
+  pl.ns = ns;
+  pl.D = (int)D;
+  pl.RB = (int)((D + 127) / 128);
+  pl.T = pl.RB;
+  pl.KB = (int)((N + 63) / 64);
+  // pairs s <= t, s + t <= wmax, ordered by weight (largest s + t first)
+  pl.np = 0;
+  for (int w = std::min(wmax, 2 * ns - 2); w >= 0; --w)
+    for (int s = 0; s <= w / 2; ++s) {
+      const int t = w - s;
+      if (t >= ns) continue;
+      pl.ps[pl.np] = (int8_t)s;
+      pl.pt[pl.np] = (int8_t)t;
+      ++pl.np;
+    }
+  int64_t tiles = 0;
+  for (int p = 0; p < pl.np; ++p)
+    tiles += pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T;
+  // split the rows so that every item stays within SL_KB_MAX K-blocks and the GPU gets >= 2 waves
+  int nsplit = (pl.KB + SL_KB_MAX - 1) / SL_KB_MAX;
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  nsplit = (int)std::max<int64_t>(nsplit, std::min<int64_t>(want, std::max(1, pl.KB / 16)));
+  pl.kbper = (pl.KB + nsplit - 1) / nsplit;
+  pl.nsplit = (pl.KB + pl.kbper - 1) / pl.kbper;
+  int64_t b = 0;
+  for (int p = 0; p < pl.np; ++p) {
+    pl.base[p] = (int)b;
+    b += (pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T) * pl.nsplit;
+  }
+  pl.base[pl.np] = (int)b;
+  return pl;
+}
+
+template <class Mode, int ET>
+cudaError_t gram_slices_typed(ihsbin_problem* p, cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t N = A.N, D = A.D;
+  const SlicePlan pl = make_slice_plan(N, D, kGramSlices, kGramMaxWeight);
+  const int items = pl.base[pl.np];
+  unsigned* cmax = nullptr;
+  __nv_bfloat16* S = nullptr;
+  int* out = nullptr;
+  CK(prob_alloc(p, (size_t)D * sizeof(unsigned), (void**)&cmax, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2, (void**)&S, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)items * 16384 * sizeof(int), (void**)&out, SCOPE_SCRATCH));
+  CK(cudaMemsetAsync(cmax, 0, (size_t)D * sizeof(unsigned), st));
+  const size_t es = ET == ELEM_F32 ? 4 : 2;
+  {
+    KTimer kt(p, K_GRAM_SLICE, st, 0, (double)N * D * es);
+    const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, N / 64), 1024);
+    k_col_absmax<ET><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(A.A, A.ld, N, D, cmax);
+    CK(cudaGetLastError());
+  }
+  {
+    KTimer kt(p, K_GRAM_SLICE, st, 0, (double)N * D * es + (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2);
+    const unsigned gy = (unsigned)std::min<int64_t>((int64_t)pl.KB * 8, 32768);
+    k_slice<ET><<<dim3((unsigned)pl.RB, gy), 128, 0, st>>>(A.A, A.ld, N, D, cmax, pl.ns, pl.RB, pl.KB, S);
+    CK(cudaGetLastError());
+  }
+  {
+    // algorithmic BF16 work of the slice products (unpadded): 2 N per output entry and pair
+    double fl = 0;
+    for (int q = 0; q < pl.np; ++q) fl += 2.0 * N * (pl.ps[q] == pl.pt[q] ? D * (D + 1) / 2.0 : (double)D * D);
+    KTimer kt(p, K_GRAM_TC, st, fl, (double)items * pl.kbper * SL_STAGE_BYTES + (double)items * 65536);
+    const int smem = SL_STAGES * SL_STAGE_BYTES;
+    CK(cudaFuncSetAttribute(k_gram_slices_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_gram_slices_tc<<<(unsigned)items, SL_THREADS, smem, st>>>(S, pl, out, p->status);
+    CK(cudaGetLastError());
+  }
+  {
+    KTimer kt(p, K_GRAM_COMBINE, st, 0, (double)items * 65536 + (double)D * D * 8);
+    const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, D), 1024);
+    k_gram_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(out, pl, cmax, p->G);
+    CK(cudaGetLastError());
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st) {
+  const int et = p->A.elem;
+  if (compute == IHSBIN_COMPUTE_F64)
+    return et == ELEM_F32 ? gram_slices_typed<F64, ELEM_F32>(p, st) : gram_slices_typed<F64, ELEM_BF16>(p, st);
+  return et == ELEM_F32 ? gram_slices_typed<DD, ELEM_F32>(p, st) : gram_slices_typed<DD, ELEM_BF16>(p, st);
+}
+
+uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D) {
+  const SlicePlan pl = make_slice_plan(N, D, kGramSlices, kGramMaxWeight);
+  return (uint64_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (uint64_t)pl.base[pl.np] * 65536 + (uint64_t)D * 4;
+}
+
+}  // namespace ihsbin

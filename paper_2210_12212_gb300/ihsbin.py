@@ -31,6 +31,8 @@ SKETCH_KIND = {"gaussian": SK_GAUSSIAN, "srht": SK_SRHT, "countsketch": SK_COUNT
 DTYPE = {"f64": F64, "f32": F32, "bf16": BF16}
 COMPUTE = {"f64": COMPUTE_F64, "f32x2": COMPUTE_F32X2}
 PRODUCT = {"auto": PRODUCT_AUTO, "gram": PRODUCT_GRAM, "aspace": PRODUCT_ASPACE}
+GRAM_AUTO, GRAM_SLICES, GRAM_FMA = 0, 1, 2
+GRAM = {"auto": GRAM_AUTO, "slices": GRAM_SLICES, "fma": GRAM_FMA}
 
 
 class IhsbinError(RuntimeError):
@@ -53,7 +55,8 @@ class PathDesc(C.Structure):
     _fields_ = [("lambda_min", C.c_double), ("lambda_max", C.c_double), ("L", C.c_int32),
                 ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
-                ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32)]
+                ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
+                ("gram", C.c_int)]
 
 
 class Request(C.Structure):
@@ -74,9 +77,9 @@ EXPORTED = [
     "ihsbin_sketch_matrix_export", "ihsbin_build_basis", "ihsbin_plan_export", "ihsbin_basis_export",
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
-    "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve",
+    "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
 ]
-KCAT_COUNT = 17
+KCAT_COUNT = 20
 
 
 def load(path: Optional[str] = None):
@@ -114,6 +117,7 @@ def load(path: Optional[str] = None):
         "ihsbin_serve_wait": [vp, C.c_uint64, i64, C.POINTER(C.c_int), vp],
         "ihsbin_serve_destroy": [vp],
         "ihsbin_serve": [vp, C.POINTER(ServeConfig), vp, i64, vp, vp, vp],
+        "ihsbin_gram_export": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -217,8 +221,9 @@ class Problem:
                     k: Optional[Sequence[int]] = None, k_default: int = 20,
                     rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
-                    eps: float = 0.0, auto_rho: bool = False, stream=None):
-        """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch."""
+                    eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", stream=None):
+        """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
+        gram selects the Gram kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
         pd = PathDesc()
         pd.lambda_min, pd.lambda_max, pd.L = lambda_min, lambda_max, L
         ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
@@ -230,6 +235,7 @@ class Problem:
         pd.rho, pd.jmax = rho, jmax
         pd.compute, pd.product = COMPUTE[compute], PRODUCT[product]
         pd.eps, pd.auto_rho = eps, int(auto_rho)
+        pd.gram = GRAM[gram]
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def eval_path(self, lambdas, out=None, x_dtype: str = "f64", stream=None):
@@ -258,6 +264,13 @@ class Problem:
         GS = np.empty((D, D))
         _check(_lib.ihsbin_sketch_matrix_export(self.h, _ptr(SA), _ptr(GS)))
         return SA, GS
+
+    def gram(self):
+        """G = A_hat^T A_hat (D x D, FP64) as built by the last build_basis (Gram product mode)."""
+        D = min(self.n, self.d)
+        G = np.empty((D, D))
+        _check(_lib.ihsbin_gram_export(self.h, _ptr(G)))
+        return G
 
     def plan(self):
         Lv = C.c_int32()

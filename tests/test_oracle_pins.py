@@ -351,3 +351,29 @@ def test_auto_plan_effective_dimension_limits():
     de_large = 9 - p_large.lam0[0] * np.trace(np.linalg.inv(GS + p_large.lam0[0] * np.eye(9)))
     assert abs(de_small - 6) < 1e-6 and de_large < 1e-6
     assert p_small.k[0] > p_large.k[0] >= 1
+
+
+# ---- extended-precision Gram (checks the tensor-core Gram below FP64 GEMM rounding)
+def test_gram_extended_exact_on_integers():
+    rng = np.random.default_rng(11)
+    A = rng.integers(-1000, 1001, size=(50, 7))
+    exact = [[sum(int(A[k, i]) * int(A[k, j]) for k in range(50)) for j in range(7)] for i in range(7)]
+    assert np.array_equal(ob.gram_extended(A.astype(np.float64)), np.array(exact, dtype=np.float64))
+
+
+def test_gram_extended_rational_reference():
+    from fractions import Fraction
+    rng = np.random.default_rng(12)
+    A = (rng.standard_normal((20, 4)) * np.exp2(rng.integers(-20, 20, size=(20, 4)))).astype(np.float32)
+    G = ob.gram_extended(A)
+    for i in range(4):
+        for j in range(4):
+            ref = float(sum(Fraction(float(A[k, i])) * Fraction(float(A[k, j])) for k in range(20)))
+            assert abs(G[i, j] - ref) <= np.spacing(abs(ref))
+
+
+def test_gram_entries_extended_match_full():
+    rng = np.random.default_rng(13)
+    A = rng.standard_normal((300, 9)).astype(np.float32)
+    rows, cols = rng.integers(0, 9, 40), rng.integers(0, 9, 40)
+    assert np.array_equal(ob.gram_entries_extended(A, rows, cols), ob.gram_extended(A)[rows, cols])
