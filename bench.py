@@ -489,7 +489,7 @@ def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
 
 def kernel_peak(name, compute):
     """(bound, peak TFLOP/s, how the peak was obtained) for a kernel category."""
-    if name == "gram_tc_mma":  # BF16 tensor-core slice products, timed inside a long step
+    if name in ("gram_tc_mma", "loop_gram_tc", "loop_precond_tc"):  # BF16 tensor-core slice products
         try:
             with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
                 pk = json.load(f)["bf16_tflops_sustained"]

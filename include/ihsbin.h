@@ -145,6 +145,18 @@ typedef struct {
  *  FMA    : CUDA-core contraction in FP64 (F64 compute) or float-float (F32X2). */
 typedef enum { IHSBIN_GRAM_AUTO = 0, IHSBIN_GRAM_SLICES = 1, IHSBIN_GRAM_FMA = 2 } ihsbin_gram;
 
+/* Kernel for the two products of every step of the basis recursion
+ * (A_hat^T A_hat U in the Gram product mode, and P_l R).
+ *  AUTO   : SLICES in the F32X2 compute mode, FMA otherwise.
+ *  SLICES : F32X2 compute only.  The Gram and every P_l are cut by rows, and the
+ *           step's columns by columns, into 6 integer slices exact in BF16 (each
+ *           entry held to 2^-47 of its row's / column's largest magnitude); the 26
+ *           slice pairs with s + t <= 6 run on the tensor cores (tcgen05), exact in
+ *           chunks and drained into int32, and are combined in FP64 into the
+ *           float-float state: the accuracy class of the float-float contraction.
+ *  FMA    : CUDA-core contraction in the compute mode's arithmetic. */
+typedef enum { IHSBIN_LOOP_AUTO = 0, IHSBIN_LOOP_SLICES = 1, IHSBIN_LOOP_FMA = 2 } ihsbin_loop;
+
 typedef struct {
   double lambda_min, lambda_max;
   int32_t L;
@@ -159,6 +171,7 @@ typedef struct {
   double eps;
   int32_t auto_rho;
   ihsbin_gram gram;
+  ihsbin_loop loop;
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -250,7 +263,7 @@ IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
  * is also bracketed by CUDA events on the stream it runs on and its device
  * time is added at the call's synchronisation point.  Categories 0 ..
  * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 20
+#define IHSBIN_KCAT_COUNT 23
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,

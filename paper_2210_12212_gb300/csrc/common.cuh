@@ -56,6 +56,11 @@ __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (do
 __device__ __forceinline__ dd dd_renorm(dd a) { return fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
 
+// An int64 of magnitude < 2^62 as a float-float value (hi rounded, lo the rounded remainder).
+__device__ __forceinline__ dd ll_to_dd(long long x) {
+  const float h = __ll2float_rn(x);
+  return {h, __ll2float_rn(x - __float2ll_rn(h))};
+}
 __device__ __forceinline__ dd dd_add(dd a, dd b) {
   dd s = two_sum(a.hi, b.hi);
   dd t = two_sum(a.lo, b.lo);

@@ -48,6 +48,7 @@ struct Plan {
   int compute = IHSBIN_COMPUTE_F64;
   int product = IHSBIN_PRODUCT_GRAM;
   int gram = IHSBIN_GRAM_FMA;   // resolved Gram kernel (never AUTO)
+  int loop = IHSBIN_LOOP_FMA;   // resolved product kernel of the basis recursion (never AUTO)
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
@@ -63,7 +64,7 @@ struct DevBuf {
 enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
-  K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_NCAT
+  K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -164,6 +165,25 @@ constexpr int kGramSlices = 6;     // BF16 slices per entry
 constexpr int kGramMaxWeight = 6;  // slice pairs (s, t) kept: s + t <= kGramMaxWeight
 cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st);
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);
+
+// Exact-slice tensor-core products of the basis recursion (tc_loop.cu).  A operands
+// (D x D, rows sliced, once per build) and B operands (column panels, every step).
+int oz_tile_n(int64_t ncolg);
+size_t oz_rows_elems(int64_t D);
+size_t oz_rows_exps(int64_t D);
+size_t oz_cols_elems(int64_t D, int64_t ncolg, int NT);
+size_t oz_cols_exps(int64_t ncolg, int NT);
+// (float-float operands)
+cudaError_t oz_slice_rows(CBuf X, int64_t D, int groups, int64_t gs, __nv_bfloat16* out, int* ea, cudaStream_t st);
+cudaError_t oz_slice_cols(CBuf X, int64_t D, int ngroups, int64_t ncolg, int NT, int64_t cpg, int64_t gs,
+                          const int* perm, __nv_bfloat16* out, int* eb, cudaStream_t st);
+int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap);
+cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
+                       const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
+                       int ksplit, CBuf out, int* status, cudaStream_t st);
+double oz_pair_flops(int64_t M, int64_t N, int64_t K);
+// device bytes of the recursion's slices (G, every P_l, one step's B operand)
+uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
 cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,

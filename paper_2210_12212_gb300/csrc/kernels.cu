@@ -1238,11 +1238,22 @@ struct LdWcol {  // operand (k, j) = Wtmp[g][j][k] (column-major, N rows)
 
 constexpr int SPLIT_MAX = 16;
 
+// Tensor-core operands of the recursion's products (exact slices, tc_loop.cu)
+struct OzLoop {
+  bool on = false;
+  const __nv_bfloat16* Gs = nullptr;  // the Gram, rows sliced (Gram product mode)
+  const int* eg = nullptr;
+  const __nv_bfloat16* Ps = nullptr;  // P_l of every interval, rows sliced
+  const int* ep = nullptr;
+  __nv_bfloat16* Bs = nullptr;        // the step's B operand, columns sliced
+  int* eb = nullptr;
+};
+
 template <class Mode, int ET>
 static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf Y, CBuf Z, CBuf R, CBuf Wtmp,
                               const int* perm_dev,
                               const double* tau_dev, const double* lam0_dev, const std::vector<int>& order,
-                              cudaStream_t st) {
+                              const OzLoop& oz, cudaStream_t st) {
   const Tall& A = p->A;
   const int64_t D = A.D, K = p->K;
   const Plan& pl = p->plan;
@@ -1267,7 +1278,19 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t ys = nold * D;
     const int64_t mt = (D + 63) / 64;
     int ny = 1;
-    if (pl.product == IHSBIN_PRODUCT_GRAM) {
+    if (pl.product == IHSBIN_PRODUCT_GRAM && oz.on) {
+      // G times the concatenated old columns of every live interval, on the tensor cores
+      const int64_t ncat = nold * live;
+      const int NT = oz_tile_n(ncat);
+      {
+        KTimer kt(p, K_LOOP_SLICE, st, 0, 8.0 * D * ncat + 12.0 * D * ncat);
+        CK(oz_slice_cols(Uin, D, 1, ncat, NT, nold, gs, perm_dev, oz.Bs, oz.eb, st));
+      }
+      ny = oz_pick_split(D, ncat, 1, NT, SPLIT_MAX);
+      KTimer kt(p, K_LOOP_Y_TC, st, oz_pair_flops(D, ncat, D),
+                (double)oz_rows_elems(D) * 2 + (double)oz_cols_elems(D, ncat, NT) * 2 + 8.0 * ny * D * ncat);
+      CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, Y, p->status, st));
+    } else if (pl.product == IHSBIN_PRODUCT_GRAM) {
       // every live interval multiplies the same G: one contraction over their concatenated columns
       const int64_t ncat = nold * live;
       GemmShape sh{D, ncat, D, 0};
@@ -1305,6 +1328,28 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       k_make_R<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
           Y, ny, (int64_t)live * ys, Uin, live, nold, nnew, D, K, inew, perm_dev, tau_dev, lam0_dev, gs, R);
       CK(cudaGetLastError());
+    }
+    if (oz.on) {
+      // P_l R_l of every live interval, on the tensor cores
+      const int NT = oz_tile_n(nnew);
+      {
+        KTimer kt(p, K_LOOP_SLICE, st, 0, 20.0 * D * nnew * live);
+        CK(oz_slice_cols(R, D, live, nnew, NT, nnew, nnew * D, nullptr, oz.Bs, oz.eb, st));
+      }
+      const int ks = oz_pick_split(D, nnew, live, NT, SPLIT_MAX);
+      {
+        KTimer kt(p, K_LOOP_P_TC, st, oz_pair_flops(D, nnew, D) * live,
+                  (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 8.0 * ks * D * nnew * live);
+        CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, oz.eb, D, nnew, live, NT, ks, Z, p->status, st));
+      }
+      {
+        KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * 8 * (ks + 3));
+        k_update<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(Z, ks, live, nnew, D, K, i, Uin,
+                                                                              Uout, p->Ut, perm_dev, gs);
+        CK(cudaGetLastError());
+      }
+      std::swap(Uin, Uout);
+      continue;
     }
     const LdCColB<Mode> ldr{R, D, nnew * D, nullptr};
     {
@@ -1460,7 +1505,36 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   if (U0.p1) CK(cudaMemsetAsync(U0.p1, 0, per * L * 4, st));
   CK(cudaMemsetAsync(p->Ut.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
   if (p->Ut.p1) CK(cudaMemsetAsync(p->Ut.p1, 0, per * L * 4, st));
-  CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Z, R, Wtmp, perm_dev, tau_dev, lam0_dev, order, st)));
+  OzLoop oz;
+  if (Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES) {
+    oz.on = true;
+    const int64_t bcols = (int64_t)L * (ncol_max + 32);
+    __nv_bfloat16 *Ps = nullptr, *Bs = nullptr;
+    int *ep = nullptr, *eb = nullptr;
+    CK(prob_alloc(p, oz_rows_elems(D) * 2 * L, (void**)&Ps, SCOPE_SCRATCH));
+    CK(prob_alloc(p, oz_rows_exps(D) * 4 * L, (void**)&ep, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)bcols * ((D + 31) / 32) * 6 * 32 * 2, (void**)&Bs, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)bcols * 4, (void**)&eb, SCOPE_SCRATCH));
+    {
+      KTimer kt(p, K_LOOP_SLICE, st, 0, (double)L * D * D * 16 + (double)L * oz_rows_elems(D) * 2);
+      CK(oz_slice_rows(p->Pinv, D, L, D * D, Ps, ep, st));
+    }
+    if (pl.product == IHSBIN_PRODUCT_GRAM) {
+      __nv_bfloat16* Gs = nullptr;
+      int* eg = nullptr;
+      CK(prob_alloc(p, oz_rows_elems(D) * 2, (void**)&Gs, SCOPE_SCRATCH));
+      CK(prob_alloc(p, oz_rows_exps(D) * 4, (void**)&eg, SCOPE_SCRATCH));
+      KTimer kt(p, K_LOOP_SLICE, st, 0, (double)D * D * 16 + (double)oz_rows_elems(D) * 2);
+      CK(oz_slice_rows(p->G, D, 1, 0, Gs, eg, st));
+      oz.Gs = Gs;
+      oz.eg = eg;
+    }
+    oz.Ps = Ps;
+    oz.ep = ep;
+    oz.Bs = Bs;
+    oz.eb = eb;
+  }
+  CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Z, R, Wtmp, perm_dev, tau_dev, lam0_dev, order, oz, st)));
 
   // a5: primal image of the dual basis, W_l = A_hat utilde_l (N x jc K)
   if (p->dual && csr) {

@@ -90,6 +90,9 @@ uint64_t request_footprint(const ihsbin_request* q) {
   if (pd.k) for (int l = 0; l < (int)L; ++l) kmax = std::max(kmax, (double)pd.k[l]);
   const double jc = pd.jmax > 0 ? std::min((double)pd.jmax, kmax) : kmax;
   bytes += 3 * L * D * D * 8 + D * D * 8 * 9;
+  // slices of the tensor-core products of the recursion (float-float compute)
+  if (pd.compute == IHSBIN_COMPUTE_F32X2 && pd.loop != IHSBIN_LOOP_FMA)
+    bytes += (double)loop_slices_bytes((int64_t)D, (int)L, (int64_t)(jc * K));
   // integer slices and tiles of the tensor-core Gram (dense FP32/BF16 data)
   if (A.layout == IHSBIN_DENSE_ROWMAJOR && A.dtype != IHSBIN_F64 && pd.gram != IHSBIN_GRAM_FMA &&
       pd.product != IHSBIN_PRODUCT_ASPACE)

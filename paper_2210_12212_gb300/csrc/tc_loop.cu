@@ -1,0 +1,495 @@
+// The two products of every step of the basis recursion (Algorithm 2) in the
+// float-float compute mode, on the 5th-generation tensor cores:
+//   Y   = A_hat^T A_hat U   (the Gram times the old columns of all live intervals)
+//   Z_l = P_l R_l           (interval l's preconditioner times its right-hand sides)
+// by the exact-slice method of the Gram kernel (tc_gram.cu), now on both operands:
+//  * A operand (the Gram, or P_l; fixed during the recursion): row i scaled by
+//    2^(7 - ea_i), ea_i the exponent of its largest magnitude, and cut into
+//    OZ_S = 6 integer slices exact in BF16; done once per build;
+//  * B operand (the columns of U or R; new every step): column j scaled by
+//    2^(7 - eb_j) and cut the same way, every step;
+//  * C_ij = 2^(ea_i + eb_j - 14) sum_{s + t <= 6} 2^(-8(s+t)) sum_k a_s(i,k) b_t(k,j).
+// The 26 slice pairs of one k-block accumulate by weight w = s + t into seven
+// Tensor Memory accumulators.  Between two drains an accumulator receives at most
+// 6 pairs x 128 k integer products of magnitude <= 2^14 (|sum| < 2^24: exact in
+// its FP32 accumulator); drained chunks add exactly in int32, the weights are
+// combined in FP64 (smallest first), and the result is written as a float-float
+// split partial -- the format the recursion's update kernels read.
+// Slicing: each entry is rounded to an integer V in units of 2^(e - 47) (|V| <= 2^47,
+// e the exponent of its row's / column's largest magnitude) and written as six
+// balanced base-256 digits.  Combination: the seven weights are joined exactly in
+// int64 and converted to float-float with FP32 operations only.
+// Accuracy: every operand entry is held to 2^-47 of its row's (column's) largest
+// magnitude and the dropped pairs weigh at most 2^-52 of the leading product, the
+// accuracy class of the float-float contraction these products replace.
+//
+// Kernel roles (one CTA per 128-row tile x NT-column tile x group x k-range):
+// warp 0 (one lane) streams each k-block's 6 A slices (48 KiB) and 6 B slices
+// with two bulk copies into a ring of stages; warp 1 owns the Tensor Memory and
+// one lane issues the 52 MMAs (M = 128, N = NT, K = 16) of a stage; the
+// epilogue warps drain finished accumulators into int32 while the MMAs of the
+// next chunk run into the other buffer.  All waits are bounded in time
+// (DEV_TIMEOUT in the status word).
+#include <algorithm>
+#include <cfloat>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace ihsbin {
+namespace {
+
+#define CK(x)                              \
+  do {                                     \
+    cudaError_t e__ = (x);                 \
+    if (e__ != cudaSuccess) return e__;    \
+  } while (0)
+
+constexpr int OZ_S = 6;              // slices per operand entry
+constexpr int OZ_W = 6;              // kept pairs: s + t <= OZ_W
+constexpr int OZ_NW = OZ_W + 1;      // weights 0 .. OZ_W
+constexpr int OZ_BK = 32;            // k per block
+constexpr int OZ_ABLK = 128 * OZ_BK; // A block: 128 rows x 32 k (8 KiB)
+constexpr int OZ_CHUNK = 4;          // k-blocks between drains (6 x 128 x 2^14 < 2^24)
+constexpr int OZ_KB_MAX = 512;       // k-blocks per CTA (int32 sums: 6 x 16384 x 2^14 < 2^31)
+constexpr int OZ_NONFINITE = 1 << 20;
+
+template <int NT>
+struct OzCfg {
+  static constexpr int BBLK = NT * OZ_BK;               // B block: NT rows x 32 k
+  static constexpr int A_BYTES = OZ_S * OZ_ABLK * 2;    // 48 KiB
+  static constexpr int B_BYTES = OZ_S * BBLK * 2;       // 6 / 12 KiB
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int STAGES = NT == 16 ? 4 : 3;
+  static constexpr int SMEM = STAGES * STAGE;           // 216 / 180 KiB
+  static constexpr int EPI_WARPS = NT == 16 ? 4 : 8;
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int COLS = NT == 16 ? 256 : 512;     // two buffers of 7 accumulators
+  static constexpr int WPG = NT == 16 ? OZ_NW : 4;      // weights per epilogue warpgroup
+};
+
+struct OzArgs {
+  const __nv_bfloat16* As;
+  int64_t a_gstride;     // elements per A group (0: one A shared by every group)
+  const int* a_perm;     // group -> A group (nullptr: identity)
+  const int* ea;
+  int64_t ea_gstride;
+  const __nv_bfloat16* Bs;
+  int64_t b_gstride;
+  const int* eb;
+  int64_t eb_gstride;
+  int KB;                // k-blocks of the contraction
+  int64_t M, N;          // valid rows, valid columns per group
+  int groups, ksplit, kbper;
+  CBuf out;              // float-float partials: out[((s * groups + g) * N + j) * M + i]
+  int* status;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
+  using C = OzCfg<NT>;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = blockIdx.x, mt = blockIdx.y;
+  const int g = blockIdx.z / a.ksplit, sp = blockIdx.z - g * a.ksplit;
+  const int kb0 = sp * a.kbper, kb1 = min(a.KB, kb0 + a.kbper);
+  const int nkb = kb1 - kb0, nch = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+  const int ag = a.a_perm ? a.a_perm[g] : g;
+  const __nv_bfloat16* gA = a.As + (int64_t)ag * a.a_gstride + ((int64_t)mt * a.KB + kb0) * (OZ_S * OZ_ABLK);
+  const __nv_bfloat16* gB = a.Bs + (int64_t)g * a.b_gstride + ((int64_t)nt * a.KB + kb0) * (OZ_S * C::BBLK);
+
+  if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_base), C::COLS);
+  if (tid == 0) {
+    for (int i = 0; i < C::STAGES; ++i) {
+      tc::bar_init(tc::smem_addr(&full[i]), 1);
+      tc::bar_init(tc::smem_addr(&empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::bar_init(tc::smem_addr(&tfull[i]), 1);
+      tc::bar_init(tc::smem_addr(&tempty[i]), C::EPI_WARPS);
+    }
+    tc::bar_init(tc::smem_addr(&done), 1);
+    abort_flag = 0;
+    tc::bar_init_fence();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  volatile int* abort_v = &abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      int issued = 0;
+      for (int it = 0; it < nkb; ++it) {
+        const int st = it % C::STAGES, rnd = it / C::STAGES;
+        if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
+          dev_fail(a.status, DEV_TIMEOUT);
+          *abort_v = 1;
+          break;
+        }
+        if (*abort_v) break;
+        const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), fb = tc::smem_addr(&full[st]);
+        tc::bar_arrive_tx(fb, C::STAGE);
+        tc::bulk_load(sa, gA + (int64_t)it * (OZ_S * OZ_ABLK), C::A_BYTES, fb);
+        tc::bulk_load(sa + C::A_BYTES, gB + (int64_t)it * (OZ_S * C::BBLK), C::B_BYTES, fb);
+        issued = it + 1;
+      }
+      for (int it = issued > C::STAGES ? issued - C::STAGES : 0; it < issued; ++it)
+        tc::bar_wait(tc::smem_addr(&full[it % C::STAGES]), (it / C::STAGES) & 1);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = tc::idesc_bf16(128, NT);
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int h = c & 1;
+        if (c >= 2 && !tc::bar_wait(tc::smem_addr(&tempty[h]), ((c >> 1) - 1) & 1)) {
+          dev_fail(a.status, DEV_TIMEOUT);
+          *abort_v = 1;
+          break;
+        }
+        tc::fence_after_sync();
+        const uint32_t dbase = tmem + (uint32_t)(h * (C::COLS / 2));
+        const int i0 = c * OZ_CHUNK, i1 = min(nkb, i0 + OZ_CHUNK);
+        for (int it = i0; it < i1; ++it) {
+          const int st = it % C::STAGES, rnd = it / C::STAGES;
+          if (!tc::bar_wait(tc::smem_addr(&full[st]), rnd & 1) || *abort_v) {
+            dev_fail(a.status, DEV_TIMEOUT);
+            *abort_v = 1;
+            ok = false;
+            break;
+          }
+          tc::fence_after_sync();
+          const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), sb = sa + C::A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < OZ_BK / 16; ++ks)
+#pragma unroll
+            for (int s = 0; s < OZ_S; ++s)
+#pragma unroll
+              for (int t = 0; t < OZ_S; ++t) {
+                if (s + t > OZ_W) continue;
+                const int w = s + t;
+                // the first MMA into accumulator w of a chunk overwrites it
+                const bool first = it == i0 && ks == 0 && s == (w > OZ_S - 1 ? w - (OZ_S - 1) : 0);
+                tc::mma_bf16(dbase + (uint32_t)(w * NT),
+                             tc::smem_desc(sa + s * (OZ_ABLK * 2) + ks * 256, 128, 512),
+                             tc::smem_desc(sb + t * (C::BBLK * 2) + ks * 256, 128, 512), idesc, first ? 0u : 1u);
+              }
+          tc::commit(tc::smem_addr(&empty[st]));
+        }
+        if (ok) tc::commit(tc::smem_addr(&tfull[h]));
+      }
+      tc::commit(tc::smem_addr(&done));
+      tc::bar_wait(tc::smem_addr(&done), 0);
+    }
+  } else {  // epilogue warps: warpgroup q drains weights [q * WPG, q * WPG + WPG)
+    const int q = (warp - 2) >> 2, lq = warp & 3;
+    const int w0 = q * C::WPG;
+    const int r = lq * 32 + lane;  // Tensor Memory lane = row of the tile
+    int acc[C::WPG * NT];
+#pragma unroll
+    for (int x = 0; x < C::WPG * NT; ++x) acc[x] = 0;
+    for (int c = 0; c < nch; ++c) {
+      const int h = c & 1;
+      if (!tc::bar_wait(tc::smem_addr(&tfull[h]), (c >> 1) & 1) || *abort_v) {
+        if (lane == 0) dev_fail(a.status, DEV_TIMEOUT);
+        *abort_v = 1;
+        break;
+      }
+      tc::fence_after_sync();
+#pragma unroll
+      for (int wi = 0; wi < C::WPG; ++wi) {
+        if (w0 + wi >= OZ_NW) continue;  // warp-uniform
+        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT);
+        if constexpr (NT == 16) {
+          uint32_t v[16];
+          tc::tmem_ld16(ta, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+        } else {
+          uint32_t v[32];
+          tc::tmem_ld32(ta, v);
+          tc::tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::bar_arrive(tc::smem_addr(&tempty[h]));
+    }
+    // every epilogue warp reaches these barriers, aborted or not
+    tc::named_sync(1, 32 * C::EPI_WARPS);
+    const bool live = *abort_v == 0;
+    // Combination without FP64 (a slow pipe on this part): per column,
+    //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3 and lo = acc_4 2^16 + acc_5 2^8 + acc_6
+    // are exact in int64 (|acc_w| < 2^31), and C = 2^(ea + eb - 38) hi + 2^(ea + eb - 62) lo.
+    long long* xch = reinterpret_cast<long long*>(smem);  // the stages are idle: every MMA has completed
+    if constexpr (C::EPI_WARPS == 8) {
+      if (q == 1 && live) {
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+          xch[j * 128 + r] = ((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j];  // weights 4, 5, 6
+      }
+      tc::named_sync(2, 32 * C::EPI_WARPS);
+    }
+    if (q == 0 && live) {
+      const int64_t i = (int64_t)mt * 128 + r;
+      if (i < a.M) {
+        const int ei = a.ea[(int64_t)ag * a.ea_gstride + i];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const int64_t jj = (int64_t)nt * NT + j;
+          if (jj >= a.N) break;
+          const long long hi = (((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j]) * 256 + acc[3 * NT + j];
+          long long lo;
+          if constexpr (C::EPI_WARPS == 8)
+            lo = xch[j * 128 + r];
+          else
+            lo = ((long long)acc[4 * NT + j] * 256 + acc[5 * NT + j]) * 256 + acc[6 * NT + j];
+          const int ej = a.eb[(int64_t)g * a.eb_gstride + jj];
+          dd y;
+          if (ei == OZ_NONFINITE || ej == OZ_NONFINITE) {
+            y = dd{__int_as_float(0x7fc00000), 0.f};
+          } else {
+            const int sc = ei + ej;
+            dd yh = ll_to_dd(hi), yl = ll_to_dd(lo);
+            yh = dd{ldexpf(yh.hi, sc - 38), ldexpf(yh.lo, sc - 38)};
+            yl = dd{ldexpf(yl.hi, sc - 62), ldexpf(yl.lo, sc - 62)};
+            y = dd_add(yh, yl);
+          }
+          DD::st(a.out, (((int64_t)sp * a.groups + g) * a.N + jj) * a.M + i, y);
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 1) tc::tmem_dealloc(tmem, C::COLS);
+}
+
+// Block-wide maximum of a non-negative float (blockDim.x = 128).
+__device__ __forceinline__ float block_max128(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  return fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+}
+
+// Exponent e with |x| < 2^e for the row / column maximum m (its high words: a
+// normalised float-float value never exceeds the float below 2^e plus half its ulp).
+__device__ __forceinline__ int oz_exp(float m) {
+  if (!(m <= 3.402823466e38f)) return OZ_NONFINITE;  // Inf or NaN
+  int e = 0;
+  if (m > 0.f) frexpf(m, &e);
+  return e;
+}
+
+// v = hi + lo scaled by 2^(47 - e) to the nearest integer V (|V| <= 2^47, error <= 1 unit,
+// i.e. 2^-47 of 2^e), then V = sum_t a_t 2^(8 (5 - t)) in balanced base-256 digits |a_t| <= 128.
+__device__ __forceinline__ void store_digits(const float (&hi)[8], const float (&lo)[8], int e, bool live,
+                                             __nv_bfloat16* dst, int64_t tstride) {
+  long long V[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    V[q] = live ? __float2ll_rn(ldexpf(hi[q], 47 - e)) + __float2ll_rn(ldexpf(lo[q], 47 - e)) : 0ll;
+  int dg[OZ_S][8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    long long x = V[q];
+#pragma unroll
+    for (int t = OZ_S - 1; t >= 1; --t) {
+      int d = (int)(x & 255);
+      d -= d > 128 ? 256 : 0;
+      dg[t][q] = d;
+      x = (x - d) >> 8;  // exact: x - d is a multiple of 256
+    }
+    dg[0][q] = (int)x;
+  }
+#pragma unroll
+  for (int t = 0; t < OZ_S; ++t) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn((float)dg[t][q]);  // |digit| <= 128: exact
+    *reinterpret_cast<uint4*>(dst + t * tstride) = *reinterpret_cast<const uint4*>(h);
+  }
+}
+
+// A operand: the rows of D x D row-major float-float matrices (group stride gs), one
+// CTA of 128 threads per row.  Block (g, mt, kb, s) of `out` holds slice s of rows
+// 128 mt .. +127, k = 32 kb .. +31; element (r, kk) at byte (r/8)*512 + (kk/8)*128 + (r%8)*16 + (kk%8)*2.
+__global__ void __launch_bounds__(128) k_oz_slice_rows(CBuf X, int64_t D, int64_t gs, int MT, int KB,
+                                                       __nv_bfloat16* out, int* ea) {
+  __shared__ float red[4];
+  const int64_t i = blockIdx.x;
+  const int g = blockIdx.y;
+  const float* xh = (const float*)X.p0 + (int64_t)g * gs + i * D;
+  const float* xl = (const float*)X.p1 + (int64_t)g * gs + i * D;
+  float m = 0.f;
+  if (i < D)
+    for (int64_t k = threadIdx.x; k < D; k += 128) {
+      const float a = fabsf(xh[k]);
+      m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);  // Inf / NaN mark the row
+    }
+  m = block_max128(m, red);
+  const int e = oz_exp(m);
+  const bool live = i < D && e != OZ_NONFINITE;
+  if (threadIdx.x == 0) ea[(int64_t)g * MT * 128 + i] = e;
+  const int mt = (int)(i >> 7), r = (int)(i & 127);
+  for (int c = threadIdx.x; c < KB * 4; c += 128) {
+    const int kb = c >> 2, kc = c & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)c * 8 + q;
+      h[q] = (live && k < D) ? xh[k] : 0.f;
+      l[q] = (live && k < D) ? xl[k] : 0.f;
+    }
+    store_digits(h, l, e, live, out + ((((int64_t)g * MT + mt) * KB + kb) * OZ_S) * OZ_ABLK +
+                                   ((r >> 3) * 512 + kc * 128 + (r & 7) * 16) / 2, OZ_ABLK);
+  }
+}
+
+// B operand: columns of column-major float-float panels (a column is contiguous over its D
+// entries).  Column cl < ncolg of group g is source column cg = g * ncolg + cl, stored at
+// (perm ? perm[cg / cpg] : cg / cpg) * gs + (cg % cpg) * D.  One CTA of 128 threads per
+// column (padded to NTL * NT per group).  Block (g, nt, kb, t) holds NT columns x 32 k.
+__global__ void __launch_bounds__(128) k_oz_slice_cols(CBuf X, int64_t D, int64_t ncolg, int NT, int NTL, int64_t cpg,
+                                                       int64_t gs, const int* perm, int KB, __nv_bfloat16* out,
+                                                       int* eb) {
+  __shared__ float red[4];
+  const int64_t c = blockIdx.x;
+  const int64_t per = (int64_t)NTL * NT;
+  const int g = (int)(c / per);
+  const int64_t cl = c - g * per;
+  const bool valid = cl < ncolg;
+  int64_t base = 0;
+  if (valid) {
+    const int64_t cg = (int64_t)g * ncolg + cl;
+    const int64_t grp = cg / cpg;
+    base = (perm ? (int64_t)perm[grp] : grp) * gs + (cg - grp * cpg) * D;
+  }
+  const float* xh = (const float*)X.p0 + base;
+  const float* xl = (const float*)X.p1 + base;
+  float m = 0.f;
+  if (valid)
+    for (int64_t k = threadIdx.x; k < D; k += 128) {
+      const float a = fabsf(xh[k]);
+      m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+    }
+  m = block_max128(m, red);
+  const int e = oz_exp(m);
+  const bool live = valid && e != OZ_NONFINITE;
+  if (threadIdx.x == 0) eb[c] = e;
+  const int ntile = (int)(cl / NT), nl = (int)(cl - (int64_t)ntile * NT);
+  const int64_t bblk = (int64_t)NT * OZ_BK;
+  for (int ch = threadIdx.x; ch < KB * 4; ch += 128) {
+    const int kb = ch >> 2, kc = ch & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)ch * 8 + q;
+      h[q] = (live && k < D) ? xh[k] : 0.f;
+      l[q] = (live && k < D) ? xl[k] : 0.f;
+    }
+    store_digits(h, l, e, live, out + ((((int64_t)g * NTL + ntile) * KB + kb) * OZ_S) * bblk +
+                                   ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+  }
+}
+
+inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
+inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
+
+template <int NT>
+cudaError_t launch_oz(const OzArgs& a, int MT, int NTL, cudaStream_t st) {
+  using C = OzCfg<NT>;
+  CK(cudaFuncSetAttribute(k_oz_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  dim3 grid((unsigned)NTL, (unsigned)MT, (unsigned)(a.groups * a.ksplit));
+  k_oz_mma<NT><<<grid, C::THREADS, C::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host interface
+int oz_tile_n(int64_t ncolg) { return ncolg <= 16 ? 16 : 32; }
+
+size_t oz_rows_elems(int64_t D) { return (size_t)oz_mt(D) * oz_kb(D) * OZ_S * OZ_ABLK; }
+size_t oz_rows_exps(int64_t D) { return (size_t)oz_mt(D) * 128; }
+size_t oz_cols_elems(int64_t D, int64_t ncolg, int NT) {
+  return (size_t)((ncolg + NT - 1) / NT) * oz_kb(D) * OZ_S * NT * OZ_BK;
+}
+size_t oz_cols_exps(int64_t ncolg, int NT) { return (size_t)((ncolg + NT - 1) / NT) * NT; }
+
+cudaError_t oz_slice_rows(CBuf X, int64_t D, int groups, int64_t gs, __nv_bfloat16* out, int* ea, cudaStream_t st) {
+  dim3 grid((unsigned)(oz_mt(D) * 128), (unsigned)groups);
+  k_oz_slice_rows<<<grid, 128, 0, st>>>(X, D, gs, oz_mt(D), oz_kb(D), out, ea);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_slice_cols(CBuf X, int64_t D, int ngroups, int64_t ncolg, int NT, int64_t cpg, int64_t gs,
+                          const int* perm, __nv_bfloat16* out, int* eb, cudaStream_t st) {
+  const int NTL = (int)((ncolg + NT - 1) / NT);
+  const int64_t cols = (int64_t)ngroups * NTL * NT;
+  k_oz_slice_cols<<<(unsigned)cols, 128, 0, st>>>(X, D, ncolg, NT, NTL, cpg, gs, perm, oz_kb(D), out, eb);
+  return cudaGetLastError();
+}
+
+int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap) {
+  const int KB = oz_kb(D);
+  const int64_t ctas = (int64_t)oz_mt(D) * ((ncolg + NT - 1) / NT) * groups;
+  int s = (int)std::max<int64_t>(1, (2 * 152 + ctas - 1) / ctas);
+  s = std::min(s, std::max(1, KB / OZ_CHUNK));            // at least one drain chunk per split
+  s = std::max(s, (KB + OZ_KB_MAX - 1) / OZ_KB_MAX);     // int32 bound per CTA
+  s = std::min(s, cap);
+  const int kbper = (KB + s - 1) / s;
+  return (KB + kbper - 1) / kbper;                        // every split non-empty
+}
+
+cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
+                       const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
+                       int ksplit, CBuf out, int* status, cudaStream_t st) {
+  OzArgs a{};
+  const int KB = oz_kb(D), MT = oz_mt(D), NTL = (int)((ncolg + NT - 1) / NT);
+  a.As = As;
+  a.a_gstride = a_shared ? 0 : (int64_t)oz_rows_elems(D);
+  a.a_perm = a_perm;
+  a.ea = ea;
+  a.ea_gstride = a_shared ? 0 : (int64_t)oz_rows_exps(D);
+  a.Bs = Bs;
+  a.b_gstride = (int64_t)oz_cols_elems(D, ncolg, NT);
+  a.eb = eb;
+  a.eb_gstride = (int64_t)NTL * NT;
+  a.KB = KB;
+  a.M = D;
+  a.N = ncolg;
+  a.groups = groups;
+  a.kbper = (KB + ksplit - 1) / ksplit;
+  a.ksplit = (KB + a.kbper - 1) / a.kbper;
+  if (a.ksplit != ksplit || a.kbper > OZ_KB_MAX) return cudaErrorInvalidValue;
+  a.out = out;
+  a.status = status;
+  return NT == 16 ? launch_oz<16>(a, MT, NTL, st) : launch_oz<32>(a, MT, NTL, st);
+}
+
+uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max) {
+  const uint64_t bcols = (uint64_t)L * (uint64_t)(ncol_max + 32);  // one step's columns, padded per group
+  return (uint64_t)(L + 1) * (oz_rows_elems(D) * 2 + oz_rows_exps(D) * 4) +
+         bcols * (uint64_t)oz_kb(D) * OZ_S * OZ_BK * 2 + bcols * 4;
+}
+
+double oz_pair_flops(int64_t M, int64_t N, int64_t K) {
+  int pairs = 0;
+  for (int s = 0; s < OZ_S; ++s)
+    for (int t = 0; t < OZ_S; ++t) pairs += s + t <= OZ_W;
+  return 2.0 * pairs * (double)M * (double)N * (double)K;
+}
+
+}  // namespace ihsbin
