@@ -154,22 +154,34 @@ def oracle_sample(prob, par, reps=1):
     t_fixed = time.perf_counter() - t0
     ks = np.array(par["k"])
     l = int(np.argsort(ks)[len(ks) // 2])          # the median-k interval
-    samples = []
-    for _ in range(reps):
-        t1 = time.perf_counter()
-        P = ob.precond(GS, plan.lam0[l])
-        ut = ob.basis(lambda V: G @ V, P, c, plan.tau[l], int(ks[l]))
-        for lam in prob.lambdas[(prob.lambdas >= plan.edges[l]) & (prob.lambdas <= plan.edges[l + 1])]:
-            ob.evaluate(ut, plan.tau[l], plan.lam0[l], lam)
-        samples.append(time.perf_counter() - t1)
-    t_int = min(samples)
+    # its basis with k_s = 8, 16, ... terms until one sample takes a few seconds (or k_s = k_l):
+    # every term of step i costs one product and one preconditioner solve per column, so the
+    # time per basis column is what extrapolates
+    t1 = time.perf_counter()
+    P = ob.precond(GS, plan.lam0[l])
+    t_factor = time.perf_counter() - t1
+    k_s = min(8, int(ks[l]))
+    while True:
+        samples = []
+        for _ in range(reps):
+            t1 = time.perf_counter()
+            ut = ob.basis(lambda V: G @ V, P, c, plan.tau[l], k_s)
+            for lam in prob.lambdas[(prob.lambdas >= plan.edges[l]) & (prob.lambdas <= plan.edges[l + 1])]:
+                ob.evaluate(ut, plan.tau[l], plan.lam0[l], lam)
+            samples.append(time.perf_counter() - t1)
+        if k_s >= int(ks[l]) or min(samples) > 3.0:
+            break
+        k_s = min(2 * k_s, int(ks[l]))
+    t_cols = min(samples)
     cols = ks * (ks + 1) / 2
-    per_path = t_fixed + t_int * cols.sum() / cols[l]
+    per_path = t_fixed + len(ks) * t_factor + t_cols * cols.sum() / (k_s * (k_s + 1) / 2)
+    t_int = t_factor + t_cols * cols[l] / (k_s * (k_s + 1) / 2)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return dict(value=1.0 / per_path, unit="paths/s", cores=cores, kind="oracle",
-                sample=f"FP64 numpy oracle: sketch+Gram+rhs ({t_fixed:.2f}s) and interval {l} "
-                       f"(k={int(ks[l])}, {t_int:.2f}s) of the {prob.name} path; per-path time "
-                       f"extrapolated by basis columns sum_l k_l(k_l+1)/2", t_fixed=t_fixed, t_interval=t_int)
+                sample=f"FP64 numpy oracle: sketch+Gram+rhs ({t_fixed:.2f}s), the factor of interval {l} "
+                       f"({t_factor:.2f}s) and its first {k_s} of k={int(ks[l])} basis terms with evaluation "
+                       f"({t_cols:.2f}s) on the {prob.name} path; per-path time = fixed + L factors + "
+                       f"time per basis column x sum_l k_l(k_l+1)/2", t_fixed=t_fixed, t_interval=t_int)
 
 
 def oracle_matrix(prob):
@@ -307,6 +319,14 @@ def serving_arm(args):
     print(json.dumps(line), flush=True)
 
 
+_T0 = time.perf_counter()
+
+
+def note(msg):
+    """Progress of the run on stderr (the JSON result line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f}s] {msg}", file=sys.stderr, flush=True)
+
+
 def main():
     args = parse()
     if args.config == "c5":
@@ -314,6 +334,7 @@ def main():
         return
     from synthetic import make_problem
     prob = make_problem(args.config, seed=0)
+    note(f"workload {args.config} generated")
     par = None if args.auto else load_params(args.config[:-1] if args.config == "c3t" else args.config)
     if args.impl == "reference":
         reference_arm(args, prob, par)
@@ -365,6 +386,7 @@ def main():
     for _ in range(max(args.warmup, 0)):
         step(p, X_dev)
     torch.cuda.synchronize()
+    note("warm-up done")
 
     # ---- timed region: K steps, per-kernel events on the launching stream
     p.set_timing(True)
@@ -414,6 +436,7 @@ def main():
 
     # ---- parity of the timed result against the FP64 oracle (sampled lambdas, rank 0)
     check = None
+    note("timed region done")
     if rank == 0 and not args.no_check:
         check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6,
                               eps=args.eps)
@@ -429,6 +452,7 @@ def main():
             "avg_launch_ms": ms / launches, "peak_basis": peak_note}
 
     cpu = None
+    note("parity done")
     if rank == 0 and not args.no_cpu and world == 1:
         info = oracle_sample(prob, par if par is not None else p.plan_dict_for_oracle())
         cpu = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
