@@ -445,9 +445,13 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, flops, byts) = dom
     bound, peak, peak_note = kernel_peak(name, args.compute)
-    achieved = flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0
+    if bound == "hbm":
+        achieved, unit = (byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0), "GB/s"
+    else:
+        achieved, unit = (flops / (ms * 1e-3) / 1e12 if ms > 0 else 0.0), "TFLOP/s"
     traffic = read_traffic(name, launches / args.steps if args.steps else 0)
-    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+            "algorithmic_bytes_per_launch": byts / launches if launches else 0.0,
             "traffic": traffic, "kernel": name, "launches_per_step": launches / args.steps,
             "avg_launch_ms": ms / launches, "peak_basis": peak_note}
 
@@ -511,15 +515,27 @@ def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
             "oracle_max_rel_dist_to_exact_ridge": max(conv)}
 
 
+def measured_peak(key, fallback):
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "of fallback"
+
+
+# Categories whose binding resource is HBM: every step of the recursion streams the live
+# intervals' preconditioner slices (12 bytes per entry), which do not stay in L2.
+HBM_BOUND = ("loop_precond_tc",)
+
+
 def kernel_peak(name, compute):
-    """(bound, peak TFLOP/s, how the peak was obtained) for a kernel category."""
-    if name in ("gram_tc_mma", "loop_gram_tc", "loop_precond_tc"):  # BF16 tensor-core slice products
-        try:
-            with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-                pk = json.load(f)["bf16_tflops_sustained"]
-            return "tensor", float(pk), "measured cuBLAS bf16 sustained (MEASURED_PEAKS.json), of measured"
-        except (OSError, KeyError, ValueError):
-            return "tensor", 1700.0, "fallback bf16 sustained figure, of fallback"
+    """(bound, peak, how the peak was obtained) for a kernel category; TFLOP/s, or GB/s for hbm."""
+    if name in HBM_BOUND:
+        pk, how = measured_peak("hbm_gbs", 6800.0)
+        return "hbm", pk, f"copy bandwidth (MEASURED_PEAKS.json hbm_gbs), {how}"
+    if name in ("gram_tc_mma", "loop_gram_tc"):  # BF16 tensor-core slice products, inside a long step
+        pk, how = measured_peak("bf16_tflops_sustained", 1700.0)
+        return "tensor", pk, f"cuBLAS bf16 sustained (MEASURED_PEAKS.json), {how}"
     if compute == "f64":
         return "alu", 2 * FP64_FMA_PEAK / 1e12, "FP64 FMA rate from unit counts (152 SMs x 2 DFMA/clk x 2070 MHz)"
     instr = INSTR_PER_MAC.get(name) or 12
