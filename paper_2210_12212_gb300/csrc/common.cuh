@@ -56,11 +56,6 @@ __device__ __forceinline__ double dd_to_double(dd a) { return (double)a.hi + (do
 __device__ __forceinline__ dd dd_renorm(dd a) { return fast_two_sum(a.hi, a.lo); }
 __device__ __forceinline__ dd dd_neg(dd a) { return {-a.hi, -a.lo}; }
 
-// An int64 of magnitude < 2^62 as a float-float value (hi rounded, lo the rounded remainder).
-__device__ __forceinline__ dd ll_to_dd(long long x) {
-  const float h = __ll2float_rn(x);
-  return {h, __ll2float_rn(x - __float2ll_rn(h))};
-}
 __device__ __forceinline__ dd dd_add(dd a, dd b) {
   dd s = two_sum(a.hi, b.hi);
   dd t = two_sum(a.lo, b.lo);
@@ -70,6 +65,33 @@ __device__ __forceinline__ dd dd_add(dd a, dd b) {
   return fast_two_sum(s.hi, s.lo);
 }
 __device__ __forceinline__ dd dd_sub(dd a, dd b) { return dd_add(a, dd_neg(b)); }
+// An int64 as a float-float value with 32-bit conversions only (64-bit integer <-> float
+// conversions run on the FP64 pipe): x = a 2^48 + b 2^32 + c 2^16 + d with a signed and b, c, d
+// in [0, 2^16), every part exact in FP32; each pair adds exactly (TwoSum), the two pairs with a
+// float-float addition (relative error about 2^-48).
+__device__ __forceinline__ dd ll_to_dd(long long x) {
+  const unsigned long long u = (unsigned long long)x;
+  const int a = (int)(x >> 48);
+  const unsigned b = (unsigned)(u >> 32) & 0xffffu, c = (unsigned)(u >> 16) & 0xffffu, d = (unsigned)u & 0xffffu;
+  return dd_add(two_sum((float)a * 281474976710656.f, (float)b * 4294967296.f),
+                two_sum((float)c * 65536.f, (float)d));
+}
+// x 2^k, exact unless the result leaves the normal range (then as ldexpf)
+__device__ __forceinline__ float scale_pow2(float x, int k) {
+  return (k >= -126 && k <= 127) ? x * __int_as_float((k + 127) << 23) : ldexpf(x, k);
+}
+
+// Exact-slice products (tc_loop.cu) leave, per output entry, the exact integers
+//   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6
+// of the weight accumulators; the entry is 2^(e_row + e_col - 38) hi + 2^(e_row + e_col - 62) lo.
+constexpr int OZ_EXP_NONFINITE = 1 << 20;  // row/column exponent marking an Inf/NaN entry
+__device__ __forceinline__ dd oz_join(long long hi, long long lo, int erow, int ecol) {
+  if (erow == OZ_EXP_NONFINITE || ecol == OZ_EXP_NONFINITE) return dd{__int_as_float(0x7fc00000), 0.f};
+  const int sc = erow + ecol;
+  const dd yh = ll_to_dd(hi), yl = ll_to_dd(lo);
+  return dd_add(dd{scale_pow2(yh.hi, sc - 38), scale_pow2(yh.lo, sc - 38)},
+                dd{scale_pow2(yl.hi, sc - 62), scale_pow2(yl.lo, sc - 62)});
+}
 __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   dd p = two_prod(a.hi, b.hi);
   p.lo = __fmaf_rn(a.hi, b.lo, p.lo);

@@ -178,9 +178,10 @@ cudaError_t oz_slice_rows(CBuf X, int64_t D, int groups, int64_t gs, __nv_bfloat
 cudaError_t oz_slice_cols(CBuf X, int64_t D, int ngroups, int64_t ncolg, int NT, int64_t cpg, int64_t gs,
                           const int* perm, __nv_bfloat16* out, int* eb, cudaStream_t st);
 int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap);
+// writes the exact int64 partials ohi / olo (see oz_join in common.cuh), entry ((s * groups + g) * ncolg + j) * D + i
 cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
                        const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
-                       int ksplit, CBuf out, int* status, cudaStream_t st);
+                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st);
 double oz_pair_flops(int64_t M, int64_t N, int64_t K);
 // device bytes of the recursion's slices (G, every P_l, one step's B operand)
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);

@@ -1208,6 +1208,58 @@ __global__ void k_update(CBuf Z, int S, int live, int64_t ncol, int64_t D, int64
   Mode::st(Ut, o, Mode::add(Mode::ld(Ut, o), u));
 }
 
+// The same two kernels when the products ran on the tensor cores (tc_loop.cu): a product entry
+// is the sum over the k-splits of two exact int64 partials, joined into float-float with its
+// row exponent (G, or P_l) and column exponent (U, or R) -- oz_join in common.cuh.
+__global__ void k_make_R_oz(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
+                            const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
+                            const int* perm, const double* tau, const double* lam0, int64_t gs, CBuf R) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)live * nnew * D) return;
+  const int g = (int)(e / (nnew * D));
+  const int64_t col = (e / D) % nnew, k = e % D;
+  const int l = perm[g];
+  const int64_t j = col / K;
+  const int64_t o = (int64_t)l * gs + col * D + k;
+  const dd lm = dd_from_double(lam0[l]);
+  dd r;
+  if (j == inew) {
+    r = dd_mul(lm, DD::ld(U, o - K * D));
+  } else {
+    const int64_t c = (int64_t)g * nold + col, yo = c * D + k;
+    long long h = Yhi[yo], lo = Ylo[yo];
+    for (int s = 1; s < ny; ++s) {
+      h += Yhi[s * ny_stride + yo];
+      lo += Ylo[s * ny_stride + yo];
+    }
+    const dd y = oz_join(h, lo, eg[k], eu[c]);
+    r = dd_mul(dd_from_double(tau[l]), dd_add(y, dd_mul(lm, DD::ld(U, o))));
+    if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
+  }
+  DD::st(R, e, r);
+}
+__global__ void k_update_oz(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
+                            const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i,
+                            CBuf Uin, CBuf Uout, CBuf Ut, const int* perm, int64_t gs) {
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)live * ncol * D) return;
+  const int g = (int)(e / (ncol * D));
+  const int64_t col = (e / D) % ncol, row = e % D;
+  const int64_t zo = ((int64_t)g * ncol + col) * D + row, ss = (int64_t)live * ncol * D;
+  long long h = Zhi[zo], lo = Zlo[zo];
+  for (int s = 1; s < S; ++s) {
+    h += Zhi[s * ss + zo];
+    lo += Zlo[s * ss + zo];
+  }
+  const dd z = oz_join(h, lo, ep[(int64_t)perm[g] * ep_gs + row], er[(int64_t)g * er_gs + col]);
+  const int64_t o = (int64_t)perm[g] * gs + col * D + row;
+  const int64_t j = col / K;
+  dd u = (j < i) ? DD::ld(Uin, o) : DD::zero();
+  u = dd_sub(u, z);
+  DD::st(Uout, o, u);
+  DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
+}
+
 // Y = A^T A U for the Gram product: the B operand is U (column j, contiguous over k)
 template <class Mode>
 struct EpY {
@@ -1247,6 +1299,7 @@ struct OzLoop {
   const int* ep = nullptr;
   __nv_bfloat16* Bs = nullptr;        // the step's B operand, columns sliced
   int* eb = nullptr;
+  long long *Yhi = nullptr, *Ylo = nullptr, *Zhi = nullptr, *Zlo = nullptr;  // exact split partials
 };
 
 template <class Mode, int ET>
@@ -1288,8 +1341,8 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       }
       ny = oz_pick_split(D, ncat, 1, NT, SPLIT_MAX);
       KTimer kt(p, K_LOOP_Y_TC, st, oz_pair_flops(D, ncat, D),
-                (double)oz_rows_elems(D) * 2 + (double)oz_cols_elems(D, ncat, NT) * 2 + 8.0 * ny * D * ncat);
-      CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, Y, p->status, st));
+                (double)oz_rows_elems(D) * 2 + (double)oz_cols_elems(D, ncat, NT) * 2 + 16.0 * ny * D * ncat);
+      CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, oz.Yhi, oz.Ylo, p->status, st));
     } else if (pl.product == IHSBIN_PRODUCT_GRAM) {
       // every live interval multiplies the same G: one contraction over their concatenated columns
       const int64_t ncat = nold * live;
@@ -1323,7 +1376,13 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int inew = (i < J) ? i : -1;
     sp.ksplit = std::min(pick_split(mt * ((nnew + tile_n(nnew) - 1) / tile_n(nnew)) * live, D, tile_k(nnew)),
                          SPLIT_MAX);
-    {
+    if (oz.on && pl.product == IHSBIN_PRODUCT_GRAM) {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ny + 24));
+      k_make_R_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
+          oz.Yhi, oz.Ylo, ny, (int64_t)live * ys, oz.eg, oz.eb, Uin, live, nold, nnew, D, K, inew, perm_dev, tau_dev,
+          lam0_dev, gs, R);
+      CK(cudaGetLastError());
+    } else {
       KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * 8 * (ny + 3));
       k_make_R<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
           Y, ny, (int64_t)live * ys, Uin, live, nold, nnew, D, K, inew, perm_dev, tau_dev, lam0_dev, gs, R);
@@ -1339,13 +1398,15 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       const int ks = oz_pick_split(D, nnew, live, NT, SPLIT_MAX);
       {
         KTimer kt(p, K_LOOP_P_TC, st, oz_pair_flops(D, nnew, D) * live,
-                  (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 8.0 * ks * D * nnew * live);
-        CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, oz.eb, D, nnew, live, NT, ks, Z, p->status, st));
+                  (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 16.0 * ks * D * nnew * live);
+        CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, oz.eb, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
+                      st));
       }
       {
-        KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * 8 * (ks + 3));
-        k_update<Mode><<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(Z, ks, live, nnew, D, K, i, Uin,
-                                                                              Uout, p->Ut, perm_dev, gs);
+        KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24));
+        k_update_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
+            oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.eb, (int64_t)oz_cols_exps(nnew, NT), live, nnew, D,
+            K, i, Uin, Uout, p->Ut, perm_dev, gs);
         CK(cudaGetLastError());
       }
       std::swap(Uin, Uout);
@@ -1495,8 +1556,10 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   p->Ut = alloc_cbuf(p, cm, per * L, SCOPE_BASIS, &err);
   CK(err);
   const int64_t ncol_max = (int64_t)pl.jc * K;
-  CBuf Y = cb((size_t)SPLIT_MAX * ncol_max * D * L);
-  CBuf Z = cb((size_t)SPLIT_MAX * ncol_max * D * L);
+  const bool oz_on = Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES;
+  // the tensor-core products leave exact int64 partials instead of float-float ones
+  CBuf Y = cb((oz_on && pl.product == IHSBIN_PRODUCT_GRAM) ? 1 : (size_t)SPLIT_MAX * ncol_max * D * L);
+  CBuf Z = cb(oz_on ? 1 : (size_t)SPLIT_MAX * ncol_max * D * L);
   CBuf R = cb((size_t)ncol_max * D * L);
   CBuf Wtmp{};
   if (pl.product == IHSBIN_PRODUCT_ASPACE) Wtmp = cb((size_t)ncol_max * A.N * L);
@@ -1506,7 +1569,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaMemsetAsync(p->Ut.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
   if (p->Ut.p1) CK(cudaMemsetAsync(p->Ut.p1, 0, per * L * 4, st));
   OzLoop oz;
-  if (Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES) {
+  if (oz_on) {
     oz.on = true;
     const int64_t bcols = (int64_t)L * (ncol_max + 32);
     __nv_bfloat16 *Ps = nullptr, *Bs = nullptr;
@@ -1515,6 +1578,25 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     CK(prob_alloc(p, oz_rows_exps(D) * 4 * L, (void**)&ep, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * ((D + 31) / 32) * 6 * 32 * 2, (void**)&Bs, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * 4, (void**)&eb, SCOPE_SCRATCH));
+    // the largest split partials of any step, replaying the recursion's (live, columns, splits)
+    size_t ymax = 1, zmax = 1;
+    {
+      const int J = pl.jmax > 0 ? pl.jmax : (1 << 30);
+      for (int i = 1; i < pl.kmax; ++i) {
+        int live = 0;
+        while (live < L && pl.k[order[live]] > i) ++live;
+        if (live == 0) break;
+        const int64_t nold = (int64_t)std::min(i, J) * K, nnew = (int64_t)std::min(i + 1, J) * K;
+        const int64_t ncat = nold * live;
+        if (pl.product == IHSBIN_PRODUCT_GRAM)
+          ymax = std::max(ymax, (size_t)oz_pick_split(D, ncat, 1, oz_tile_n(ncat), SPLIT_MAX) * ncat * D);
+        zmax = std::max(zmax, (size_t)oz_pick_split(D, nnew, live, oz_tile_n(nnew), SPLIT_MAX) * live * nnew * D);
+      }
+    }
+    CK(prob_alloc(p, ymax * 8, (void**)&oz.Yhi, SCOPE_SCRATCH));
+    CK(prob_alloc(p, ymax * 8, (void**)&oz.Ylo, SCOPE_SCRATCH));
+    CK(prob_alloc(p, zmax * 8, (void**)&oz.Zhi, SCOPE_SCRATCH));
+    CK(prob_alloc(p, zmax * 8, (void**)&oz.Zlo, SCOPE_SCRATCH));
     {
       KTimer kt(p, K_LOOP_SLICE, st, 0, (double)L * D * D * 16 + (double)L * oz_rows_elems(D) * 2);
       CK(oz_slice_rows(p->Pinv, D, L, D * D, Ps, ep, st));

@@ -13,23 +13,23 @@
 // Tensor Memory accumulators.  Between two drains an accumulator receives at most
 // 6 pairs x 128 k integer products of magnitude <= 2^14 (|sum| < 2^24: exact in
 // its FP32 accumulator); drained chunks add exactly in int32, the weights are
-// combined in FP64 (smallest first), and the result is written as a float-float
-// split partial -- the format the recursion's update kernels read.
+// joined exactly in int64 and written per k-split; the recursion's update kernels
+// add the splits exactly and convert to float-float with the row/column exponents.
 // Slicing: each entry is rounded to an integer V in units of 2^(e - 47) (|V| <= 2^47,
 // e the exponent of its row's / column's largest magnitude) and written as six
 // balanced base-256 digits.  Combination: the seven weights are joined exactly in
-// int64 and converted to float-float with FP32 operations only.
+// int64 (two Horner groups); the conversion to float-float uses FP32 operations only.
 // Accuracy: every operand entry is held to 2^-47 of its row's (column's) largest
 // magnitude and the dropped pairs weigh at most 2^-52 of the leading product, the
 // accuracy class of the float-float contraction these products replace.
 //
-// Kernel roles (one CTA per 128-row tile x NT-column tile x group x k-range):
-// warp 0 (one lane) streams each k-block's 6 A slices (48 KiB) and 6 B slices
-// with two bulk copies into a ring of stages; warp 1 owns the Tensor Memory and
-// one lane issues the 52 MMAs (M = 128, N = NT, K = 16) of a stage; the
-// epilogue warps drain finished accumulators into int32 while the MMAs of the
-// next chunk run into the other buffer.  All waits are bounded in time
-// (DEV_TIMEOUT in the status word).
+// Kernel roles (persistent: one CTA per SM walks the work items, a work item being a
+// 128-row tile x NT-column tile x group x k-range): warp 0 (one lane) streams each
+// k-block's 6 A slices (48 KiB) and 6 B slices with two bulk copies into a ring of
+// stages; warp 1 owns the Tensor Memory and one lane issues the 52 MMAs (M = 128,
+// N = NT, K = 16) of a stage; the epilogue warps drain finished accumulators into
+// int32 while the MMAs of the next chunk (of this or the next item) run into the
+// other buffer.  All waits are bounded in time (DEV_TIMEOUT in the status word).
 #include <algorithm>
 #include <cfloat>
 
@@ -53,16 +53,17 @@ constexpr int OZ_BK = 32;            // k per block
 constexpr int OZ_ABLK = 128 * OZ_BK; // A block: 128 rows x 32 k (8 KiB)
 constexpr int OZ_CHUNK = 4;          // k-blocks between drains (6 x 128 x 2^14 < 2^24)
 constexpr int OZ_KB_MAX = 512;       // k-blocks per CTA (int32 sums: 6 x 16384 x 2^14 < 2^31)
-constexpr int OZ_NONFINITE = 1 << 20;
+constexpr int OZ_NONFINITE = OZ_EXP_NONFINITE;
 
 template <int NT>
 struct OzCfg {
   static constexpr int BBLK = NT * OZ_BK;               // B block: NT rows x 32 k
   static constexpr int A_BYTES = OZ_S * OZ_ABLK * 2;    // 48 KiB
-  static constexpr int B_BYTES = OZ_S * BBLK * 2;       // 6 / 12 KiB
-  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int B_BYTES = OZ_S * BBLK * 2;       // 6 / 12 KiB copied per stage
+  static constexpr int B_SLOT = (OZ_S + 1) * BBLK * 2;  // plus one all-zero slice (see the MMA issue)
+  static constexpr int STAGE = A_BYTES + B_SLOT;
   static constexpr int STAGES = NT == 16 ? 4 : 3;
-  static constexpr int SMEM = STAGES * STAGE;           // 216 / 180 KiB
+  static constexpr int SMEM = STAGES * STAGE;              // 220 / 186 KiB
   static constexpr int EPI_WARPS = NT == 16 ? 4 : 8;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr int COLS = NT == 16 ? 256 : 512;     // two buffers of 7 accumulators
@@ -80,12 +81,17 @@ struct OzArgs {
   const int* eb;
   int64_t eb_gstride;
   int KB;                // k-blocks of the contraction
+  int MT, NTL;           // row tiles, column tiles per group
   int64_t M, N;          // valid rows, valid columns per group
   int groups, ksplit, kbper;
-  CBuf out;              // float-float partials: out[((s * groups + g) * N + j) * M + i]
+  long long* ohi;        // exact partials (weights 0..3 / 4..6), entry ((s * groups + g) * N + j) * M + i
+  long long* olo;
   int* status;
 };
 
+// Persistent: CTA b takes work items b, b + gridDim.x, ...; item = ((g * ksplit + sp) * MT + mt) * NTL + nt
+// (column tiles fastest, so CTAs running at the same time share the A rows in L2).  The stage ring
+// and the two Tensor Memory buffers run on counters that continue across items.
 template <int NT>
 __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
   using C = OzCfg<NT>;
@@ -94,13 +100,24 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = blockIdx.x, mt = blockIdx.y;
-  const int g = blockIdx.z / a.ksplit, sp = blockIdx.z - g * a.ksplit;
-  const int kb0 = sp * a.kbper, kb1 = min(a.KB, kb0 + a.kbper);
-  const int nkb = kb1 - kb0, nch = (nkb + OZ_CHUNK - 1) / OZ_CHUNK;
-  const int ag = a.a_perm ? a.a_perm[g] : g;
-  const __nv_bfloat16* gA = a.As + (int64_t)ag * a.a_gstride + ((int64_t)mt * a.KB + kb0) * (OZ_S * OZ_ABLK);
-  const __nv_bfloat16* gB = a.Bs + (int64_t)g * a.b_gstride + ((int64_t)nt * a.KB + kb0) * (OZ_S * C::BBLK);
+  const int items = a.NTL * a.MT * a.groups * a.ksplit;
+
+  struct Item {
+    int nt, mt, g, sp, ag, kb0, nkb;
+  };
+  auto decode = [&](int item) {
+    Item w;
+    w.nt = item % a.NTL;
+    int r = item / a.NTL;
+    w.mt = r % a.MT;
+    r /= a.MT;
+    w.sp = r % a.ksplit;
+    w.g = r / a.ksplit;
+    w.ag = a.a_perm ? a.a_perm[w.g] : w.g;
+    w.kb0 = w.sp * a.kbper;
+    w.nkb = min(a.KB, w.kb0 + a.kbper) - w.kb0;
+    return w;
+  };
 
   if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_base), C::COLS);
   if (tid == 0) {
@@ -116,6 +133,11 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
     abort_flag = 0;
     tc::bar_init_fence();
   }
+  // the seventh B slice of every stage stays zero (the copies fill slices 0..5 only)
+  for (int st = 0; st < C::STAGES; ++st)
+    for (int x = tid; x < C::BBLK * 2 / 16; x += C::THREADS)
+      reinterpret_cast<uint4*>(smem + st * C::STAGE + C::A_BYTES + C::B_BYTES)[x] = make_uint4(0, 0, 0, 0);
+  tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
@@ -124,147 +146,147 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
 
   if (warp == 0) {
     if (lane == 0) {  // producer
-      int issued = 0;
-      for (int it = 0; it < nkb; ++it) {
-        const int st = it % C::STAGES, rnd = it / C::STAGES;
-        if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
-          dev_fail(a.status, DEV_TIMEOUT);
-          *abort_v = 1;
-          break;
+      uint32_t q = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const Item w = decode(item);
+        const __nv_bfloat16* gA =
+            a.As + (int64_t)w.ag * a.a_gstride + ((int64_t)w.mt * a.KB + w.kb0) * (OZ_S * OZ_ABLK);
+        const __nv_bfloat16* gB =
+            a.Bs + (int64_t)w.g * a.b_gstride + ((int64_t)w.nt * a.KB + w.kb0) * (OZ_S * C::BBLK);
+        for (int it = 0; it < w.nkb; ++it, ++q) {
+          const uint32_t st = q % C::STAGES, rnd = q / C::STAGES;
+          if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
+            dev_fail(a.status, DEV_TIMEOUT);
+            *abort_v = 1;
+          }
+          if (*abort_v) {
+            ok = false;
+            break;
+          }
+          const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), fb = tc::smem_addr(&full[st]);
+          tc::bar_arrive_tx(fb, C::A_BYTES + C::B_BYTES);
+          tc::bulk_load(sa, gA + (int64_t)it * (OZ_S * OZ_ABLK), C::A_BYTES, fb);
+          tc::bulk_load(sa + C::A_BYTES, gB + (int64_t)it * (OZ_S * C::BBLK), C::B_BYTES, fb);
         }
-        if (*abort_v) break;
-        const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), fb = tc::smem_addr(&full[st]);
-        tc::bar_arrive_tx(fb, C::STAGE);
-        tc::bulk_load(sa, gA + (int64_t)it * (OZ_S * OZ_ABLK), C::A_BYTES, fb);
-        tc::bulk_load(sa + C::A_BYTES, gB + (int64_t)it * (OZ_S * C::BBLK), C::B_BYTES, fb);
-        issued = it + 1;
       }
-      for (int it = issued > C::STAGES ? issued - C::STAGES : 0; it < issued; ++it)
-        tc::bar_wait(tc::smem_addr(&full[it % C::STAGES]), (it / C::STAGES) & 1);
+      // the copies of the last stages land before the CTA may leave
+      for (uint32_t qq = q > (uint32_t)C::STAGES ? q - C::STAGES : 0; qq < q; ++qq)
+        tc::bar_wait(tc::smem_addr(&full[qq % C::STAGES]), (qq / C::STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      constexpr uint32_t idesc = tc::idesc_bf16(128, NT);
+      uint32_t q = 0, cc = 0;
       bool ok = true;
-      for (int c = 0; c < nch && ok; ++c) {
-        const int h = c & 1;
-        if (c >= 2 && !tc::bar_wait(tc::smem_addr(&tempty[h]), ((c >> 1) - 1) & 1)) {
-          dev_fail(a.status, DEV_TIMEOUT);
-          *abort_v = 1;
-          break;
-        }
-        tc::fence_after_sync();
-        const uint32_t dbase = tmem + (uint32_t)(h * (C::COLS / 2));
-        const int i0 = c * OZ_CHUNK, i1 = min(nkb, i0 + OZ_CHUNK);
-        for (int it = i0; it < i1; ++it) {
-          const int st = it % C::STAGES, rnd = it / C::STAGES;
-          if (!tc::bar_wait(tc::smem_addr(&full[st]), rnd & 1) || *abort_v) {
+      for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+        const Item w = decode(item);
+        const int nch = (w.nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+        for (int c = 0; c < nch && ok; ++c, ++cc) {
+          const int h = cc & 1;
+          if (cc >= 2 && !tc::bar_wait(tc::smem_addr(&tempty[h]), ((cc >> 1) - 1) & 1)) {
             dev_fail(a.status, DEV_TIMEOUT);
             *abort_v = 1;
             ok = false;
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), sb = sa + C::A_BYTES;
+          const uint32_t dbase = tmem + (uint32_t)(h * (C::COLS / 2));
+          const int i0 = c * OZ_CHUNK, i1 = min(w.nkb, i0 + OZ_CHUNK);
+          for (int it = i0; it < i1; ++it, ++q) {
+            const uint32_t st = q % C::STAGES, rnd = q / C::STAGES;
+            if (!tc::bar_wait(tc::smem_addr(&full[st]), rnd & 1) || *abort_v) {
+              dev_fail(a.status, DEV_TIMEOUT);
+              *abort_v = 1;
+              ok = false;
+              break;
+            }
+            tc::fence_after_sync();
+            const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), sb = sa + C::A_BYTES;
+            const uint64_t da0 = tc::smem_desc(sa, 128, 512), db0 = tc::smem_desc(sb, 128, 512);
+            // One MMA per A slice s: a_s times the B slices b_0 .. b_{6-s} stacked as (7 - s) NT rows
+            // (slice 6 is the zero slice), written from Tensor Memory column s NT on, so the block of
+            // b_t lands in the accumulator of weight s + t.  The s = 0 MMA spans all seven weights and
+            // opens a chunk by overwriting them.
 #pragma unroll
-          for (int ks = 0; ks < OZ_BK / 16; ++ks)
+            for (int ks = 0; ks < OZ_BK / 16; ++ks)
 #pragma unroll
-            for (int s = 0; s < OZ_S; ++s)
-#pragma unroll
-              for (int t = 0; t < OZ_S; ++t) {
-                if (s + t > OZ_W) continue;
-                const int w = s + t;
-                // the first MMA into accumulator w of a chunk overwrites it
-                const bool first = it == i0 && ks == 0 && s == (w > OZ_S - 1 ? w - (OZ_S - 1) : 0);
-                tc::mma_bf16(dbase + (uint32_t)(w * NT),
-                             tc::smem_desc(sa + s * (OZ_ABLK * 2) + ks * 256, 128, 512),
-                             tc::smem_desc(sb + t * (C::BBLK * 2) + ks * 256, 128, 512), idesc, first ? 0u : 1u);
+              for (int s = 0; s < OZ_S; ++s) {
+                const bool first = it == i0 && ks == 0 && s == 0;
+                // descriptor start-address field: byte offset / 16 (no carry: shared addresses < 2^18)
+                tc::mma_bf16(dbase + (uint32_t)(s * NT), da0 + (uint64_t)((s * (OZ_ABLK * 2) + ks * 256) >> 4),
+                             db0 + (uint64_t)((ks * 256) >> 4), tc::idesc_bf16(128, (OZ_W + 1 - s) * NT),
+                             first ? 0u : 1u);
               }
-          tc::commit(tc::smem_addr(&empty[st]));
+            tc::commit(tc::smem_addr(&empty[st]));
+          }
+          if (ok) tc::commit(tc::smem_addr(&tfull[h]));
         }
-        if (ok) tc::commit(tc::smem_addr(&tfull[h]));
       }
       tc::commit(tc::smem_addr(&done));
       tc::bar_wait(tc::smem_addr(&done), 0);
     }
-  } else {  // epilogue warps: warpgroup q drains weights [q * WPG, q * WPG + WPG)
-    const int q = (warp - 2) >> 2, lq = warp & 3;
-    const int w0 = q * C::WPG;
+  } else {  // epilogue warps: warpgroup qg drains weights [qg * WPG, qg * WPG + WPG)
+    const int qg = (warp - 2) >> 2, lq = warp & 3;
+    const int w0 = qg * C::WPG;
     const int r = lq * 32 + lane;  // Tensor Memory lane = row of the tile
-    int acc[C::WPG * NT];
+    uint32_t cc = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+      const Item w = decode(item);
+      const int nch = (w.nkb + OZ_CHUNK - 1) / OZ_CHUNK;
+      int acc[C::WPG * NT];
 #pragma unroll
-    for (int x = 0; x < C::WPG * NT; ++x) acc[x] = 0;
-    for (int c = 0; c < nch; ++c) {
-      const int h = c & 1;
-      if (!tc::bar_wait(tc::smem_addr(&tfull[h]), (c >> 1) & 1) || *abort_v) {
-        if (lane == 0) dev_fail(a.status, DEV_TIMEOUT);
-        *abort_v = 1;
-        break;
-      }
-      tc::fence_after_sync();
-#pragma unroll
-      for (int wi = 0; wi < C::WPG; ++wi) {
-        if (w0 + wi >= OZ_NW) continue;  // warp-uniform
-        const uint32_t ta = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT);
-        if constexpr (NT == 16) {
-          uint32_t v[16];
-          tc::tmem_ld16(ta, v);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
-        } else {
-          uint32_t v[32];
-          tc::tmem_ld32(ta, v);
-          tc::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 32; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+      for (int x = 0; x < C::WPG * NT; ++x) acc[x] = 0;
+      for (int c = 0; c < nch; ++c, ++cc) {
+        const int h = cc & 1;
+        if (!tc::bar_wait(tc::smem_addr(&tfull[h]), (cc >> 1) & 1) || *abort_v) {
+          if (lane == 0) dev_fail(a.status, DEV_TIMEOUT);
+          *abort_v = 1;
+          break;
         }
-      }
-      tc::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) tc::bar_arrive(tc::smem_addr(&tempty[h]));
-    }
-    // every epilogue warp reaches these barriers, aborted or not
-    tc::named_sync(1, 32 * C::EPI_WARPS);
-    const bool live = *abort_v == 0;
-    // Combination without FP64 (a slow pipe on this part): per column,
-    //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3 and lo = acc_4 2^16 + acc_5 2^8 + acc_6
-    // are exact in int64 (|acc_w| < 2^31), and C = 2^(ea + eb - 38) hi + 2^(ea + eb - 62) lo.
-    long long* xch = reinterpret_cast<long long*>(smem);  // the stages are idle: every MMA has completed
-    if constexpr (C::EPI_WARPS == 8) {
-      if (q == 1 && live) {
+        tc::fence_after_sync();
 #pragma unroll
-        for (int j = 0; j < NT; ++j)
-          xch[j * 128 + r] = ((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j];  // weights 4, 5, 6
+        for (int wi = 0; wi < C::WPG; ++wi) {
+          if (w0 + wi >= OZ_NW) continue;  // warp-uniform
+          const uint32_t ta =
+              tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT);
+          if constexpr (NT == 16) {
+            uint32_t v[16];
+            tc::tmem_ld16(ta, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+          } else {
+            uint32_t v[32];
+            tc::tmem_ld32(ta, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+          }
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::bar_arrive(tc::smem_addr(&tempty[h]));
       }
-      tc::named_sync(2, 32 * C::EPI_WARPS);
-    }
-    if (q == 0 && live) {
-      const int64_t i = (int64_t)mt * 128 + r;
+      // every epilogue warp reaches this barrier; after it they agree on aborting
+      tc::named_sync(1, 32 * C::EPI_WARPS);
+      if (*abort_v) break;
+      // The weights joined exactly in int64 (|acc_w| < 2^31); the consumer adds the splits and
+      // converts (with the row / column exponents) at full occupancy:
+      //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6.
+      const int64_t i = (int64_t)w.mt * 128 + r;
       if (i < a.M) {
-        const int ei = a.ea[(int64_t)ag * a.ea_gstride + i];
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
-          const int64_t jj = (int64_t)nt * NT + j;
+          const int64_t jj = (int64_t)w.nt * NT + j;
           if (jj >= a.N) break;
-          const long long hi = (((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j]) * 256 + acc[3 * NT + j];
-          long long lo;
-          if constexpr (C::EPI_WARPS == 8)
-            lo = xch[j * 128 + r];
-          else
-            lo = ((long long)acc[4 * NT + j] * 256 + acc[5 * NT + j]) * 256 + acc[6 * NT + j];
-          const int ej = a.eb[(int64_t)g * a.eb_gstride + jj];
-          dd y;
-          if (ei == OZ_NONFINITE || ej == OZ_NONFINITE) {
-            y = dd{__int_as_float(0x7fc00000), 0.f};
+          const int64_t o = (((int64_t)w.sp * a.groups + w.g) * a.N + jj) * a.M + i;
+          if (qg == 0)
+            a.ohi[o] = (((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j]) * 256 + acc[3 * NT + j];
+          if constexpr (C::EPI_WARPS == 8) {
+            if (qg == 1) a.olo[o] = ((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j];  // weights 4..6
           } else {
-            const int sc = ei + ej;
-            dd yh = ll_to_dd(hi), yl = ll_to_dd(lo);
-            yh = dd{ldexpf(yh.hi, sc - 38), ldexpf(yh.lo, sc - 38)};
-            yl = dd{ldexpf(yl.hi, sc - 62), ldexpf(yl.lo, sc - 62)};
-            y = dd_add(yh, yl);
+            a.olo[o] = ((long long)acc[4 * NT + j] * 256 + acc[5 * NT + j]) * 256 + acc[6 * NT + j];
           }
-          DD::st(a.out, (((int64_t)sp * a.groups + g) * a.N + jj) * a.M + i, y);
         }
       }
     }
@@ -407,11 +429,22 @@ __global__ void __launch_bounds__(128) k_oz_slice_cols(CBuf X, int64_t D, int64_
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
 inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
 
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      n = 148;
+  }
+  return n;
+}
+
 template <int NT>
-cudaError_t launch_oz(const OzArgs& a, int MT, int NTL, cudaStream_t st) {
+cudaError_t launch_oz(const OzArgs& a, cudaStream_t st) {
   using C = OzCfg<NT>;
   CK(cudaFuncSetAttribute(k_oz_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
-  dim3 grid((unsigned)NTL, (unsigned)MT, (unsigned)(a.groups * a.ksplit));
+  const int64_t items = (int64_t)a.NTL * a.MT * a.groups * a.ksplit;
+  const unsigned grid = (unsigned)std::min<int64_t>(items, sm_count());  // one CTA per SM (shared memory)
   k_oz_mma<NT><<<grid, C::THREADS, C::SMEM, st>>>(a);
   return cudaGetLastError();
 }
@@ -445,7 +478,7 @@ cudaError_t oz_slice_cols(CBuf X, int64_t D, int ngroups, int64_t ncolg, int NT,
 int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap) {
   const int KB = oz_kb(D);
   const int64_t ctas = (int64_t)oz_mt(D) * ((ncolg + NT - 1) / NT) * groups;
-  int s = (int)std::max<int64_t>(1, (2 * 152 + ctas - 1) / ctas);
+  int s = (int)std::max<int64_t>(1, (sm_count() + ctas - 1) / ctas);  // about one work item per SM
   s = std::min(s, std::max(1, KB / OZ_CHUNK));            // at least one drain chunk per split
   s = std::max(s, (KB + OZ_KB_MAX - 1) / OZ_KB_MAX);     // int32 bound per CTA
   s = std::min(s, cap);
@@ -455,7 +488,7 @@ int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap) {
 
 cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
                        const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
-                       int ksplit, CBuf out, int* status, cudaStream_t st) {
+                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st) {
   OzArgs a{};
   const int KB = oz_kb(D), MT = oz_mt(D), NTL = (int)((ncolg + NT - 1) / NT);
   a.As = As;
@@ -468,15 +501,18 @@ cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm
   a.eb = eb;
   a.eb_gstride = (int64_t)NTL * NT;
   a.KB = KB;
+  a.MT = MT;
+  a.NTL = NTL;
   a.M = D;
   a.N = ncolg;
   a.groups = groups;
   a.kbper = (KB + ksplit - 1) / ksplit;
   a.ksplit = (KB + a.kbper - 1) / a.kbper;
   if (a.ksplit != ksplit || a.kbper > OZ_KB_MAX) return cudaErrorInvalidValue;
-  a.out = out;
+  a.ohi = ohi;
+  a.olo = olo;
   a.status = status;
-  return NT == 16 ? launch_oz<16>(a, MT, NTL, st) : launch_oz<32>(a, MT, NTL, st);
+  return NT == 16 ? launch_oz<16>(a, st) : launch_oz<32>(a, st);
 }
 
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max) {
