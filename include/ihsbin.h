@@ -157,6 +157,14 @@ typedef enum { IHSBIN_GRAM_AUTO = 0, IHSBIN_GRAM_SLICES = 1, IHSBIN_GRAM_FMA = 2
  *  FMA    : CUDA-core contraction in the compute mode's arithmetic. */
 typedef enum { IHSBIN_LOOP_AUTO = 0, IHSBIN_LOOP_SLICES = 1, IHSBIN_LOOP_FMA = 2 } ihsbin_loop;
 
+/* Kernel for the explicit inverse P_l = W_l^T W_l (W_l = L_l^-1) of every interval.
+ *  AUTO   : SLICES in the F32X2 compute mode, FMA otherwise.
+ *  SLICES : F32X2 compute only.  The columns of W_l are cut into exact BF16 slices and the
+ *           product runs on the tensor cores as the recursion's products do, skipping the
+ *           zero blocks of the triangular W_l and the mirrored half of the symmetric result.
+ *  FMA    : CUDA-core contraction in the compute mode's arithmetic. */
+typedef enum { IHSBIN_FACTOR_AUTO = 0, IHSBIN_FACTOR_SLICES = 1, IHSBIN_FACTOR_FMA = 2 } ihsbin_factor;
+
 typedef struct {
   double lambda_min, lambda_max;
   int32_t L;
@@ -172,6 +180,7 @@ typedef struct {
   int32_t auto_rho;
   ihsbin_gram gram;
   ihsbin_loop loop;
+  ihsbin_factor factor;
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -263,7 +272,7 @@ IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
  * is also bracketed by CUDA events on the stream it runs on and its device
  * time is added at the call's synchronisation point.  Categories 0 ..
  * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 23
+#define IHSBIN_KCAT_COUNT 25
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,

@@ -533,6 +533,12 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
     return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: the sliced tensor-core loop products take the F32X2 compute mode");
   pl.loop = d->loop == IHSBIN_LOOP_FMA ? IHSBIN_LOOP_FMA
             : d->compute == IHSBIN_COMPUTE_F32X2 ? IHSBIN_LOOP_SLICES : IHSBIN_LOOP_FMA;
+  if (d->factor != IHSBIN_FACTOR_AUTO && d->factor != IHSBIN_FACTOR_SLICES && d->factor != IHSBIN_FACTOR_FMA)
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown factor kernel");
+  if (d->factor == IHSBIN_FACTOR_SLICES && d->compute != IHSBIN_COMPUTE_F32X2)
+    return fail(IHSBIN_ERR_UNSUPPORTED, "build_basis: the sliced tensor-core inverse takes the F32X2 compute mode");
+  pl.factor = d->factor == IHSBIN_FACTOR_FMA ? IHSBIN_FACTOR_FMA
+              : d->compute == IHSBIN_COMPUTE_F32X2 ? IHSBIN_FACTOR_SLICES : IHSBIN_FACTOR_FMA;
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "build_basis");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
@@ -681,7 +687,7 @@ static const char* kcat_names[K_NCAT] = {
     "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
     "eval_coef", "eval", "sparse", "gram_slice", "gram_tc_mma", "gram_combine", "loop_slice", "loop_gram_tc",
-    "loop_precond_tc"};
+    "loop_precond_tc", "inverse_slice", "inverse_tc"};
 
 ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");

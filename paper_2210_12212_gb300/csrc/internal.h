@@ -49,6 +49,7 @@ struct Plan {
   int product = IHSBIN_PRODUCT_GRAM;
   int gram = IHSBIN_GRAM_FMA;   // resolved Gram kernel (never AUTO)
   int loop = IHSBIN_LOOP_FMA;   // resolved product kernel of the basis recursion (never AUTO)
+  int factor = IHSBIN_FACTOR_FMA;  // resolved kernel of the explicit inverse (never AUTO)
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
@@ -64,7 +65,8 @@ struct DevBuf {
 enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
-  K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_NCAT
+  K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
+  K_INVERSE_TC, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -183,6 +185,30 @@ cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm
                        const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
                        int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st);
 double oz_pair_flops(int64_t M, int64_t N, int64_t K);
+
+// General form: C_g = X_g Y_g^T (M x N, contraction K) for every group g, X sliced into 128-row
+// tiles (A operand), Y into NT-row tiles (NT = 16 or 32, B operand).  Triangular operands: zero
+// k-blocks skipped per output tile; sym: only the tiles that touch i <= j are computed.
+enum OzTri : int { OZ_TRI_GE_ROW = 1, OZ_TRI_GE_COL = 2, OZ_TRI_LE_ROW = 4 };
+struct OzGemm {
+  const __nv_bfloat16* As = nullptr;
+  const int* ea = nullptr;
+  const int* a_perm = nullptr;
+  bool a_shared = false;
+  const __nv_bfloat16* Bs = nullptr;
+  const int* eb = nullptr;
+  int64_t M = 0, N = 0, K = 0;
+  int groups = 1, NT = 32, ksplit = 1, tri = 0, sym = 0;
+  long long* ohi = nullptr;  // exact partials, entry ((s * groups + g) * N + j) * M + i
+  long long* olo = nullptr;
+  int* status = nullptr;
+};
+cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st);
+size_t oz_vec_elems(int64_t nvec, int64_t K, int TH);  // slices of nvec vectors of length K, tile height TH
+size_t oz_vec_exps(int64_t nvec, int TH);
+// vectors = the columns of row-major float-float matrices (K rows, row stride ld, group stride gs)
+cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int groups, int64_t gs, int TH,
+                             __nv_bfloat16* out, int* e, cudaStream_t st);
 // device bytes of the recursion's slices (G, every P_l, one step's B operand)
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);

@@ -743,6 +743,7 @@ __global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, C
   const int nb = (D - r0 < NB) ? (int)(D - r0) : NB;
   __shared__ V a[NB][NB + 1];
   __shared__ V inv[NB][NB + 1];
+  __shared__ V red[8][NB];
   __shared__ int bad;
   const int tid = threadIdx.x;
   if (tid == 0) bad = 0;
@@ -771,19 +772,30 @@ __global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, C
     }
     __syncthreads();
   }
-  // inverse of the lower-triangular block by forward substitution, one column per thread
-  for (int c = tid; c < NB; c += blockDim.x) {
+  // inverse of the lower-triangular block, row by row (forward substitution):
+  //   inv[i][c] = (delta_ic - sum_{c <= k < i} a[i][k] inv[k][c]) / a[i][i];
+  // thread (ks, c) = (tid / 32, tid % 32) forms the partial sum over k = c + ks, c + ks + 8, ...
+  {
+    const int c = tid & (NB - 1), ks = tid >> 5;  // blockDim.x = 256 = 8 x NB
     for (int i = 0; i < NB; ++i) {
-      if (i < c || i >= nb || c >= nb) {
-        inv[i][c] = Mode::zero();
-        continue;
+      V s = Mode::zero();
+      if (i < nb && c < i)
+        for (int k = c + ks; k < i; k += 8) s = Mode::add(s, Mode::mul(a[i][k], inv[k][c]));
+      red[ks][c] = s;
+      __syncthreads();
+      if (ks == 0) {
+        if (i < nb && c <= i) {
+          V t = Mode::zero();
+          for (int q = 0; q < 8; ++q) t = Mode::add(t, red[q][c]);
+          t = Mode::sub(c == i ? Mode::from_d(1.0) : Mode::zero(), t);
+          inv[i][c] = Mode::div(t, a[i][i]);
+        } else {
+          inv[i][c] = Mode::zero();
+        }
       }
-      V s = (i == c) ? Mode::from_d(1.0) : Mode::zero();
-      for (int k = c; k < i; ++k) s = Mode::sub(s, Mode::mul(a[i][k], inv[k][c]));
-      inv[i][c] = Mode::div(s, a[i][i]);
+      __syncthreads();
     }
   }
-  __syncthreads();
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int i = e / NB, j = e % NB;
     if (i < nb && j < nb) Mode::st(H, off + (r0 + i) * D + r0 + j, j <= i ? a[i][j] : Mode::zero());
@@ -974,6 +986,58 @@ struct LdW {  // operand (k, j) = W[k][j]
   }
 };
 
+// P_l[i][j] = P_l[j][i] (i <= j) from the exact partials of W_l^T W_l on the tensor cores
+__global__ void k_oz_store_sym(const long long* hi, const long long* lo, int S, int64_t D, int L, const int* ea,
+                               int64_t ea_gs, const int* eb, int64_t eb_gs, CBuf P) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * D * D) return;
+  const int64_t l = e / (D * D), rr = e - l * D * D, j = rr / D, i = rr - j * D;
+  if (i > j) return;
+  long long h = 0, w = 0;
+  for (int s = 0; s < S; ++s) {
+    h += hi[(int64_t)s * L * D * D + e];
+    w += lo[(int64_t)s * L * D * D + e];
+  }
+  const dd v = oz_join(h, w, ea[l * ea_gs + i], eb[l * eb_gs + j]);
+  DD::st(P, l * D * D + j * D + i, v);
+  DD::st(P, l * D * D + i * D + j, v);
+}
+
+// P_l = W_l^T W_l on the tensor cores: X = Y = W_l^T (vectors = the columns of W_l), k >= max(i, j)
+static cudaError_t inverse_slices(ihsbin_problem* p, CBuf Wm, cudaStream_t st) {
+  const int64_t D = p->A.D;
+  const int L = p->plan.L;
+  __nv_bfloat16 *As = nullptr, *Bs = nullptr;
+  int *ea = nullptr, *eb = nullptr;
+  long long *hi = nullptr, *lo = nullptr;
+  CK(prob_alloc(p, oz_vec_elems(D, D, 128) * 2 * L, (void**)&As, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(D, 128) * 4 * L, (void**)&ea, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_elems(D, D, 32) * 2 * L, (void**)&Bs, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(D, 32) * 4 * L, (void**)&eb, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)L * D * D * 8, (void**)&hi, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)L * D * D * 8, (void**)&lo, SCOPE_SCRATCH));
+  {
+    KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * D * D * 8 * 2 + (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2);
+    CK(oz_slice_matcols(Wm, D, D, D, L, D * D, 128, As, ea, st));
+    CK(oz_slice_matcols(Wm, D, D, D, L, D * D, 32, Bs, eb, st));
+  }
+  {
+    OzGemm q;
+    q.As = As; q.ea = ea; q.Bs = Bs; q.eb = eb;
+    q.M = D; q.N = D; q.K = D; q.groups = L; q.NT = 32; q.ksplit = 1;
+    q.tri = OZ_TRI_GE_ROW | OZ_TRI_GE_COL;
+    q.sym = 1;
+    q.ohi = hi; q.olo = lo; q.status = p->status;
+    KTimer kt(p, K_INVERSE_TC, st, oz_pair_flops(1, 1, 1) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
+              (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2 + (double)L * D * D * 16);
+    CK(oz_gemm(q, st));
+  }
+  KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * D * D * (16 + 16));
+  k_oz_store_sym<<<nblocks((int64_t)L * D * D, 256), 256, 0, st>>>(hi, lo, 1, D, L, ea, (int64_t)oz_vec_exps(D, 128), eb,
+                                                                 (int64_t)oz_vec_exps(D, 32), p->Pinv);
+  return cudaGetLastError();
+}
+
 template <class Mode>
 static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf dinv, const double* lam0_dev,
                                      cudaStream_t st) {
@@ -1019,6 +1083,7 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
     CK(trtri_doubling<Mode>(p, H, dinv, Wm, Tm, L, st));
   }
   // P_l = W^T W  (W lower triangular: the sum starts at k = max(i, j))
+  if (Mode::id == 1 && p->plan.factor == IHSBIN_FACTOR_SLICES) return inverse_slices(p, Wm, st);
   GemmShape sh{D, D, D, 1};
   sh.kdiag = 1;
   KTimer kt(p, K_INVERSE, st, (double)L * D * (D + 1) * (D + 2) / 3.0, (double)L * D * D * cs * 2);

@@ -93,6 +93,10 @@ uint64_t request_footprint(const ihsbin_request* q) {
   // slices of the tensor-core products of the recursion (float-float compute)
   if (pd.compute == IHSBIN_COMPUTE_F32X2 && pd.loop != IHSBIN_LOOP_FMA)
     bytes += (double)loop_slices_bytes((int64_t)D, (int)L, (int64_t)(jc * K));
+  // slices and exact partials of the tensor-core inverse W^T W
+  if (pd.compute == IHSBIN_COMPUTE_F32X2 && pd.factor != IHSBIN_FACTOR_FMA)
+    bytes += L * (2.0 * (oz_vec_elems((int64_t)D, (int64_t)D, 128) + oz_vec_elems((int64_t)D, (int64_t)D, 32)) +
+                  16.0 * D * D);
   // integer slices and tiles of the tensor-core Gram (dense FP32/BF16 data)
   if (A.layout == IHSBIN_DENSE_ROWMAJOR && A.dtype != IHSBIN_F64 && pd.gram != IHSBIN_GRAM_FMA &&
       pd.product != IHSBIN_PRODUCT_ASPACE)

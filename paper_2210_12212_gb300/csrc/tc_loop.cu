@@ -84,6 +84,8 @@ struct OzArgs {
   int MT, NTL;           // row tiles, column tiles per group
   int64_t M, N;          // valid rows, valid columns per group
   int groups, ksplit, kbper;
+  int tri;               // OZ_TRI_* flags: zero blocks of triangular operands skipped per tile
+  int sym;               // 1: only tiles that touch i <= j (symmetric result)
   long long* ohi;        // exact partials (weights 0..3 / 4..6), entry ((s * groups + g) * N + j) * M + i
   long long* olo;
   int* status;
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
 
   struct Item {
     int nt, mt, g, sp, ag, kb0, nkb;
+    bool skip;
   };
   auto decode = [&](int item) {
     Item w;
@@ -115,7 +118,12 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
     w.g = r / a.ksplit;
     w.ag = a.a_perm ? a.a_perm[w.g] : w.g;
     w.kb0 = w.sp * a.kbper;
-    w.nkb = min(a.KB, w.kb0 + a.kbper) - w.kb0;
+    int kb1 = min(a.KB, w.kb0 + a.kbper);
+    if (a.tri & OZ_TRI_GE_ROW) w.kb0 = max(w.kb0, (w.mt * 128) / OZ_BK);         // k >= the tile's first row
+    if (a.tri & OZ_TRI_GE_COL) w.kb0 = max(w.kb0, (w.nt * NT) / OZ_BK);          // k >= its first column
+    if (a.tri & OZ_TRI_LE_ROW) kb1 = min(kb1, (w.mt * 128 + 127) / OZ_BK + 1);   // k <= its last row
+    w.skip = a.sym && w.mt * 128 > w.nt * NT + NT - 1;                          // entirely below the diagonal
+    w.nkb = w.skip ? 0 : max(0, kb1 - w.kb0);
     return w;
   };
 
@@ -274,7 +282,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
       // converts (with the row / column exponents) at full occupancy:
       //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6.
       const int64_t i = (int64_t)w.mt * 128 + r;
-      if (i < a.M) {
+      if (i < a.M && !w.skip) {
 #pragma unroll
         for (int j = 0; j < NT; ++j) {
           const int64_t jj = (int64_t)w.nt * NT + j;
@@ -426,6 +434,53 @@ __global__ void __launch_bounds__(128) k_oz_slice_cols(CBuf X, int64_t D, int64_
   }
 }
 
+// Vectors = the columns of row-major float-float matrices (group stride gs, row stride ld), K rows
+// each: CTA (32 x 8 threads) per 32 columns; a column's maximum from its 8 threads, then thread
+// (x, y) cuts rows 8c .. 8c+7 (c = y, y + 8, ...) of column x (loads coalesced across x).
+// Layout as k_oz_slice_cols with tile height TH.
+__global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int64_t gs,
+                                                          int TH, int NTL, int KB, __nv_bfloat16* out, int* e) {
+  __shared__ float red[8][33];
+  __shared__ int ex[32];
+  const int x = threadIdx.x, y = threadIdx.y, g = blockIdx.y;
+  const int64_t v = (int64_t)blockIdx.x * 32 + x;
+  const bool valid = v < nvec;
+  const float* xh = (const float*)X.p0 + (int64_t)g * gs;
+  const float* xl = (const float*)X.p1 + (int64_t)g * gs;
+  float m = 0.f;
+  if (valid)
+    for (int64_t k = y; k < K; k += 8) {
+      const float a = fabsf(xh[k * ld + v]);
+      m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+    }
+  red[y][x] = m;
+  __syncthreads();
+  if (y == 0) {
+    float mm = red[0][x];
+    for (int q = 1; q < 8; ++q) mm = fmaxf(mm, red[q][x]);
+    ex[x] = oz_exp(mm);
+    if (v < (int64_t)NTL * TH) e[(int64_t)g * NTL * TH + v] = ex[x];
+  }
+  __syncthreads();
+  if (v >= (int64_t)NTL * TH) return;
+  const int ev = ex[x];
+  const bool live = valid && ev != OZ_NONFINITE;
+  const int tile = (int)(v / TH), nl = (int)(v - (int64_t)tile * TH);
+  const int64_t bblk = (int64_t)TH * OZ_BK;
+  for (int c = y; c < KB * 4; c += 8) {
+    const int kb = c >> 2, kc = c & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)c * 8 + q;
+      h[q] = (live && k < K) ? xh[k * ld + v] : 0.f;
+      l[q] = (live && k < K) ? xl[k * ld + v] : 0.f;
+    }
+    store_digits(h, l, ev, live, out + ((((int64_t)g * NTL + tile) * KB + kb) * OZ_S) * bblk +
+                                    ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+  }
+}
+
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
 inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
 
@@ -486,33 +541,59 @@ int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap) {
   return (KB + kbper - 1) / kbper;                        // every split non-empty
 }
 
-cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
-                       const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
-                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st) {
+cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   OzArgs a{};
-  const int KB = oz_kb(D), MT = oz_mt(D), NTL = (int)((ncolg + NT - 1) / NT);
-  a.As = As;
-  a.a_gstride = a_shared ? 0 : (int64_t)oz_rows_elems(D);
-  a.a_perm = a_perm;
-  a.ea = ea;
-  a.ea_gstride = a_shared ? 0 : (int64_t)oz_rows_exps(D);
-  a.Bs = Bs;
-  a.b_gstride = (int64_t)oz_cols_elems(D, ncolg, NT);
-  a.eb = eb;
-  a.eb_gstride = (int64_t)NTL * NT;
+  const int KB = (int)((q.K + OZ_BK - 1) / OZ_BK), MT = (int)((q.M + 127) / 128);
+  const int NTL = (int)((q.N + q.NT - 1) / q.NT);
+  if (q.NT != 16 && q.NT != 32) return cudaErrorInvalidValue;
+  a.As = q.As;
+  a.a_gstride = q.a_shared ? 0 : (int64_t)oz_vec_elems(q.M, q.K, 128);
+  a.a_perm = q.a_perm;
+  a.ea = q.ea;
+  a.ea_gstride = q.a_shared ? 0 : (int64_t)oz_vec_exps(q.M, 128);
+  a.Bs = q.Bs;
+  a.b_gstride = (int64_t)oz_vec_elems(q.N, q.K, q.NT);
+  a.eb = q.eb;
+  a.eb_gstride = (int64_t)oz_vec_exps(q.N, q.NT);
   a.KB = KB;
   a.MT = MT;
   a.NTL = NTL;
-  a.M = D;
-  a.N = ncolg;
-  a.groups = groups;
-  a.kbper = (KB + ksplit - 1) / ksplit;
+  a.M = q.M;
+  a.N = q.N;
+  a.groups = q.groups;
+  a.kbper = (KB + q.ksplit - 1) / q.ksplit;
   a.ksplit = (KB + a.kbper - 1) / a.kbper;
-  if (a.ksplit != ksplit || a.kbper > OZ_KB_MAX) return cudaErrorInvalidValue;
-  a.ohi = ohi;
-  a.olo = olo;
-  a.status = status;
-  return NT == 16 ? launch_oz<16>(a, st) : launch_oz<32>(a, st);
+  if (a.ksplit != q.ksplit || a.kbper > OZ_KB_MAX) return cudaErrorInvalidValue;
+  a.tri = q.tri;
+  a.sym = q.sym;
+  a.ohi = q.ohi;
+  a.olo = q.olo;
+  a.status = q.status;
+  return q.NT == 16 ? launch_oz<16>(a, st) : launch_oz<32>(a, st);
+}
+
+cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
+                       const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
+                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st) {
+  OzGemm q;
+  q.As = As; q.ea = ea; q.a_perm = a_perm; q.a_shared = a_shared;
+  q.Bs = Bs; q.eb = eb;
+  q.M = D; q.N = ncolg; q.K = D; q.groups = groups; q.NT = NT; q.ksplit = ksplit;
+  q.ohi = ohi; q.olo = olo; q.status = status;
+  return oz_gemm(q, st);
+}
+
+size_t oz_vec_elems(int64_t nvec, int64_t K, int TH) {
+  return (size_t)((nvec + TH - 1) / TH) * ((K + OZ_BK - 1) / OZ_BK) * OZ_S * TH * OZ_BK;
+}
+size_t oz_vec_exps(int64_t nvec, int TH) { return (size_t)((nvec + TH - 1) / TH) * TH; }
+
+cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int groups, int64_t gs, int TH,
+                             __nv_bfloat16* out, int* e, cudaStream_t st) {
+  const int NTL = (int)((nvec + TH - 1) / TH);
+  dim3 grid((unsigned)((NTL * TH + 31) / 32), (unsigned)groups), blk(32, 8);
+  k_oz_slice_matcols<<<grid, blk, 0, st>>>(X, ld, K, nvec, gs, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out, e);
+  return cudaGetLastError();
 }
 
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max) {

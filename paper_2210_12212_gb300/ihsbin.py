@@ -34,6 +34,7 @@ PRODUCT = {"auto": PRODUCT_AUTO, "gram": PRODUCT_GRAM, "aspace": PRODUCT_ASPACE}
 GRAM_AUTO, GRAM_SLICES, GRAM_FMA = 0, 1, 2
 GRAM = {"auto": GRAM_AUTO, "slices": GRAM_SLICES, "fma": GRAM_FMA}
 LOOP = {"auto": 0, "slices": 1, "fma": 2}
+FACTOR = {"auto": 0, "slices": 1, "fma": 2}
 
 
 class IhsbinError(RuntimeError):
@@ -57,7 +58,7 @@ class PathDesc(C.Structure):
                 ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
                 ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
-                ("gram", C.c_int), ("loop", C.c_int)]
+                ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int)]
 
 
 class Request(C.Structure):
@@ -80,7 +81,7 @@ EXPORTED = [
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
 ]
-KCAT_COUNT = 23
+KCAT_COUNT = 25
 
 
 def load(path: Optional[str] = None):
@@ -223,10 +224,10 @@ class Problem:
                     rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
                     eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", loop: str = "auto",
-                    stream=None):
+                    factor: str = "auto", stream=None):
         """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
-        gram / loop select the Gram kernel and the recursion's product kernel ("auto", "slices" =
-        tensor-core exact slices, "fma" = CUDA cores)."""
+        gram / loop / factor select the Gram kernel, the recursion's product kernel and the inverse's
+        product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
         pd = PathDesc()
         pd.lambda_min, pd.lambda_max, pd.L = lambda_min, lambda_max, L
         ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
@@ -240,6 +241,7 @@ class Problem:
         pd.eps, pd.auto_rho = eps, int(auto_rho)
         pd.gram = GRAM[gram]
         pd.loop = LOOP[loop]
+        pd.factor = FACTOR[factor]
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def eval_path(self, lambdas, out=None, x_dtype: str = "f64", stream=None):

@@ -85,3 +85,23 @@ def test_loop_slices_refused_outside_f32x2(ctx):
         gp.build_basis(prob.lambda_min, prob.lambda_max, L=1, k_default=2, compute="f64", loop="slices")
     assert e.value.status == ihs.ERR_UNSUPPORTED
     gp.close()
+
+
+@pytest.mark.parametrize("name,k", [("c2_small", 40), ("c4_small", 30), ("c1_small", 30)])
+def test_inverse_slices_match_fma(ctx, name, k):
+    """P_l = W_l^T W_l on the tensor cores (triangular and symmetric blocks skipped) against the
+    float-float CUDA-core product, through the whole path."""
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small(name)
+    L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
+    r1, r2, kk = default_params(prob, L, k)
+    out = {}
+    for factor in ("slices", "fma"):
+        gp = gpu_problem(ihs, ctx, prob)
+        gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
+        gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute="f32x2", factor=factor)
+        out[factor] = gp.eval_path(prob.lambdas)
+        gp.close()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L)
+    assert rel_err_max(out["slices"], _oracle(prob, plan).X) <= 1e-10
+    assert rel_err_max(out["slices"], out["fma"]) <= 1e-10
