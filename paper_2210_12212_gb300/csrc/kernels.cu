@@ -232,18 +232,6 @@ __global__ void k_reduce_sym(CBuf part, int S, int64_t D, CBuf out) {
   Mode::st(out, i * D + j, v);
   Mode::st(out, j * D + i, v);
 }
-// float-float partials of a symmetric D x D result into an FP64 matrix
-__global__ void k_reduce_sym_to_f64(CBuf part, int S, int64_t D, double* out) {
-  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= D * D) return;
-  int64_t i = e / D, j = e % D;
-  if (i > j) return;
-  dd v = DD::ld(part, j * D + i);
-  for (int s = 1; s < S; ++s) v = dd_add(v, DD::ld(part, ((int64_t)s * D + j) * D + i));
-  const double x = dd_to_double(v);
-  out[i * D + j] = x;
-  out[j * D + i] = x;
-}
 
 // column-major M x N result (one group) from S partials
 template <class Mode>
@@ -689,32 +677,9 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
 }
 
 // G_S = (S A_hat)^T (S A_hat) in FP64 (the sketched Hessian without the shift).
-cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) {
-  const int64_t m = p->sk.m, D = p->A.D;
-  const int64_t tm = (D + 63) / 64;
-  GemmShape sh{D, D, m, 1};
-  sh.ksplit = pick_split(tm * (tm + 1) / 2, m, 16);
-  KTimer kt(p, K_SKETCH_GRAM, st, (double)m * D * (D + 1), (double)m * D * 8 + (double)D * D * 8);
-  if (sh.ksplit == 1)
-    return launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
-                                               EpStoreSymF64{p->GS, D}, st);
-  if (p->A.elem != ELEM_F64) {
-    // float-float: SA split exactly into hi + lo floats, products and sums at ~44 bits
-    cudaError_t err = cudaSuccess;
-    CBuf part = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)sh.ksplit * D * D, SCOPE_SCRATCH, &err);
-    CK(err);
-    CK((launch_gemm<DD, 64, 64, 16, 4, 4>(sh, 1, LdTrans<DD, ELEM_F64>{p->SA, D}, LdRowB<DD, ELEM_F64>{p->SA, D},
-                                          EpPartial<DD>{part, D, D, 1}, st)));
-    k_reduce_sym_to_f64<<<nblocks(D * D, 256), 256, 0, st>>>(part, sh.ksplit, D, p->GS);
-    return cudaGetLastError();
-  }
-  CBuf part;
-  CK(prob_alloc(p, (size_t)sh.ksplit * D * D * 8, &part.p0, SCOPE_SCRATCH));
-  CK((launch_gemm<F64, 64, 64, 16, 4, 4>(sh, 1, LdTrans<F64, ELEM_F64>{p->SA, D}, LdRowB<F64, ELEM_F64>{p->SA, D},
-                                          EpPartial<F64>{part, D, D, 1}, st)));
-  k_reduce_sym<F64><<<nblocks(D * D, 256), 256, 0, st>>>(part, sh.ksplit, D, CBuf{p->GS, nullptr});
-  return cudaGetLastError();
-}
+// The sketched Gram G_S = (S A_hat)^T (S A_hat): on the tensor cores from exact slices of the FP64
+// sketch (tc_gram.cu).
+cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st) { return sketch_gram_slices(p, st); }
 
 // ======================================================= a2: factor and inverse
 // H_l = G_S + lam0_l I in compute precision, for every interval l.

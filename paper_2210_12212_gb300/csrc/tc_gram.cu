@@ -90,7 +90,14 @@ __global__ void k_col_absmax(const void* A, int64_t ld, int64_t N, int64_t D, un
   float m = 0.f;
   bool bad = false;
   for (int64_t k = blockIdx.y; k < N; k += gridDim.y) {
-    const float a = fabsf(load_f<ET>(A, k * ld + j));
+    float a;
+    if (ET == ELEM_F64) {
+      const double x = fabs(((const double*)A)[k * ld + j]);
+      bad |= !(x <= 1.0e38);
+      a = __double2float_ru(x);  // rounded up: every |entry| stays below 2^e of the float maximum
+    } else {
+      a = fabsf(load_f<ET>(A, k * ld + j));
+    }
     bad |= !(a <= 3.402823466e38f);
     m = fmaxf(m, a);
   }
@@ -109,6 +116,30 @@ __global__ void k_slice(const void* A, int64_t ld, int64_t N, int64_t D, const u
   const bool live = j < D && e != SL_NONFINITE;
   if (!live) e = 0;
   const int r = (int)(j & 127), rb = (int)(j >> 7);
+  if (ET == ELEM_F64) {  // FP64 data: the digits in double arithmetic (53-bit entries, up to 7 slices)
+    for (int64_t k8 = blockIdx.y; k8 < (int64_t)KB * 8; k8 += gridDim.y) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t k = k8 * 8 + q;
+        v[q] = (live && k < N) ? ldexp(((const double*)A)[k * ld + j], 7 - e) : 0.0;  // exact, |v| < 2^7
+      }
+      const int64_t kb = k8 >> 3, kc = k8 & 7;
+      const int64_t off = ((r >> 3) * 1024 + kc * 128 + (r & 7) * 16) / 2;
+      for (int t = 0; t < ns; ++t) {
+        __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const double a = rint(v[q]);
+          h[q] = __float2bfloat16_rn((float)a);
+          v[q] = (v[q] - a) * 256.0;
+        }
+        *reinterpret_cast<uint4*>(S + (((int64_t)t * RB + rb) * KB + kb) * SL_BLOCK_ELEMS + off) =
+            *reinterpret_cast<const uint4*>(h);
+      }
+    }
+    return;
+  }
   for (int64_t k8 = blockIdx.y; k8 < (int64_t)KB * 8; k8 += gridDim.y) {
     float v[8];
 #pragma unroll
@@ -352,11 +383,16 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
   return pl;
 }
 
+// G = X^T X for X (N x D, row-major, row stride ld, element type ET) into `G` (Mode precision):
+// ns slices per entry, pairs s + t <= wmax.
 template <class Mode, int ET>
-cudaError_t gram_slices_typed(ihsbin_problem* p, cudaStream_t st) {
-  const Tall& A = p->A;
-  const int64_t N = A.N, D = A.D;
-  const SlicePlan pl = make_slice_plan(N, D, kGramSlices, kGramMaxWeight);
+cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int64_t N, int64_t D, int ns, int wmax,
+                              CBuf G, int cat_slice, int cat_tc, int cat_combine, cudaStream_t st) {
+  struct {
+    const void* A;
+    int64_t ld;
+  } A{X, ld};
+  const SlicePlan pl = make_slice_plan(N, D, ns, wmax);
   const int items = pl.base[pl.np];
   unsigned* cmax = nullptr;
   __nv_bfloat16* S = nullptr;
@@ -365,15 +401,15 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, cudaStream_t st) {
   CK(prob_alloc(p, (size_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2, (void**)&S, SCOPE_SCRATCH));
   CK(prob_alloc(p, (size_t)items * 16384 * sizeof(int), (void**)&out, SCOPE_SCRATCH));
   CK(cudaMemsetAsync(cmax, 0, (size_t)D * sizeof(unsigned), st));
-  const size_t es = ET == ELEM_F32 ? 4 : 2;
+  const size_t es = ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2;
   {
-    KTimer kt(p, K_GRAM_SLICE, st, 0, (double)N * D * es);
+    KTimer kt(p, cat_slice, st, 0, (double)N * D * es);
     const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, N / 64), 1024);
     k_col_absmax<ET><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(A.A, A.ld, N, D, cmax);
     CK(cudaGetLastError());
   }
   {
-    KTimer kt(p, K_GRAM_SLICE, st, 0, (double)N * D * es + (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2);
+    KTimer kt(p, cat_slice, st, 0, (double)N * D * es + (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2);
     const unsigned gy = (unsigned)std::min<int64_t>((int64_t)pl.KB * 8, 32768);
     k_slice<ET><<<dim3((unsigned)pl.RB, gy), 128, 0, st>>>(A.A, A.ld, N, D, cmax, pl.ns, pl.RB, pl.KB, S);
     CK(cudaGetLastError());
@@ -382,16 +418,16 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, cudaStream_t st) {
     // algorithmic BF16 work of the slice products (unpadded): 2 N per output entry and pair
     double fl = 0;
     for (int q = 0; q < pl.np; ++q) fl += 2.0 * N * (pl.ps[q] == pl.pt[q] ? D * (D + 1) / 2.0 : (double)D * D);
-    KTimer kt(p, K_GRAM_TC, st, fl, (double)items * pl.kbper * SL_STAGE_BYTES + (double)items * 65536);
+    KTimer kt(p, cat_tc, st, fl, (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536);
     const int smem = SL_STAGES * SL_STAGE_BYTES;
     CK(cudaFuncSetAttribute(k_gram_slices_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_gram_slices_tc<<<(unsigned)items, SL_THREADS, smem, st>>>(S, pl, out, p->status);
     CK(cudaGetLastError());
   }
   {
-    KTimer kt(p, K_GRAM_COMBINE, st, 0, (double)items * 65536 + (double)D * D * 8);
+    KTimer kt(p, cat_combine, st, 0, (double)items * 65536 + (double)D * D * 8);
     const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, D), 1024);
-    k_gram_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(out, pl, cmax, p->G);
+    k_gram_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(out, pl, cmax, G);
     CK(cudaGetLastError());
   }
   return cudaSuccess;
@@ -400,10 +436,24 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, cudaStream_t st) {
 }  // namespace
 
 cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st) {
-  const int et = p->A.elem;
+  const Tall& A = p->A;
+  const int et = A.elem;
+  const int cs = K_GRAM_SLICE, ct = K_GRAM_TC, cc = K_GRAM_COMBINE;
   if (compute == IHSBIN_COMPUTE_F64)
-    return et == ELEM_F32 ? gram_slices_typed<F64, ELEM_F32>(p, st) : gram_slices_typed<F64, ELEM_BF16>(p, st);
-  return et == ELEM_F32 ? gram_slices_typed<DD, ELEM_F32>(p, st) : gram_slices_typed<DD, ELEM_BF16>(p, st);
+    return et == ELEM_F32
+               ? gram_slices_typed<F64, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st)
+               : gram_slices_typed<F64, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st);
+  return et == ELEM_F32
+             ? gram_slices_typed<DD, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st)
+             : gram_slices_typed<DD, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st);
+}
+
+// G_S = (S A_hat)^T (S A_hat) of the FP64 sketch: seven slices (55 bits) and pairs s + t <= 7, so
+// every entry of S A_hat within 2^-48 of its column's largest magnitude is exact and the result
+// matches the exact Gram to about FP64 rounding.
+cudaError_t sketch_gram_slices(ihsbin_problem* p, cudaStream_t st) {
+  return gram_slices_typed<F64, ELEM_F64>(p, p->SA, p->A.D, p->sk.m, p->A.D, 7, 7, CBuf{p->GS, nullptr},
+                                          K_SKETCH_GRAM, K_SKETCH_GRAM, K_SKETCH_GRAM, st);
 }
 
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D) {
