@@ -66,7 +66,7 @@ enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
   K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
-  K_INVERSE_TC, K_NCAT
+  K_INVERSE_TC, K_TRTRI_TC, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -211,6 +211,10 @@ size_t oz_vec_exps(int64_t nvec, int TH);
 // vectors = the columns of row-major float-float matrices (K rows, row stride ld, group stride gs)
 cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int groups, int64_t gs, int TH,
                              __nv_bfloat16* out, int* e, cudaStream_t st);
+// vectors with contiguous entries: vector v of group g at g * gs + off + v * vstride, K entries
+cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K, int64_t nvec, int groups,
+                          int TH, __nv_bfloat16* out, int* e, cudaStream_t st);
+int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int cap);
 // device bytes of the recursion's slices (G, every P_l, one step's B operand)
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);

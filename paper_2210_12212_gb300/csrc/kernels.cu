@@ -904,14 +904,15 @@ struct EpPairOff {  // W[r0 + s + i][r0 + j] = -acc
 };
 
 template <class Mode>
-static cudaError_t trtri_doubling(ihsbin_problem* p, CBuf H, CBuf dinv, CBuf Wm, CBuf Tm, int L, cudaStream_t st) {
+static cudaError_t trtri_doubling(ihsbin_problem* p, CBuf H, CBuf dinv, CBuf Wm, CBuf Tm, int L, int64_t smax,
+                                  cudaStream_t st) {
   const int64_t D = p->A.D;
   {
     KTimer kt(p, K_TRTRI, st, 0, (double)L * D * D * 8);
     k_wdiag<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(dinv, D, Wm);
     CK(cudaGetLastError());
   }
-  for (int64_t s = NB; s < D; s *= 2) {
+  for (int64_t s = NB; s < D && s < smax; s *= 2) {
     const int npairs = (int)((D + 2 * s - 1) / (2 * s));
     // pairs whose lower block starts beyond D contribute nothing (loaders return zeros, stores are skipped)
     const int groups = npairs * L;
@@ -950,6 +951,101 @@ struct LdW {  // operand (k, j) = W[k][j]
     return Mode::ld(Wm, (int64_t)g * D * D + k * D + j);
   }
 };
+
+// ---- W = L^-1 with the tensor cores: doubling on CUDA cores up to the 128 x 128 diagonal blocks,
+// then the block columns J (128 wide) from right to left, with R the rows below J:
+//   W_RJ = -W_RR (L_RJ W_JJ),
+// W_RR being complete when J is reached.  T = L_RJ W_JJ is a float-float contraction; W_RR T is
+// an exact-slice product (rows of W_RR against the columns of T), W_RR lower triangular.
+template <class Mode>
+struct LdBlockB {  // operand (k, j) = M[g][r0 + k][c0 + j]
+  using T = typename Mode::V;
+  static constexpr bool k_contig = false;
+  CBuf M;
+  int64_t D, r0, c0;
+  __device__ __forceinline__ T operator()(int g, int64_t k, int64_t j) const {
+    return Mode::ld(M, (int64_t)g * D * D + (r0 + k) * D + c0 + j);
+  }
+};
+template <class Mode>
+struct EpStoreRowMajor {  // out[g * gs + i * ld + j]
+  CBuf M;
+  int64_t ld, gs;
+  __device__ __forceinline__ void operator()(int g, int, int64_t i, int64_t j, typename Mode::V a) const {
+    Mode::st(M, (int64_t)g * gs + i * ld + j, Mode::renorm(a));
+  }
+};
+// W[g][R0 + i][J0 + j] = -(W_RR T)_ij from the exact split partials (M = |R| rows, N = 128 columns)
+__global__ void k_oz_store_wblock(const long long* hi, const long long* lo, int S, int64_t M, int64_t N, int L,
+                                  const int* ex, int64_t exg, const int* ey, int64_t eyg, int64_t D, int64_t R0,
+                                  int64_t J0, CBuf W) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * M * N) return;
+  const int64_t i = e % M, j = (e / M) % N, g = e / (M * N);
+  long long h = 0, w = 0;
+  for (int s = 0; s < S; ++s) {
+    h += hi[(int64_t)s * L * M * N + e];
+    w += lo[(int64_t)s * L * M * N + e];
+  }
+  const dd v = oz_join(h, w, ex[g * exg + i], ey[g * eyg + j]);
+  DD::st(W, g * D * D + (R0 + i) * D + J0 + j, dd_neg(v));
+}
+
+static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaStream_t st) {
+  const int64_t D = p->A.D, B = 128;
+  const int L = p->plan.L;
+  const int nbk = (int)((D + B - 1) / B);
+  if (nbk < 2) return cudaSuccess;
+  const int64_t nRmax = D - B;
+  size_t hmax = 1;  // the largest split partials of any step
+  for (int j = nbk - 2; j >= 0; --j) {
+    const int64_t nR = D - (int64_t)(j + 1) * B;
+    hmax = std::max(hmax, (size_t)oz_pick_split_mnk(nR, B, nR, L, 32, 16) * L * nR * B);
+  }
+  cudaError_t err = cudaSuccess;
+  CBuf T = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)L * nRmax * B, SCOPE_SCRATCH, &err);
+  CK(err);
+  __nv_bfloat16 *Xs = nullptr, *Ys = nullptr;
+  int *ex = nullptr, *ey = nullptr;
+  long long *hi = nullptr, *lo = nullptr;
+  CK(prob_alloc(p, oz_vec_elems(nRmax, nRmax, 128) * 2 * L, (void**)&Xs, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(nRmax, 128) * 4 * L, (void**)&ex, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_elems(B, nRmax, 32) * 2 * L, (void**)&Ys, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(B, 32) * 4 * L, (void**)&ey, SCOPE_SCRATCH));
+  CK(prob_alloc(p, hmax * 8, (void**)&hi, SCOPE_SCRATCH));
+  CK(prob_alloc(p, hmax * 8, (void**)&lo, SCOPE_SCRATCH));
+  for (int j = nbk - 2; j >= 0; --j) {
+    const int64_t J0 = (int64_t)j * B, R0 = J0 + B, nR = D - R0;
+    {
+      KTimer kt(p, K_TRTRI, st, 2.0 * L * nR * B * B, (double)L * (nR * B + B * B + nR * B) * 8);
+      CK((launch_gemm<DD, 64, 64, 16, 4, 4>(GemmShape{nR, B, B, 0}, L, LdPanel<DD>{H, D, R0, J0},
+                                            LdBlockB<DD>{Wm, D, J0, J0}, EpStoreRowMajor<DD>{T, B, nR * B}, st)));
+    }
+    {
+      KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * (nR * nR + nR * B) * 20);
+      CK(oz_slice_vecs(Wm, D * D, R0 * D + R0, D, nR, nR, L, 128, Xs, ex, st));
+      CK(oz_slice_matcols(T, B, nR, B, L, nR * B, 32, Ys, ey, st));
+    }
+    const int S = oz_pick_split_mnk(nR, B, nR, L, 32, 16);
+    {
+      OzGemm q;
+      q.As = Xs; q.ea = ex; q.Bs = Ys; q.eb = ey;
+      q.M = nR; q.N = B; q.K = nR; q.groups = L; q.NT = 32; q.ksplit = S;
+      q.tri = OZ_TRI_LE_ROW;
+      q.ohi = hi; q.olo = lo; q.status = p->status;
+      KTimer kt(p, K_TRTRI_TC, st, oz_pair_flops(1, 1, 1) * L * (nR * (nR + 1.0) / 2.0) * B,
+                (double)L * (oz_vec_elems(nR, nR, 128) + oz_vec_elems(B, nR, 32)) * 2 + 16.0 * S * L * nR * B);
+      CK(oz_gemm(q, st));
+    }
+    {
+      KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * nR * B * (16.0 * S + 8));
+      k_oz_store_wblock<<<nblocks((int64_t)L * nR * B, 256), 256, 0, st>>>(
+          hi, lo, S, nR, B, L, ex, (int64_t)oz_vec_exps(nR, 128), ey, (int64_t)oz_vec_exps(B, 32), D, R0, J0, Wm);
+      CK(cudaGetLastError());
+    }
+  }
+  return cudaSuccess;
+}
 
 // P_l[i][j] = P_l[j][i] (i <= j) from the exact partials of W_l^T W_l on the tensor cores
 __global__ void k_oz_store_sym(const long long* hi, const long long* lo, int S, int64_t D, int L, const int* ea,
@@ -1045,7 +1141,9 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
     CBuf Tm = alloc_cbuf(p, Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2, (size_t)L * tmax,
                          SCOPE_SCRATCH, &err);
     CK(err);
-    CK(trtri_doubling<Mode>(p, H, dinv, Wm, Tm, L, st));
+    const bool sweep = Mode::id == 1 && p->plan.factor == IHSBIN_FACTOR_SLICES;
+    CK(trtri_doubling<Mode>(p, H, dinv, Wm, Tm, L, sweep ? 128 : D, st));
+    if (sweep) CK(trtri_sweep_slices(p, H, Wm, st));
   }
   // P_l = W^T W  (W lower triangular: the sum starts at k = max(i, j))
   if (Mode::id == 1 && p->plan.factor == IHSBIN_FACTOR_SLICES) return inverse_slices(p, Wm, st);

@@ -481,6 +481,45 @@ __global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, in
   }
 }
 
+// Vectors with contiguous entries: vector v < nvec of group g starts at g * gs + off + v * vstride
+// and has K entries.  One CTA of 128 threads per vector (padded to NTL * TH per group); layout as
+// k_oz_slice_cols with tile height TH.
+__global__ void __launch_bounds__(128) k_oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K,
+                                                       int64_t nvec, int TH, int NTL, int KB, __nv_bfloat16* out,
+                                                       int* e) {
+  __shared__ float red[4];
+  const int64_t v = blockIdx.x;
+  const int g = blockIdx.y;
+  const bool valid = v < nvec;
+  const int64_t base = (int64_t)g * gs + off + (valid ? v : 0) * vstride;
+  const float* xh = (const float*)X.p0 + base;
+  const float* xl = (const float*)X.p1 + base;
+  float m = 0.f;
+  if (valid)
+    for (int64_t k = threadIdx.x; k < K; k += 128) {
+      const float a = fabsf(xh[k]);
+      m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+    }
+  m = block_max128(m, red);
+  const int ev = oz_exp(m);
+  const bool live = valid && ev != OZ_NONFINITE;
+  if (threadIdx.x == 0) e[(int64_t)g * NTL * TH + v] = ev;
+  const int tile = (int)(v / TH), nl = (int)(v - (int64_t)tile * TH);
+  const int64_t bblk = (int64_t)TH * OZ_BK;
+  for (int c = threadIdx.x; c < KB * 4; c += 128) {
+    const int kb = c >> 2, kc = c & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)c * 8 + q;
+      h[q] = (live && k < K) ? xh[k] : 0.f;
+      l[q] = (live && k < K) ? xl[k] : 0.f;
+    }
+    store_digits(h, l, ev, live, out + ((((int64_t)g * NTL + tile) * KB + kb) * OZ_S) * bblk +
+                                    ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+  }
+}
+
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
 inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
 
@@ -581,6 +620,25 @@ cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm
   q.M = D; q.N = ncolg; q.K = D; q.groups = groups; q.NT = NT; q.ksplit = ksplit;
   q.ohi = ohi; q.olo = olo; q.status = status;
   return oz_gemm(q, st);
+}
+
+cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K, int64_t nvec, int groups,
+                          int TH, __nv_bfloat16* out, int* e, cudaStream_t st) {
+  const int NTL = (int)((nvec + TH - 1) / TH);
+  dim3 grid((unsigned)(NTL * TH), (unsigned)groups);
+  k_oz_slice_vecs<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out, e);
+  return cudaGetLastError();
+}
+
+int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int cap) {
+  const int KB = (int)((K + OZ_BK - 1) / OZ_BK);
+  const int64_t ctas = ((M + 127) / 128) * ((N + NT - 1) / NT) * groups;
+  int s = (int)std::max<int64_t>(1, (sm_count() + ctas - 1) / ctas);
+  s = std::min(s, std::max(1, KB / OZ_CHUNK));
+  s = std::max(s, (KB + OZ_KB_MAX - 1) / OZ_KB_MAX);
+  s = std::min(s, cap);
+  const int kbper = (KB + s - 1) / s;
+  return (KB + kbper - 1) / kbper;
 }
 
 size_t oz_vec_elems(int64_t nvec, int64_t K, int TH) {
