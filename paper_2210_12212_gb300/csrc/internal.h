@@ -66,7 +66,7 @@ enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
   K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
-  K_INVERSE_TC, K_TRTRI_TC, K_NCAT
+  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;

@@ -1047,6 +1047,66 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
   return cudaSuccess;
 }
 
+// ---- Two-level Cholesky: within a 128-wide panel the 32-wide steps update only the panel's
+// columns; at the panel's end the trailing matrix takes the delayed rank-128 update
+//   H[c1:, c1:] -= L_p L_p^T,  L_p = L[c1:, c0:c1],
+// as an exact-slice product on the tensor cores (symmetric: tiles touching i <= j).
+__global__ void k_oz_sub_sym(const long long* hi, const long long* lo, int S, int64_t M, int L, const int* ea,
+                             int64_t eag, const int* eb, int64_t ebg, int64_t D, int64_t c1, CBuf H) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)L * M * M) return;
+  const int64_t i = e % M, j = (e / M) % M, g = e / (M * M);
+  if (i > j) return;
+  long long h = 0, w = 0;
+  for (int s = 0; s < S; ++s) {
+    h += hi[(int64_t)s * L * M * M + e];
+    w += lo[(int64_t)s * L * M * M + e];
+  }
+  const dd v = oz_join(h, w, ea[g * eag + i], eb[g * ebg + j]);
+  const int64_t o = g * D * D + (c1 + j) * D + c1 + i;  // the lower-triangle entry (c1 + j, c1 + i)
+  DD::st(H, o, dd_sub(DD::ld(H, o), v));
+}
+
+struct PanelUpdate {
+  __nv_bfloat16 *Xs = nullptr, *Ys = nullptr;
+  int *ea = nullptr, *eb = nullptr;
+  long long *hi = nullptr, *lo = nullptr;
+};
+static cudaError_t panel_update_alloc(ihsbin_problem* p, PanelUpdate& u) {
+  const int64_t D = p->A.D, M = D > 128 ? D - 128 : 1;
+  const int L = p->plan.L;
+  CK(prob_alloc(p, oz_vec_elems(M, 128, 128) * 2 * L, (void**)&u.Xs, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(M, 128) * 4 * L, (void**)&u.ea, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_elems(M, 128, 32) * 2 * L, (void**)&u.Ys, SCOPE_SCRATCH));
+  CK(prob_alloc(p, oz_vec_exps(M, 32) * 4 * L, (void**)&u.eb, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)L * M * M * 8, (void**)&u.hi, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)L * M * M * 8, (void**)&u.lo, SCOPE_SCRATCH));
+  return cudaSuccess;
+}
+static cudaError_t panel_update(ihsbin_problem* p, CBuf H, const PanelUpdate& u, int64_t c0, int64_t c1,
+                                cudaStream_t st) {
+  const int64_t D = p->A.D, M = D - c1, w = c1 - c0;
+  const int L = p->plan.L;
+  {
+    KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * M * w * 8 * 2 + (double)L * (oz_vec_elems(M, w, 128) + oz_vec_elems(M, w, 32)) * 2);
+    CK(oz_slice_vecs(H, D * D, c1 * D + c0, D, w, M, L, 128, u.Xs, u.ea, st));
+    CK(oz_slice_vecs(H, D * D, c1 * D + c0, D, w, M, L, 32, u.Ys, u.eb, st));
+  }
+  {
+    OzGemm q;
+    q.As = u.Xs; q.ea = u.ea; q.Bs = u.Ys; q.eb = u.eb;
+    q.M = M; q.N = M; q.K = w; q.groups = L; q.NT = 32; q.ksplit = 1; q.sym = 1;
+    q.ohi = u.hi; q.olo = u.lo; q.status = p->status;
+    KTimer kt(p, K_SYRK_TC, st, oz_pair_flops(1, 1, 1) * L * (M * (M + 1.0) / 2.0) * w,
+              (double)L * (oz_vec_elems(M, w, 128) + oz_vec_elems(M, w, 32)) * 2 + 16.0 * L * M * M);
+    CK(oz_gemm(q, st));
+  }
+  KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * M * M * (16.0 + 16.0));
+  k_oz_sub_sym<<<nblocks((int64_t)L * M * M, 256), 256, 0, st>>>(u.hi, u.lo, 1, M, L, u.ea, (int64_t)oz_vec_exps(M, 128),
+                                                                 u.eb, (int64_t)oz_vec_exps(M, 32), D, c1, H);
+  return cudaGetLastError();
+}
+
 // P_l[i][j] = P_l[j][i] (i <= j) from the exact partials of W_l^T W_l on the tensor cores
 __global__ void k_oz_store_sym(const long long* hi, const long long* lo, int S, int64_t D, int L, const int* ea,
                                int64_t ea_gs, const int* eb, int64_t eb_gs, CBuf P) {
@@ -1111,6 +1171,9 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
     k_shift_copy<Mode><<<dim3(nblocks(D * D, 256), L), 256, 0, st>>>(p->GS, D, lam0_dev, H);
   }
   CK(cudaGetLastError());
+  const bool two_level = Mode::id == 1 && p->plan.factor == IHSBIN_FACTOR_SLICES && D > 128;
+  PanelUpdate pu;
+  if (two_level) CK(panel_update_alloc(p, pu));
   for (int kb = 0; kb < nblk; ++kb) {
     {
       KTimer kt(p, K_FACTOR_POTRF, st, (double)L * NB * NB * NB * 2.0 / 3.0, (double)L * NB * NB * cs * 3);
@@ -1127,12 +1190,17 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
       CK((launch_gemm<Mode, 64, 32, 16, 4, 2>(sp, L, LdPanel<Mode>{H, D, r0, c0}, LdDinvT<Mode>{dinv, nblk, kb},
                                               EpPanel<Mode>{H, D, r0, c0}, st)));
     }
-    GemmShape su{rem, rem, NB, 2};
-    {
-      KTimer kt(p, K_FACTOR_SYRK, st, (double)L * rem * (rem + 1) * NB, (double)L * rem * rem * cs);
+    // two-level: the 32-wide step updates only the columns of its 128-wide panel
+    const int64_t pend = two_level ? std::min<int64_t>(D, (int64_t)(kb / 4 + 1) * 128) : D;
+    const int64_t wcols = pend - r0;
+    if (wcols > 0) {
+      GemmShape su{rem, wcols, NB, 2};
+      KTimer kt(p, K_FACTOR_SYRK, st, (double)L * wcols * (2.0 * rem - wcols + 1) * NB, (double)L * rem * wcols * cs);
       CK((launch_gemm<Mode, 64, 64, 16, 4, 4>(su, L, LdPanel<Mode>{H, D, r0, c0}, LdPanelT<Mode>{H, D, r0, c0},
                                               EpTrailing<Mode>{H, D, r0}, st)));
     }
+    if (two_level && (kb % 4 == 3 || kb == nblk - 1) && pend < D)
+      CK(panel_update(p, H, pu, (int64_t)(kb / 4) * 128, pend, st));
   }
   {
     cudaError_t err = cudaSuccess;

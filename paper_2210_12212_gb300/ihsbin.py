@@ -81,7 +81,7 @@ EXPORTED = [
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
 ]
-KCAT_COUNT = 26
+KCAT_COUNT = 27
 
 
 def load(path: Optional[str] = None):
