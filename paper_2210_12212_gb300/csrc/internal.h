@@ -215,6 +215,17 @@ cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int gr
 cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K, int64_t nvec, int groups,
                           int TH, __nv_bfloat16* out, int* e, cudaStream_t st);
 int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int cap);
+// The recursion's elementwise steps with the slicing of their output fused (one CTA per column,
+// the column in D x 8 bytes of shared memory; oz_fused_ok(D) says whether it fits).
+bool oz_fused_ok(int64_t D);
+cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
+                            const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
+                            const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
+                            __nv_bfloat16* Rs, int* er, cudaStream_t st);
+cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
+                            const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
+                            CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
+                            int* eu, cudaStream_t st);
 // device bytes of the recursion's slices (G, every P_l, one step's B operand)
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);

@@ -1494,7 +1494,8 @@ struct OzLoop {
   const __nv_bfloat16* Ps = nullptr;  // P_l of every interval, rows sliced
   const int* ep = nullptr;
   __nv_bfloat16* Bs = nullptr;        // the step's B operand, columns sliced
-  int* eb = nullptr;
+  int* eb = nullptr;                  // its column exponents (the step's U columns)
+  int* er = nullptr;                  // column exponents of R (fused path)
   long long *Yhi = nullptr, *Ylo = nullptr, *Zhi = nullptr, *Zlo = nullptr;  // exact split partials
 };
 
@@ -1527,11 +1528,13 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t ys = nold * D;
     const int64_t mt = (D + 63) / 64;
     int ny = 1;
+    const bool fused = oz.on && pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D);
     if (pl.product == IHSBIN_PRODUCT_GRAM && oz.on) {
-      // G times the concatenated old columns of every live interval, on the tensor cores
+      // G times the concatenated old columns of every live interval, on the tensor cores (with the
+      // fused path the previous step's update already sliced them)
       const int64_t ncat = nold * live;
       const int NT = oz_tile_n(ncat);
-      {
+      if (!fused || i == 1) {
         KTimer kt(p, K_LOOP_SLICE, st, 0, 8.0 * D * ncat + 12.0 * D * ncat);
         CK(oz_slice_cols(Uin, D, 1, ncat, NT, nold, gs, perm_dev, oz.Bs, oz.eb, st));
       }
@@ -1572,7 +1575,11 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int inew = (i < J) ? i : -1;
     sp.ksplit = std::min(pick_split(mt * ((nnew + tile_n(nnew) - 1) / tile_n(nnew)) * live, D, tile_k(nnew)),
                          SPLIT_MAX);
-    if (oz.on && pl.product == IHSBIN_PRODUCT_GRAM) {
+    if (fused) {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ny + 24 + 12));
+      CK(oz_make_R_slice(oz.Yhi, oz.Ylo, ny, (int64_t)live * ys, oz.eg, oz.eb, Uin, live, nold, nnew, D, K, inew,
+                         perm_dev, tau_dev, lam0_dev, gs, oz_tile_n(nnew), oz.Bs, oz.er, st));
+    } else if (oz.on && pl.product == IHSBIN_PRODUCT_GRAM) {
       KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ny + 24));
       k_make_R_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
           oz.Yhi, oz.Ylo, ny, (int64_t)live * ys, oz.eg, oz.eb, Uin, live, nold, nnew, D, K, inew, perm_dev, tau_dev,
@@ -1587,7 +1594,8 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     if (oz.on) {
       // P_l R_l of every live interval, on the tensor cores
       const int NT = oz_tile_n(nnew);
-      {
+      int* erv = fused ? oz.er : oz.eb;  // column exponents of R
+      if (!fused) {
         KTimer kt(p, K_LOOP_SLICE, st, 0, 20.0 * D * nnew * live);
         CK(oz_slice_cols(R, D, live, nnew, NT, nnew, nnew * D, nullptr, oz.Bs, oz.eb, st));
       }
@@ -1595,10 +1603,19 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       {
         KTimer kt(p, K_LOOP_P_TC, st, oz_pair_flops(D, nnew, D) * live,
                   (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 16.0 * ks * D * nnew * live);
-        CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, oz.eb, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
+        CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, erv, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
                       st));
       }
-      {
+      if (fused) {
+        // the intervals still running at the next step take their new columns' slices now
+        int live_next = 0;
+        if (i + 1 < pl.kmax)
+          while (live_next < L && pl.k[order[live_next]] > i + 1) ++live_next;
+        const int NTn = live_next > 0 ? oz_tile_n(nnew * live_next) : 16;
+        KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24 + 12));
+        CK(oz_update_slice(oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er, (int64_t)oz_cols_exps(nnew, NT),
+                           live, nnew, D, K, i, Uin, Uout, p->Ut, perm_dev, gs, live_next, NTn, oz.Bs, oz.eb, st));
+      } else {
         KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24));
         k_update_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
             oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.eb, (int64_t)oz_cols_exps(nnew, NT), live, nnew, D,
@@ -1774,6 +1791,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     CK(prob_alloc(p, oz_rows_exps(D) * 4 * L, (void**)&ep, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * ((D + 31) / 32) * 6 * 32 * 2, (void**)&Bs, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * 4, (void**)&eb, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)bcols * 4, (void**)&oz.er, SCOPE_SCRATCH));
     // the largest split partials of any step, replaying the recursion's (live, columns, splits)
     size_t ymax = 1, zmax = 1;
     {

@@ -520,6 +520,132 @@ __global__ void __launch_bounds__(128) k_oz_slice_vecs(CBuf X, int64_t gs, int64
   }
 }
 
+// Block-wide slicing of one column held in shared memory (hi[D], lo[D]) into tile-height-NT
+// layout position (group 0): column c, tile c / NT.  Every thread of the CTA takes part.
+constexpr int OZ_FUSED_THREADS = 512;
+
+__device__ __forceinline__ float block_max_fused(float v, float* red) {  // blockDim.x = OZ_FUSED_THREADS
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  float m = red[0];
+#pragma unroll
+  for (int w = 1; w < OZ_FUSED_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+  return m;
+}
+
+__device__ __forceinline__ void slice_smem_column(const float* hi, const float* lo, int64_t D, int64_t c, int NT, int KB,
+                                                  float* red, __nv_bfloat16* out, int* e) {
+  float m = 0.f;
+  for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) {
+    const float a = fabsf(hi[k]);
+    m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+  }
+  m = block_max_fused(m, red);
+  const int ev = oz_exp(m);
+  const bool live = ev != OZ_NONFINITE;
+  if (threadIdx.x == 0) e[c] = ev;
+  const int tile = (int)(c / NT), nl = (int)(c - (int64_t)tile * NT);
+  const int64_t bblk = (int64_t)NT * OZ_BK;
+  for (int ch = threadIdx.x; ch < KB * 4; ch += OZ_FUSED_THREADS) {
+    const int kb = ch >> 2, kc = ch & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)ch * 8 + q;
+      h[q] = (live && k < D) ? hi[k] : 0.f;
+      l[q] = (live && k < D) ? lo[k] : 0.f;
+    }
+    store_digits(h, l, ev, live, out + (((int64_t)tile * KB + kb) * OZ_S) * bblk +
+                                   ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+  }
+}
+
+// The recursion's right-hand sides R (as k_make_R_oz) with their slicing fused: one CTA per
+// column of R, padded to NTL x NT per live interval; R stays in shared memory.
+__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo, int ny,
+                                                         int64_t ny_stride, const int* eg, const int* eu, CBuf U,
+                                                         int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
+                                                         const int* perm, const double* tau, const double* lam0,
+                                                         int64_t gs, int NT, int NTL, int KB, __nv_bfloat16* Rs,
+                                                         int* er) {
+  extern __shared__ float colbuf[];  // hi[D], lo[D]
+  __shared__ float red[OZ_FUSED_THREADS / 32];
+  float* bh = colbuf;
+  float* bl = colbuf + D;
+  const int64_t c = blockIdx.x, per = (int64_t)NTL * NT;
+  const int g = (int)(c / per);
+  const int64_t col = c - g * per;
+  const bool valid = col < nnew;
+  if (valid) {
+    const int l = perm[g];
+    const int64_t j = col / K;
+    const dd lm = dd_from_double(lam0[l]), tl = dd_from_double(tau[l]);
+    for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) {
+      const int64_t o = (int64_t)l * gs + col * D + k;
+      dd r;
+      if (j == inew) {
+        r = dd_mul(lm, DD::ld(U, o - K * D));
+      } else {
+        const int64_t cc = (int64_t)g * nold + col, yo = cc * D + k;
+        long long h = Yhi[yo], w = Ylo[yo];
+        for (int s = 1; s < ny; ++s) {
+          h += Yhi[s * ny_stride + yo];
+          w += Ylo[s * ny_stride + yo];
+        }
+        r = dd_mul(tl, dd_add(oz_join(h, w, eg[k], eu[cc]), dd_mul(lm, DD::ld(U, o))));
+        if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
+      }
+      bh[k] = r.hi;
+      bl[k] = r.lo;
+    }
+  } else {
+    for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) bh[k] = bl[k] = 0.f;
+  }
+  __syncthreads();
+  // group g's tiles start at tile g * NTL
+  slice_smem_column(bh, bl, D, (int64_t)g * per + col, NT, KB, red, Rs, er);
+}
+
+// The update of the recursion (as k_update_oz) with the next step's slicing of the new columns
+// fused: one CTA per new column (g, col); for an interval still live at the next step, the new
+// u is cut into the next step's concatenated-column layout (column g * ncol + col, tile NTn).
+__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long long* Zhi, const long long* Zlo, int S,
+                                                         const int* ep, int64_t ep_gs, const int* er, int64_t er_gs,
+                                                         int live, int64_t ncol, int64_t D, int64_t K, int i,
+                                                         CBuf Uin, CBuf Uout, CBuf Ut, const int* perm, int64_t gs,
+                                                         int live_next, int NTn, int KB, __nv_bfloat16* Us, int* eu) {
+  extern __shared__ float colbuf[];
+  __shared__ float red[OZ_FUSED_THREADS / 32];
+  float* bh = colbuf;
+  float* bl = colbuf + D;
+  const int g = (int)(blockIdx.x / ncol);
+  const int64_t col = blockIdx.x - (int64_t)g * ncol;
+  const int l = perm[g];
+  const int64_t j = col / K, ss = (int64_t)live * ncol * D;
+  const int ec = er[(int64_t)g * er_gs + col];
+  for (int64_t row = threadIdx.x; row < D; row += OZ_FUSED_THREADS) {
+    const int64_t zo = ((int64_t)g * ncol + col) * D + row;
+    long long h = Zhi[zo], w = Zlo[zo];
+    for (int s = 1; s < S; ++s) {
+      h += Zhi[s * ss + zo];
+      w += Zlo[s * ss + zo];
+    }
+    const dd z = oz_join(h, w, ep[(int64_t)l * ep_gs + row], ec);
+    const int64_t o = (int64_t)l * gs + col * D + row;
+    dd u = (j < i) ? DD::ld(Uin, o) : DD::zero();
+    u = dd_sub(u, z);
+    DD::st(Uout, o, u);
+    DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
+    bh[row] = u.hi;
+    bl[row] = u.lo;
+  }
+  if (g >= live_next) return;  // uniform over the CTA
+  __syncthreads();
+  slice_smem_column(bh, bl, D, (int64_t)g * ncol + col, NTn, KB, red, Us, eu);
+}
+
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
 inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
 
@@ -639,6 +765,32 @@ int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int c
   s = std::min(s, cap);
   const int kbper = (KB + s - 1) / s;
   return (KB + kbper - 1) / kbper;
+}
+
+bool oz_fused_ok(int64_t D) { return (size_t)D * 8 <= 160 * 1024; }
+
+cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
+                            const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
+                            const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
+                            __nv_bfloat16* Rs, int* er, cudaStream_t st) {
+  const int NTL = (int)((nnew + NT - 1) / NT);
+  const int smem = (int)(D * 8);
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_make_R_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k_make_R_oz_slice<<<(unsigned)((int64_t)live * NTL * NT), OZ_FUSED_THREADS, smem, st>>>(
+      Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau, lam0, gs, NT, NTL, oz_kb(D), Rs, er);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
+                            const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
+                            CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
+                            int* eu, cudaStream_t st) {
+  const int smem = (int)(D * 8);
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k_update_oz_slice<<<(unsigned)((int64_t)live * ncol), OZ_FUSED_THREADS, smem, st>>>(Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol,
+                                                                         D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn,
+                                                                         oz_kb(D), Us, eu);
+  return cudaGetLastError();
 }
 
 size_t oz_vec_elems(int64_t nvec, int64_t K, int TH) {
