@@ -668,7 +668,7 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, st);
-  e = eval_device(p, lam_dev, T, Xd, x_dtype == IHSBIN_F64 ? ELEM_F64 : ELEM_F32, st);
+  e = eval_device(p, lambdas, lam_dev, T, Xd, x_dtype == IHSBIN_F64 ? ELEM_F64 : ELEM_F32, st);
   cudaEventRecord(e1, st);
   if (e == cudaSuccess && !x_on_device) e = cudaMemcpyAsync(X, Xd, outN * oes, cudaMemcpyDeviceToHost, st);
   if (e != cudaSuccess) {

@@ -230,7 +230,7 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
-cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,
+cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_host, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,
                         cudaStream_t st);
 
 }  // namespace ihsbin

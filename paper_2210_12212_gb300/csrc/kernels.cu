@@ -1649,8 +1649,11 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
 
 // ===================================================== a6: path evaluation
 // coefficient table coef[t][j] = tau_l theta_t^j (FP64), interval per lambda
+// (the table is also written as float-float hi/lo when ch is not null, so that the evaluation's
+// inner loop does no FP64 conversion)
 __global__ void k_eval_coef(const double* lam, int64_t T, const double* edges, int L, const double* tau,
-                            const double* lam0, const int* jcount, int jc, int* tint, double* coef) {
+                            const double* lam0, const int* jcount, int jc, int* tint, double* coef, float* ch,
+                            float* cl) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
   double x = lam[t];
@@ -1665,31 +1668,52 @@ __global__ void k_eval_coef(const double* lam, int64_t T, const double* edges, i
   double th = tau[l] * (x - lam0[l]) / lam0[l];
   double cf = tau[l];
   for (int j = 0; j < jc; ++j) {
-    coef[t * jc + j] = (j < jcount[l]) ? cf : 0.0;
+    const double v = (j < jcount[l]) ? cf : 0.0;
+    coef[t * jc + j] = v;
+    if (ch) {
+      const float h = (float)v;
+      ch[t * jc + j] = h;
+      cl[t * jc + j] = (float)(v - (double)h);
+    }
     cf *= th;
   }
 }
 
-// X[t][i][r] = sum_j coef[t][j] * B_l[j][r][i]   (B = utilde, or its primal image for the dual)
+// X[t][i][r] = sum_j coef[t][j] * B_l[j][r][i]   (B = utilde, or its primal image for the dual).
+// Chunks of up to EVAL_TB lambdas of one interval: each basis entry is read once per chunk (not
+// once per lambda) and applied to every lambda of the chunk.
+constexpr int EVAL_TB = 16;
 template <class Mode>
-__global__ void k_eval(CBuf Bm, int64_t rows, int64_t K, int jc, int64_t gs, const int* tint, const double* coef,
-                       const int* jcount, int64_t T, void* X, int x_elem) {
-  const int64_t t = blockIdx.y;
+__global__ void k_eval_chunks(CBuf Bm, int64_t rows, int64_t K, int jc, int64_t gs, const int* chunk_l,
+                              const int* chunk_t0, const int* chunk_n, const int* torder, CBuf coef,
+                              const int* jcount, void* X, int x_elem) {
+  const int c = blockIdx.y;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= T || e >= rows * K) return;
+  if (e >= rows * K) return;
   const int64_t r = e / rows, i = e % rows;
-  const int l = tint[t];
+  const int l = chunk_l[c], nq = chunk_n[c], t0 = chunk_t0[c];
   const int jn = jcount[l];
-  typename Mode::V acc = Mode::zero();
-  for (int j = 0; j < jn; ++j) {
-    typename Mode::V b = Mode::ld(Bm, (int64_t)l * gs + ((int64_t)j * K + r) * rows + i);
-    typename Mode::V cf = Mode::from_d(coef[t * jc + j]);
-    acc = Mode::add(acc, Mode::mul(cf, b));
+  int tq[EVAL_TB];
+  typename Mode::V acc[EVAL_TB];
+#pragma unroll
+  for (int q = 0; q < EVAL_TB; ++q) {
+    tq[q] = q < nq ? torder[t0 + q] : 0;
+    acc[q] = Mode::zero();
   }
-  const int64_t o = t * rows * K + i * K + r;
-  double v = Mode::to_d(acc);
-  if (x_elem == ELEM_F64) ((double*)X)[o] = v;
-  else ((float*)X)[o] = (float)v;
+  for (int j = 0; j < jn; ++j) {
+    const typename Mode::V b = Mode::ld(Bm, (int64_t)l * gs + ((int64_t)j * K + r) * rows + i);
+#pragma unroll
+    for (int q = 0; q < EVAL_TB; ++q)
+      if (q < nq) acc[q] = Mode::add(acc[q], Mode::mul(Mode::ld(coef, (int64_t)tq[q] * jc + j), b));
+  }
+#pragma unroll
+  for (int q = 0; q < EVAL_TB; ++q) {
+    if (q >= nq) break;
+    const int64_t o = (int64_t)tq[q] * rows * K + i * K + r;
+    const double v = Mode::to_d(acc[q]);
+    if (x_elem == ELEM_F64) ((double*)X)[o] = v;
+    else ((float*)X)[o] = (float)v;
+  }
 }
 
 // ============================================================ orchestration
@@ -1864,8 +1888,8 @@ cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
 }
 
 template <class Mode>
-static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_dev, int64_t T, void* X, int x_elem,
-                              cudaStream_t st) {
+static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, void* X,
+                              int x_elem, cudaStream_t st) {
   const Plan& pl = p->plan;
   const int L = pl.L, jc = pl.jc;
   double *edges = nullptr, *tau = nullptr, *lam0 = nullptr, *coef = nullptr;
@@ -1876,28 +1900,64 @@ static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_dev, int64_t 
   CK(prob_alloc(p, L * sizeof(int), (void**)&jcount, SCOPE_SCRATCH));
   CK(prob_alloc(p, T * sizeof(int), (void**)&tint, SCOPE_SCRATCH));
   CK(prob_alloc(p, (size_t)T * jc * sizeof(double), (void**)&coef, SCOPE_SCRATCH));
+  CBuf coefc{coef, nullptr};  // the table in compute precision
+  if (Mode::id == 1) {
+    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc.p0, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc.p1, SCOPE_SCRATCH));
+  }
   CK(cudaMemcpyAsync(edges, pl.edges.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(tau, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(lam0, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(jcount, pl.jcount.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
   {
     KTimer kt(p, K_EVAL_COEF, st, 0, (double)T * jc * 8);
-    k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef);
+    k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef,
+                                                 Mode::id == 1 ? (float*)coefc.p0 : nullptr,
+                                                 Mode::id == 1 ? (float*)coefc.p1 : nullptr);
   }
   CK(cudaGetLastError());
   const int64_t K = p->K;
   const int64_t rows = p->dual ? p->A.N : p->A.D;
   const CBuf Bm = p->dual ? p->W : p->Ut;
   const int64_t gs = (int64_t)jc * K * rows;
-  dim3 grid(nblocks(rows * K, 256), (unsigned)T);
+  // group the lambdas by interval (the interval rule of k_eval_coef) into chunks of <= EVAL_TB
+  std::vector<std::vector<int>> by(L);
+  for (int64_t t = 0; t < T; ++t) {
+    int lo = 0, hi = L;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (pl.edges[mid] <= lam_host[t]) lo = mid; else hi = mid;
+    }
+    by[lo].push_back((int)t);
+  }
+  std::vector<int> torder, cl, ct0, cn;
+  for (int l = 0; l < L; ++l)
+    for (size_t a = 0; a < by[l].size(); a += EVAL_TB) {
+      cl.push_back(l);
+      ct0.push_back((int)torder.size() + 0);
+      cn.push_back((int)std::min<size_t>(EVAL_TB, by[l].size() - a));
+      for (size_t b = a; b < std::min(by[l].size(), a + EVAL_TB); ++b) torder.push_back(by[l][b]);
+    }
+  const int nch = (int)cl.size();
+  int* dev = nullptr;  // [torder T][chunk l][chunk t0][chunk n]
+  CK(prob_alloc(p, (T + 3 * (size_t)nch) * sizeof(int), (void**)&dev, SCOPE_SCRATCH));
+  std::vector<int> pack(torder);
+  pack.insert(pack.end(), cl.begin(), cl.end());
+  pack.insert(pack.end(), ct0.begin(), ct0.end());
+  pack.insert(pack.end(), cn.begin(), cn.end());
+  // from pageable memory: the call returns once `pack` is staged, so it may go out of scope
+  CK(cudaMemcpyAsync(dev, pack.data(), pack.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  dim3 grid(nblocks(rows * K, 256), (unsigned)nch);
   KTimer kt(p, K_EVAL, st, 2.0 * T * rows * K * jc, (double)T * rows * K * (x_elem == ELEM_F64 ? 8 : 4));
-  k_eval<Mode><<<grid, 256, 0, st>>>(Bm, rows, K, jc, gs, tint, coef, jcount, T, X, x_elem);
+  k_eval_chunks<Mode><<<grid, 256, 0, st>>>(Bm, rows, K, jc, gs, dev + T, dev + T + nch, dev + T + 2 * nch, dev, coefc,
+                                            jcount, X, x_elem);
   return cudaGetLastError();
 }
 
-cudaError_t eval_device(ihsbin_problem* p, const double* lam_dev, int64_t T, void* X, int x_elem, cudaStream_t st) {
-  if (p->plan.compute == IHSBIN_COMPUTE_F64) return eval_typed<F64>(p, lam_dev, T, X, x_elem, st);
-  return eval_typed<DD>(p, lam_dev, T, X, x_elem, st);
+cudaError_t eval_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, void* X,
+                        int x_elem, cudaStream_t st) {
+  if (p->plan.compute == IHSBIN_COMPUTE_F64) return eval_typed<F64>(p, lam_host, lam_dev, T, X, x_elem, st);
+  return eval_typed<DD>(p, lam_host, lam_dev, T, X, x_elem, st);
 }
 
 

@@ -259,37 +259,58 @@ cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------- dual map
-// W_l[col*N + r] = sum_e val[e] * Ut_l[col*D + ci[e]]: one warp per row r of A_hat,
-// lanes over the nonzeros, every column of every interval.
+// W_l[col*N + r] = sum_e val[e] * Ut_l[col*D + ci[e]] for every interval l and basis column col.
+// One warp per row r of A_hat; lane c takes the basis columns c, c + 32, ... of all intervals and
+// walks the row's nonzeros itself (broadcast loads, no cross-lane sums), reading the basis from a
+// transposed copy UtT[k][column] so that the lanes' loads are contiguous.
 template <class Mode>
-__global__ void k_csr_dual_map(const int64_t* rp, const int32_t* ci, const void* val, int elem, int64_t N, int64_t D,
-                               CBuf Ut, int64_t ncol, int L, CBuf W) {
+__global__ void k_transpose_basis(CBuf Ut, int64_t D, int64_t nc, CBuf UtT) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over D x nc, column fastest
+  if (e >= D * nc) return;
+  const int64_t k = e / nc, c = e - k * nc;
+  Mode::st(UtT, e, Mode::ld(Ut, c * D + k));
+}
+template <class Mode>
+__device__ __forceinline__ void mac_elem(typename Mode::V& acc, const void* val, int elem, int64_t e,
+                                         typename Mode::V u) {
+  if (elem == ELEM_F32) Mode::mac(acc, ((const float*)val)[e], u);  // an exact float operand
+  else if (elem == ELEM_BF16) Mode::mac(acc, __uint_as_float((uint32_t)((const uint16_t*)val)[e] << 16), u);
+  else acc = Mode::add(acc, Mode::mul(Mode::from_d(((const double*)val)[e]), u));
+}
+template <class Mode>
+__global__ void k_csr_dual_map(const int64_t* rp, const int32_t* ci, const void* val, int elem, int64_t N, int64_t nc,
+                               CBuf UtT, CBuf W) {
   const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
   if (r >= N) return;
   const int64_t e0 = rp[r], e1 = rp[r + 1];
-  for (int l = 0; l < L; ++l) {
-    for (int64_t col = 0; col < ncol; ++col) {
-      typename Mode::V acc = Mode::zero();
-      const int64_t base = ((int64_t)l * ncol + col) * D;
-      for (int64_t e = e0 + lane; e < e1; e += 32)
-        acc = Mode::add(acc, Mode::mul(Mode::from_d(load_elem_d(val, elem, e)), Mode::ld(Ut, base + ci[e])));
-      acc = warp_sum<Mode>(acc);
-      if (lane == 0) Mode::st(W, ((int64_t)l * ncol + col) * N + r, acc);
+  for (int64_t c = lane; c < nc; c += 32) {
+    typename Mode::V acc = Mode::zero();
+    for (int64_t e = e0; e < e1; ++e) {
+      mac_elem<Mode>(acc, val, elem, e, Mode::ld(UtT, (int64_t)ci[e] * nc + c));
+      if (((e - e0) & 31) == 31) acc = Mode::renorm(acc);
     }
+    Mode::st(W, c * N + r, Mode::renorm(acc));
   }
 }
 
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st) {
   const Tall& A = p->A;
   const int L = p->plan.L;
+  const int64_t nc = ncol * L, D = A.D;
   const double es = A.elem == ELEM_F64 ? 8 : A.elem == ELEM_F32 ? 4 : 2;
-  KTimer kt(p, K_DUAL_MAP, st, 2.0 * A.nnz * ncol * L, A.nnz * (es + 4) + 8.0 * ncol * L * A.N);
+  cudaError_t err = cudaSuccess;
+  CBuf UtT = alloc_cbuf(p, compute, (size_t)D * nc, SCOPE_SCRATCH, &err);
+  if (err != cudaSuccess) return err;
+  KTimer kt(p, K_DUAL_MAP, st, 2.0 * A.nnz * nc, A.nnz * (es + 4) + 8.0 * nc * A.N);
   const unsigned g = nblk(A.N * 32, 256);
-  if (compute == IHSBIN_COMPUTE_F64)
-    k_csr_dual_map<F64><<<g, 256, 0, st>>>(A.rp, A.ci, A.val, A.elem, A.N, A.D, p->Ut, ncol, L, p->W);
-  else
-    k_csr_dual_map<DD><<<g, 256, 0, st>>>(A.rp, A.ci, A.val, A.elem, A.N, A.D, p->Ut, ncol, L, p->W);
+  if (compute == IHSBIN_COMPUTE_F64) {
+    k_transpose_basis<F64><<<nblk(D * nc, 256), 256, 0, st>>>(p->Ut, D, nc, UtT);
+    k_csr_dual_map<F64><<<g, 256, 0, st>>>(A.rp, A.ci, A.val, A.elem, A.N, nc, UtT, p->W);
+  } else {
+    k_transpose_basis<DD><<<nblk(D * nc, 256), 256, 0, st>>>(p->Ut, D, nc, UtT);
+    k_csr_dual_map<DD><<<g, 256, 0, st>>>(A.rp, A.ci, A.val, A.elem, A.N, nc, UtT, p->W);
+  }
   return cudaGetLastError();
 }
 
