@@ -524,8 +524,9 @@ def measured_peak(key, fallback):
 
 
 # Categories whose binding resource is HBM: every step of the recursion streams the live
-# intervals' preconditioner slices (12 bytes per entry), which do not stay in L2.
-HBM_BOUND = ("loop_precond_tc",)
+# intervals' preconditioner slices (12 bytes per entry), which do not stay in L2; the
+# elementwise steps of the recursion and the slicing / joining kernels move data only.
+HBM_BOUND = ("loop_precond_tc", "loop_precond_update", "loop_slice", "factor_slice", "gram_slice", "gram_combine")
 
 
 def kernel_peak(name, compute):

@@ -322,14 +322,23 @@ __device__ __forceinline__ int oz_exp(float m) {
   return e;
 }
 
+// Nearest integer (ties to even) of a float of magnitude < 2^48 with 32-bit conversions only (64-bit
+// float <-> integer conversions run on the FP64 pipe): r = rint(x) is integer-valued, and
+// r = a 2^24 + b exactly with a = trunc(r 2^-24) (|a| < 2^24) and |b| < 2^24, both exact in FP32.
+__device__ __forceinline__ long long round_to_ll(float x) {
+  const float r = rintf(x);
+  const float a = truncf(r * 5.9604644775390625e-8f);  // r 2^-24, exact
+  const float b = fmaf(-a, 16777216.f, r);              // r - a 2^24, exact
+  return ((long long)__float2int_rz(a) << 24) + (long long)__float2int_rz(b);
+}
+
 // v = hi + lo scaled by 2^(47 - e) to the nearest integer V (|V| <= 2^47, error <= 1 unit,
 // i.e. 2^-47 of 2^e), then V = sum_t a_t 2^(8 (5 - t)) in balanced base-256 digits |a_t| <= 128.
 __device__ __forceinline__ void store_digits(const float (&hi)[8], const float (&lo)[8], int e, bool live,
                                              __nv_bfloat16* dst, int64_t tstride) {
   long long V[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    V[q] = live ? __float2ll_rn(ldexpf(hi[q], 47 - e)) + __float2ll_rn(ldexpf(lo[q], 47 - e)) : 0ll;
+  for (int q = 0; q < 8; ++q) V[q] = live ? round_to_ll(ldexpf(hi[q], 47 - e)) + round_to_ll(ldexpf(lo[q], 47 - e)) : 0ll;
   int dg[OZ_S][8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
