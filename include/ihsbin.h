@@ -262,6 +262,24 @@ IHSBIN_API ihsbin_status ihsbin_basis_export(ihsbin_problem* p, int32_t l, doubl
 IHSBIN_API ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t T, void* X,
                                ihsbin_dtype x_dtype, int x_on_device, void* stream);
 
+/* Section 6.1's losses along the path without forming X: for each lambdas[t]
+ *   train_loss[t] = 1/2 ||A x(lambda_t) - B||_F^2 + lambda_t/2 ||x(lambda_t)||_F^2,
+ *   test_loss[t]  = 1/2 ||A_test x(lambda_t) - B_test||_F^2,
+ * with x(lambda) the primal solution ihsbin_eval_path returns (the dual's x = A^T z).
+ * The basis's images A utilde_j and A_test utilde_j are formed once (a contraction over d
+ * per basis column) and the residual of each lambda is a combination of them with the
+ * evaluation's coefficients, in the compute mode's arithmetic; the squares are summed in
+ * FP64 in a fixed order.  lambdas: host array of T doubles, each in [lambda_min, lambda_max]
+ * (else IHSBIN_ERR_LAMBDA_RANGE).  A_test: dense row-major n_test x d (any data dtype,
+ * host or device per its on_device; CSR fails with IHSBIN_ERR_UNSUPPORTED); B_test:
+ * n_test x K, row stride ldb_test >= K, F64 or F32, host or device per b_test_on_device.
+ * train_loss / test_loss: host arrays of T doubles, either may be NULL (test_loss NULL
+ * leaves A_test / B_test unread).  Synchronous on `stream`. */
+IHSBIN_API ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64_t T,
+                                 const ihsbin_matrix* A_test, const void* B_test, int64_t ldb_test,
+                                 ihsbin_dtype b_test_dtype, int b_test_on_device, double* train_loss,
+                                 double* test_loss, void* stream);
+
 /* Device time (ms) of the phases of the last sketch / build_basis / eval_path
  * calls: [0] sketch, [1] factor+inverse, [2] Gram+rhs, [3] basis loop, [4] eval. */
 IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);

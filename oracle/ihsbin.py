@@ -139,6 +139,21 @@ def gram_operator(Ahat) -> Callable[[np.ndarray], np.ndarray]:
     return lambda V: G @ V
 
 
+def path_losses(A, B, A_test, B_test, X, lambdas):
+    """The training and test losses of Section 6.1 along a path X (T x d x K):
+    L_train(lam) = 1/2 ||A x - B||_F^2 + lam/2 ||x||_F^2,  L_test(lam) = 1/2 ||A_test x - B_test||_F^2."""
+    B = B[:, None] if B.ndim == 1 else B
+    train, test = np.empty(len(lambdas)), np.empty(len(lambdas))
+    for t, lam in enumerate(lambdas):
+        x = X[t]
+        r = A @ x - B
+        train[t] = 0.5 * float(np.sum(r * r)) + 0.5 * lam * float(np.sum(x * x))
+        if A_test is not None:
+            rt = A_test @ x - B_test
+            test[t] = 0.5 * float(np.sum(rt * rt))
+    return train, test
+
+
 def gram_extended(Ahat) -> np.ndarray:
     """G = A^T A (the Hessian of the least-squares term, Section 2) with every sum
     accumulated in numpy's extended precision (longdouble: a 64-bit significand on

@@ -683,6 +683,82 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
   return s;
 }
 
+ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64_t T, const ihsbin_matrix* A_test,
+                                 const void* B_test, int64_t ldb_test, ihsbin_dtype b_test_dtype, int b_test_on_device,
+                                 double* train_loss, double* test_loss, void* stream) {
+  if (!p || !lambdas) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: NULL argument");
+  if (!p->built) return fail(IHSBIN_ERR_STATE, "path_losses: call ihsbin_build_basis first");
+  if (T <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: T must be positive");
+  if (test_loss) {
+    if (!A_test || !B_test) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: test loss without A_test / B_test");
+    if (A_test->layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "path_losses: A_test must be dense");
+    if (A_test->d != p->d || A_test->n <= 0 || A_test->ld < A_test->d || !A_test->values)
+      return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: A_test must be n_test x d with ld >= d");
+    if (A_test->dtype < IHSBIN_F64 || A_test->dtype > IHSBIN_BF16)
+      return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: bad A_test dtype");
+    if (b_test_dtype != IHSBIN_F64 && b_test_dtype != IHSBIN_F32)
+      return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: B_test must be F64 or F32");
+    if (ldb_test < p->K) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: ldb_test < K");
+  }
+  const Plan& pl = p->plan;
+  for (int64_t t = 0; t < T; ++t)
+    if (!(lambdas[t] >= pl.edges[0] && lambdas[t] <= pl.edges[pl.L]))
+      return fail(IHSBIN_ERR_LAMBDA_RANGE, "path_losses: lambda outside [lambda_min, lambda_max]");
+  if (!train_loss && !test_loss) return IHSBIN_OK;
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "path_losses");
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  CallStream cs(st);
+  ScratchScope scratch(p);
+  double *lam_dev = nullptr, *out = nullptr;
+  if ((e = prob_alloc(p, T * 8, (void**)&lam_dev, SCOPE_SCRATCH)) != cudaSuccess ||
+      (e = prob_alloc(p, 2 * T * 8, (void**)&out, SCOPE_SCRATCH)) != cudaSuccess)
+    return cuda_fail(e, "path_losses");
+  if ((e = cudaMemcpyAsync(lam_dev, lambdas, T * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return cuda_fail(e, "path_losses");
+  const void* At = nullptr;
+  int at_elem = ELEM_F64;
+  int64_t at_ld = 0, nt = 0;
+  double* Bt = nullptr;
+  if (test_loss) {
+    nt = A_test->n;
+    const size_t es = elem_size(A_test->dtype);
+    at_elem = A_test->dtype == IHSBIN_F64 ? ELEM_F64 : A_test->dtype == IHSBIN_F32 ? ELEM_F32 : ELEM_BF16;
+    At = A_test->values;
+    at_ld = A_test->ld;
+    if (!A_test->on_device) {  // packed device copy
+      void* dptr = nullptr;
+      if ((e = prob_alloc(p, (size_t)nt * p->d * es, &dptr, SCOPE_SCRATCH)) != cudaSuccess ||
+          (e = cudaMemcpy2DAsync(dptr, p->d * es, A_test->values, A_test->ld * es, p->d * es, nt,
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "path_losses");
+      At = dptr;
+      at_ld = p->d;
+    }
+    if ((e = prob_alloc(p, (size_t)nt * p->K * 8, (void**)&Bt, SCOPE_SCRATCH)) != cudaSuccess)
+      return cuda_fail(e, "path_losses");
+    const void* bsrc = B_test;
+    if (!b_test_on_device) {  // rows as given, converted on the device
+      void* dptr = nullptr;
+      const size_t bes = elem_size(b_test_dtype);
+      if ((e = prob_alloc(p, (size_t)nt * ldb_test * bes, &dptr, SCOPE_SCRATCH)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dptr, B_test, (size_t)((nt - 1) * ldb_test + p->K) * bes, cudaMemcpyHostToDevice,
+                               st)) != cudaSuccess)
+        return cuda_fail(e, "path_losses");
+      bsrc = dptr;
+    }
+    if ((e = launch_convert_to_f64(bsrc, b_test_dtype == IHSBIN_F64 ? ELEM_F64 : ELEM_F32, nt, p->K, ldb_test, Bt,
+                                   st)) != cudaSuccess)
+      return cuda_fail(e, "path_losses");
+  }
+  e = losses_device(p, lambdas, lam_dev, T, At, at_elem, at_ld, nt, Bt, train_loss ? out : nullptr,
+                    test_loss ? out + T : nullptr, st);
+  if (e == cudaSuccess && train_loss) e = cudaMemcpyAsync(train_loss, out, T * 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && test_loss) e = cudaMemcpyAsync(test_loss, out + T, T * 8, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "path_losses");
+  return check_status(p, st, "path_losses");
+}
+
 static const char* kcat_names[K_NCAT] = {
     "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",

@@ -230,6 +230,12 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
+cudaError_t csr_basis_image(ihsbin_problem* p, int compute, const int64_t* rp, const int32_t* ci, const void* val,
+                            int64_t n_rows, CBuf W, int64_t d, int64_t nc, CBuf V, cudaStream_t st);
+// training / test losses along the path (device outputs of T doubles, either may be null)
+cudaError_t losses_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, const void* At,
+                          int at_elem, int64_t at_ld, int64_t n_test, const double* Bt, double* train_out,
+                          double* test_out, cudaStream_t st);
 cudaError_t eval_device(ihsbin_problem* p, const double* lambdas_host, const double* lambdas_dev, int64_t T, void* X_dev, int x_elem,
                         cudaStream_t st);
 

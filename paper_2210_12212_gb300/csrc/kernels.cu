@@ -1887,40 +1887,12 @@ cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   return build_typed<DD, ELEM_BF16>(p, st, ev);
 }
 
-template <class Mode>
-static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, void* X,
-                              int x_elem, cudaStream_t st) {
+// The lambdas grouped by interval (the interval rule of k_eval_coef) into chunks of <= EVAL_TB, as one
+// device array [order T][chunk interval][chunk start][chunk count].
+static cudaError_t lambda_chunks(ihsbin_problem* p, const double* lam_host, int64_t T, int** dev_out, int* nch_out,
+                                 cudaStream_t st) {
   const Plan& pl = p->plan;
-  const int L = pl.L, jc = pl.jc;
-  double *edges = nullptr, *tau = nullptr, *lam0 = nullptr, *coef = nullptr;
-  int *jcount = nullptr, *tint = nullptr;
-  CK(prob_alloc(p, (L + 1) * sizeof(double), (void**)&edges, SCOPE_SCRATCH));
-  CK(prob_alloc(p, L * sizeof(double), (void**)&tau, SCOPE_SCRATCH));
-  CK(prob_alloc(p, L * sizeof(double), (void**)&lam0, SCOPE_SCRATCH));
-  CK(prob_alloc(p, L * sizeof(int), (void**)&jcount, SCOPE_SCRATCH));
-  CK(prob_alloc(p, T * sizeof(int), (void**)&tint, SCOPE_SCRATCH));
-  CK(prob_alloc(p, (size_t)T * jc * sizeof(double), (void**)&coef, SCOPE_SCRATCH));
-  CBuf coefc{coef, nullptr};  // the table in compute precision
-  if (Mode::id == 1) {
-    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc.p0, SCOPE_SCRATCH));
-    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc.p1, SCOPE_SCRATCH));
-  }
-  CK(cudaMemcpyAsync(edges, pl.edges.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(tau, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(lam0, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
-  CK(cudaMemcpyAsync(jcount, pl.jcount.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
-  {
-    KTimer kt(p, K_EVAL_COEF, st, 0, (double)T * jc * 8);
-    k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef,
-                                                 Mode::id == 1 ? (float*)coefc.p0 : nullptr,
-                                                 Mode::id == 1 ? (float*)coefc.p1 : nullptr);
-  }
-  CK(cudaGetLastError());
-  const int64_t K = p->K;
-  const int64_t rows = p->dual ? p->A.N : p->A.D;
-  const CBuf Bm = p->dual ? p->W : p->Ut;
-  const int64_t gs = (int64_t)jc * K * rows;
-  // group the lambdas by interval (the interval rule of k_eval_coef) into chunks of <= EVAL_TB
+  const int L = pl.L;
   std::vector<std::vector<int>> by(L);
   for (int64_t t = 0; t < T; ++t) {
     int lo = 0, hi = L;
@@ -1934,12 +1906,12 @@ static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const d
   for (int l = 0; l < L; ++l)
     for (size_t a = 0; a < by[l].size(); a += EVAL_TB) {
       cl.push_back(l);
-      ct0.push_back((int)torder.size() + 0);
+      ct0.push_back((int)torder.size());
       cn.push_back((int)std::min<size_t>(EVAL_TB, by[l].size() - a));
       for (size_t b = a; b < std::min(by[l].size(), a + EVAL_TB); ++b) torder.push_back(by[l][b]);
     }
   const int nch = (int)cl.size();
-  int* dev = nullptr;  // [torder T][chunk l][chunk t0][chunk n]
+  int* dev = nullptr;
   CK(prob_alloc(p, (T + 3 * (size_t)nch) * sizeof(int), (void**)&dev, SCOPE_SCRATCH));
   std::vector<int> pack(torder);
   pack.insert(pack.end(), cl.begin(), cl.end());
@@ -1947,11 +1919,226 @@ static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const d
   pack.insert(pack.end(), cn.begin(), cn.end());
   // from pageable memory: the call returns once `pack` is staged, so it may go out of scope
   CK(cudaMemcpyAsync(dev, pack.data(), pack.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  *dev_out = dev;
+  *nch_out = nch;
+  return cudaSuccess;
+}
+
+// The coefficient table coef[t][j] = tau_l theta_t^j, in FP64 and in compute precision.
+template <class Mode>
+static cudaError_t coef_table(ihsbin_problem* p, const double* lam_dev, int64_t T, CBuf* coefc, int** jcount_out,
+                              cudaStream_t st) {
+  const Plan& pl = p->plan;
+  const int L = pl.L, jc = pl.jc;
+  double *edges = nullptr, *tau = nullptr, *lam0 = nullptr, *coef = nullptr;
+  int *jcount = nullptr, *tint = nullptr;
+  CK(prob_alloc(p, (L + 1) * sizeof(double), (void**)&edges, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(double), (void**)&tau, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(double), (void**)&lam0, SCOPE_SCRATCH));
+  CK(prob_alloc(p, L * sizeof(int), (void**)&jcount, SCOPE_SCRATCH));
+  CK(prob_alloc(p, T * sizeof(int), (void**)&tint, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)T * jc * sizeof(double), (void**)&coef, SCOPE_SCRATCH));
+  *coefc = CBuf{coef, nullptr};
+  if (Mode::id == 1) {
+    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc->p0, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)T * jc * sizeof(float), &coefc->p1, SCOPE_SCRATCH));
+  }
+  CK(cudaMemcpyAsync(edges, pl.edges.data(), (L + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(tau, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(lam0, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(jcount, pl.jcount.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
+  *jcount_out = jcount;
+  KTimer kt(p, K_EVAL_COEF, st, 0, (double)T * jc * 8);
+  k_eval_coef<<<nblocks(T, 128), 128, 0, st>>>(lam_dev, T, edges, L, tau, lam0, jcount, jc, tint, coef,
+                                               Mode::id == 1 ? (float*)coefc->p0 : nullptr,
+                                               Mode::id == 1 ? (float*)coefc->p1 : nullptr);
+  return cudaGetLastError();
+}
+
+template <class Mode>
+static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, void* X,
+                              int x_elem, cudaStream_t st) {
+  const int jc = p->plan.jc;
+  CBuf coefc;
+  int* jcount = nullptr;
+  CK(coef_table<Mode>(p, lam_dev, T, &coefc, &jcount, st));
+  const int64_t K = p->K;
+  const int64_t rows = p->dual ? p->A.N : p->A.D;
+  const CBuf Bm = p->dual ? p->W : p->Ut;
+  const int64_t gs = (int64_t)jc * K * rows;
+  int* dev = nullptr;
+  int nch = 0;
+  CK(lambda_chunks(p, lam_host, T, &dev, &nch, st));
   dim3 grid(nblocks(rows * K, 256), (unsigned)nch);
   KTimer kt(p, K_EVAL, st, 2.0 * T * rows * K * jc, (double)T * rows * K * (x_elem == ELEM_F64 ? 8 : 4));
   k_eval_chunks<Mode><<<grid, 256, 0, st>>>(Bm, rows, K, jc, gs, dev + T, dev + T + nch, dev + T + 2 * nch, dev, coefc,
                                             jcount, X, x_elem);
   return cudaGetLastError();
+}
+
+// ============================================= losses along the path (Section 6.1), without X
+// For a chunk of lambdas of interval l: ssq[pos][block] = sum over the block's entries (i, r) of
+// (sum_j coef[t][j] V_l[j][r][i] - target[i][r])^2  (target null: plain squares), pos = the lambda's
+// position in the chunk order; the residual in compute precision, its square summed in FP64.
+template <class Mode>
+__global__ void __launch_bounds__(256) k_resid_ssq_chunks(CBuf Vm, int64_t rows, int64_t K, int jc, int64_t gs,
+                                                          const int* chunk_l, const int* chunk_t0, const int* chunk_n,
+                                                          const int* torder, CBuf coef, const int* jcount,
+                                                          const double* target, double* ssq) {
+  __shared__ double red[EVAL_TB][8];
+  const int c = blockIdx.y;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = e < rows * K;
+  const int64_t r = in ? e / rows : 0, i = in ? e % rows : 0;
+  const int l = chunk_l[c], nq = chunk_n[c], t0 = chunk_t0[c];
+  const int jn = jcount[l];
+  int tq[EVAL_TB];
+  typename Mode::V acc[EVAL_TB];
+#pragma unroll
+  for (int q = 0; q < EVAL_TB; ++q) {
+    tq[q] = q < nq ? torder[t0 + q] : 0;
+    acc[q] = Mode::zero();
+  }
+  if (in)
+    for (int j = 0; j < jn; ++j) {
+      const typename Mode::V b = Mode::ld(Vm, (int64_t)l * gs + ((int64_t)j * K + r) * rows + i);
+#pragma unroll
+      for (int q = 0; q < EVAL_TB; ++q)
+        if (q < nq) acc[q] = Mode::add(acc[q], Mode::mul(Mode::ld(coef, (int64_t)tq[q] * jc + j), b));
+    }
+  const typename Mode::V tg = (in && target) ? Mode::from_d(target[i * K + r]) : Mode::zero();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < EVAL_TB; ++q) {
+    double v = 0.0;
+    if (in && q < nq) {
+      v = Mode::to_d(Mode::sub(acc[q], tg));
+      v *= v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[q][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < nq) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    ssq[(int64_t)(t0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+  }
+}
+// out[t] = 1/2 sum_b ssq[pos][b] (+ 1/2 lambda_t sum_b xsq[pos][b]); fixed summation order
+__global__ void k_loss_reduce(const double* ssq, const double* xsq, int64_t nb, int64_t nbx, const int* torder,
+                              int64_t T, const double* lam, double* out) {
+  const int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= T) return;
+  double s = 0.0;
+  for (int64_t b = 0; b < nb; ++b) s += ssq[pos * nb + b];
+  const int t = torder[pos];
+  double v = 0.5 * s;
+  if (xsq) {
+    double x = 0.0;
+    for (int64_t b = 0; b < nbx; ++b) x += xsq[pos * nbx + b];
+    v += 0.5 * lam[t] * x;
+  }
+  out[t] = v;
+}
+
+// V = M W for every basis column (l, j, r): M dense n_M x d (row-major, row stride ld, element type ET;
+// transposed view when trans), W = the primal basis (L x jc x K x d).  V: (L jc K) x n_M column-major.
+template <class Mode, int ET>
+static cudaError_t basis_image_dense(ihsbin_problem* p, const void* M, int64_t ld, bool trans, int64_t nM, CBuf PB,
+                                     int64_t d, int64_t ncols, CBuf V, cudaStream_t st) {
+  GemmShape sh{nM, ncols, d, 0};
+  KTimer kt(p, K_EVAL, st, 2.0 * nM * ncols * d, (double)nM * d * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
+  if (trans)
+    return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{M, ld}, LdCColB<Mode>{PB, d, 0, nullptr},
+                                               EpStoreColMajor<Mode>{V, nM, 0, nullptr}, st);
+  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdAhatRow<Mode, ET>{M, ld}, LdCColB<Mode>{PB, d, 0, nullptr},
+                                             EpStoreColMajor<Mode>{V, nM, 0, nullptr}, st);
+}
+template <class Mode>
+static cudaError_t basis_image_dense_any(ihsbin_problem* p, const void* M, int elem, int64_t ld, bool trans,
+                                         int64_t nM, CBuf PB, int64_t d, int64_t ncols, CBuf V, cudaStream_t st) {
+  if (elem == ELEM_F64) return basis_image_dense<Mode, ELEM_F64>(p, M, ld, trans, nM, PB, d, ncols, V, st);
+  if (elem == ELEM_F32) return basis_image_dense<Mode, ELEM_F32>(p, M, ld, trans, nM, PB, d, ncols, V, st);
+  return basis_image_dense<Mode, ELEM_BF16>(p, M, ld, trans, nM, PB, d, ncols, V, st);
+}
+
+// 1/2 ||V-combination - target||^2 per lambda into out (device, T), plus the ridge term from xsq
+template <class Mode>
+static cudaError_t resid_losses(ihsbin_problem* p, CBuf V, int64_t rows, const double* target, CBuf coefc,
+                                const int* jcount, const int* chunks, int nch, int64_t T, const double* lam_dev,
+                                const double* xsq, int64_t nbx, double* out, double** ssq_out, int64_t* nb_out,
+                                cudaStream_t st) {
+  const int jc = p->plan.jc;
+  const int64_t K = p->K, gs = (int64_t)jc * K * rows, nb = nblocks(rows * K, 256);
+  double* ssq = nullptr;
+  CK(prob_alloc(p, (size_t)T * nb * sizeof(double), (void**)&ssq, SCOPE_SCRATCH));
+  {
+    KTimer kt(p, K_EVAL, st, 2.0 * T * rows * K * jc, (double)rows * K * jc * 8 * nch);
+    k_resid_ssq_chunks<Mode><<<dim3((unsigned)nb, (unsigned)nch), 256, 0, st>>>(
+        V, rows, K, jc, gs, chunks + T, chunks + T + nch, chunks + T + 2 * nch, chunks, coefc, jcount, target, ssq);
+    CK(cudaGetLastError());
+  }
+  if (ssq_out) {  // keep the per-block sums (the squared norms of x)
+    *ssq_out = ssq;
+    *nb_out = nb;
+    return cudaSuccess;
+  }
+  k_loss_reduce<<<nblocks(T, 128), 128, 0, st>>>(ssq, xsq, nb, nbx, chunks, T, lam_dev, out);
+  return cudaGetLastError();
+}
+
+template <class Mode>
+static cudaError_t losses_typed(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T,
+                                const void* At, int at_elem, int64_t at_ld, int64_t n_test, const double* Bt,
+                                double* train_out, double* test_out, cudaStream_t st) {
+  const Plan& pl = p->plan;
+  const int64_t K = p->K, d = p->d, ncols = (int64_t)pl.L * pl.jc * K;
+  const CBuf PB = p->dual ? p->W : p->Ut;  // the primal basis: (L x jc x K) columns of length d
+  CBuf coefc;
+  int* jcount = nullptr;
+  CK(coef_table<Mode>(p, lam_dev, T, &coefc, &jcount, st));
+  int* chunks = nullptr;
+  int nch = 0;
+  CK(lambda_chunks(p, lam_host, T, &chunks, &nch, st));
+  cudaError_t err = cudaSuccess;
+  const int cm = Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2;
+  if (train_out) {
+    // ||x(lambda)||^2 from the basis itself, then A W and the residuals against B
+    double* xsq = nullptr;
+    int64_t nbx = 0;
+    CK(resid_losses<Mode>(p, PB, d, nullptr, coefc, jcount, chunks, nch, T, lam_dev, nullptr, 0, nullptr, &xsq, &nbx, st));
+    const Tall& A = p->A;
+    const int64_t n = p->n;
+    CBuf V = alloc_cbuf(p, cm, (size_t)ncols * n, SCOPE_SCRATCH, &err);
+    CK(err);
+    if (A.layout == IHSBIN_CSR) {
+      // rows of A: CSR(A_hat) over-determined, CSR(A_hat^T) for the dual
+      CK(csr_basis_image(p, cm, p->dual ? A.rpT : A.rp, p->dual ? A.ciT : A.ci, p->dual ? A.valT : A.val, n, PB, d,
+                         ncols, V, st));
+    } else {
+      CK(basis_image_dense_any<Mode>(p, A.A, A.elem, A.ld, p->dual, n, PB, d, ncols, V, st));
+    }
+    CK(resid_losses<Mode>(p, V, n, p->B, coefc, jcount, chunks, nch, T, lam_dev, xsq, nbx, train_out, nullptr,
+                          nullptr, st));
+  }
+  if (test_out) {
+    CBuf V = alloc_cbuf(p, cm, (size_t)ncols * n_test, SCOPE_SCRATCH, &err);
+    CK(err);
+    CK(basis_image_dense_any<Mode>(p, At, at_elem, at_ld, false, n_test, PB, d, ncols, V, st));
+    CK(resid_losses<Mode>(p, V, n_test, Bt, coefc, jcount, chunks, nch, T, lam_dev, nullptr, 0, test_out, nullptr,
+                          nullptr, st));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t losses_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, const void* At,
+                          int at_elem, int64_t at_ld, int64_t n_test, const double* Bt, double* train_out,
+                          double* test_out, cudaStream_t st) {
+  if (p->plan.compute == IHSBIN_COMPUTE_F64)
+    return losses_typed<F64>(p, lam_host, lam_dev, T, At, at_elem, at_ld, n_test, Bt, train_out, test_out, st);
+  return losses_typed<DD>(p, lam_host, lam_dev, T, At, at_elem, at_ld, n_test, Bt, train_out, test_out, st);
 }
 
 cudaError_t eval_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, void* X,

@@ -80,6 +80,7 @@ EXPORTED = [
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
+    "ihsbin_path_losses",
 ]
 KCAT_COUNT = 27
 
@@ -120,6 +121,7 @@ def load(path: Optional[str] = None):
         "ihsbin_serve_destroy": [vp],
         "ihsbin_serve": [vp, C.POINTER(ServeConfig), vp, i64, vp, vp, vp],
         "ihsbin_gram_export": [vp, vp],
+        "ihsbin_path_losses": [vp, vp, i64, C.POINTER(Matrix), vp, i64, C.c_int, C.c_int, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -256,6 +258,39 @@ class Problem:
         _check(_lib.ihsbin_eval_path(self.h, _ptr(lam), T, _ptr(out), DTYPE[x_dtype], on_dev,
                                      _stream(stream)))
         return out
+
+    def path_losses(self, lambdas, A_test=None, B_test=None, *, test_dtype: Optional[str] = None,
+                    train: bool = True, stream=None):
+        """Section 6.1's losses without forming X: (train, test) arrays of T doubles (either None
+        when not asked for).  A_test: dense n_test x d numpy array or CUDA tensor (element type
+        `test_dtype`, default the array's own); B_test: (n_test,) or (n_test x K)."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        T = lam.shape[0]
+        tr = np.empty(T) if train else None
+        te = None
+        keep = []
+        mref, bptr, ldb, bdt, bdev = None, None, 0, F64, 0
+        if A_test is not None:
+            if test_dtype is None:
+                test_dtype = {"float64": "f64", "float32": "f32", "torch.float64": "f64",
+                              "torch.float32": "f32", "torch.bfloat16": "bf16"}[str(A_test.dtype)]
+            m = _matrix(A_test, dtype=test_dtype, keep=keep)
+            mref = C.byref(m)
+            if B_test.ndim == 1:
+                B_test = B_test.reshape(-1, 1)
+            if hasattr(B_test, "is_cuda"):
+                bdt = F64 if str(B_test.dtype) == "torch.float64" else F32
+                ldb = B_test.stride(0)
+            else:
+                B_test = np.ascontiguousarray(B_test)
+                bdt = F64 if B_test.dtype == np.float64 else F32
+                ldb = B_test.shape[1]
+            keep.append(B_test)
+            bptr, bdev = _ptr(B_test), _on_device(B_test)
+            te = np.empty(T)
+        _check(_lib.ihsbin_path_losses(self.h, _ptr(lam), T, mref, bptr, ldb, bdt, bdev, _ptr(tr), _ptr(te),
+                                       _stream(stream)))
+        return tr, te
 
     # -- exports ---------------------------------------------------------------------------
     def sketch_export(self, cap: int):

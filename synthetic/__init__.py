@@ -14,6 +14,7 @@ from .configs import (  # noqa: F401
     Problem,
     CONFIGS,
     make_problem,
+    make_split,
     spectral_norm_sq,
     lambda_grid,
     to_bf16_bits,

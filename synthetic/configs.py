@@ -30,7 +30,7 @@ from typing import Optional
 
 import numpy as np
 
-__all__ = ["Problem", "CONFIGS", "make_problem", "spectral_norm_sq", "lambda_grid",
+__all__ = ["Problem", "CONFIGS", "make_problem", "make_split", "spectral_norm_sq", "lambda_grid",
            "to_bf16_bits", "bf16_bits_to_f32", "serving_requests"]
 
 
@@ -310,6 +310,28 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
                            if f.name not in ("name", "layout", "storage", "sketch")
                            and getattr(p, f.name) is not None})
     return p
+
+
+def make_split(name: str, n_test: int, seed: int = 0, **overrides):
+    """A held-out split as in Section 6 (part of the data kept as the test set): the workload is drawn
+    with n + n_test rows from one model and split by rows.  Returns (train Problem, A_test, B_test):
+    A_test dense (n_test x d, the training problem's storage type; CSR test rows are densified),
+    B_test (n_test x K) float64."""
+    n = overrides.pop("n", CONFIGS[name]["n"])
+    full = make_problem(name, seed=seed, n=n + n_test, **overrides)
+    B_test = np.ascontiguousarray(full.B[n:])
+    if full.layout == "csr":
+        e0, e1 = int(full.row_ptr[n]), int(full.row_ptr[-1])
+        A_test = np.zeros((n_test, full.d), dtype=full.val.dtype)
+        rows = np.repeat(np.arange(n_test), np.diff(full.row_ptr[n:]))
+        A_test[rows, full.col_idx[e0:e1]] = full.val[e0:e1]
+        train = dataclasses.replace(full, n=n, row_ptr=np.ascontiguousarray(full.row_ptr[:n + 1]),
+                                    col_idx=np.ascontiguousarray(full.col_idx[:e0]),
+                                    val=np.ascontiguousarray(full.val[:e0]), B=np.ascontiguousarray(full.B[:n]))
+    else:
+        A_test = np.ascontiguousarray(full.A[n:])
+        train = dataclasses.replace(full, n=n, A=np.ascontiguousarray(full.A[:n]), B=np.ascontiguousarray(full.B[:n]))
+    return train, A_test, B_test
 
 
 def _from_cached(name, cfg, z) -> Problem:

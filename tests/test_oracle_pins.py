@@ -377,3 +377,36 @@ def test_gram_entries_extended_match_full():
     A = rng.standard_normal((300, 9)).astype(np.float32)
     rows, cols = rng.integers(0, 9, 40), rng.integers(0, 9, 40)
     assert np.array_equal(ob.gram_entries_extended(A, rows, cols), ob.gram_extended(A)[rows, cols])
+
+
+# ---- losses along the path (Section 6.1)
+def test_train_loss_closed_form_at_ridge_solution():
+    # at x*(lam) the normal equations give ||A x - b||^2 + lam ||x||^2 = ||b||^2 - b^T A x*
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((60, 9))
+    b = rng.standard_normal((60, 2))
+    lams = np.array([0.01, 0.5, 7.0])
+    X = np.stack([ob.exact_ridge(A, b, lam) for lam in lams])
+    train, _ = ob.path_losses(A, b, None, None, X, lams)
+    closed = [0.5 * (np.sum(b * b) - np.sum(b * (A @ X[t]))) for t in range(3)]
+    np.testing.assert_allclose(train, closed, rtol=1e-12)
+
+
+def test_test_loss_on_training_data_drops_the_ridge_term():
+    rng = np.random.default_rng(22)
+    A = rng.standard_normal((40, 6))
+    b = rng.standard_normal((40, 1))
+    lams = np.array([0.1, 1.0])
+    X = rng.standard_normal((2, 6, 1))
+    train, test = ob.path_losses(A, b, A, b, X, lams)
+    np.testing.assert_allclose(test, train - 0.5 * lams * np.sum(X * X, axis=(1, 2)), rtol=1e-13)
+
+
+def test_split_keeps_the_model():
+    from synthetic import make_problem, make_split
+    full = make_problem("c2_small", seed=0, n=3400)
+    train, At, Bt = make_split("c2_small", 400, seed=0)
+    assert train.n == 3000 and At.shape == (400, train.d) and Bt.shape == (400, 1)
+    assert np.array_equal(train.A, full.A[:3000]) and np.array_equal(At, full.A[3000:])
+    tr, A2, B2 = make_split("c3_small", 50, seed=0)
+    assert tr.row_ptr.shape == (tr.n + 1,) and A2.shape == (50, tr.d)
