@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--requests", type=int, default=128, help="serving workload (c5): number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
+    ap.add_argument("--losses", type=int, default=0, metavar="N_TEST",
+                    help="validation workload: N_TEST held-out rows drawn with the training rows; a step "
+                         "returns the training and test losses of every lambda (Section 6.1) instead of X")
     return ap.parse_args()
 
 
@@ -332,8 +335,12 @@ def main():
     if args.config == "c5":
         serving_arm(args)
         return
-    from synthetic import make_problem
-    prob = make_problem(args.config, seed=0)
+    from synthetic import make_problem, make_split
+    A_test = B_test = None
+    if args.losses > 0:
+        prob, A_test, B_test = make_split(args.config, args.losses, seed=0)
+    else:
+        prob = make_problem(args.config, seed=0)
     note(f"workload {args.config} generated")
     par = None if args.auto else load_params(args.config[:-1] if args.config == "c3t" else args.config)
     if args.impl == "reference":
@@ -377,10 +384,21 @@ def main():
         make_host = lambda: ihs.Problem(ctx, A_pin, np.ascontiguousarray(prob.B), dtype=prob.storage)
         host_bytes = A_pin.numel() * A_pin.element_size()
     p = make_dev()
+    if A_test is not None:
+        At_np = np.ascontiguousarray(A_test)
+        At_dev = torch.from_numpy(At_np.view(np.int16) if prob.storage == "bf16" else At_np).cuda()
+        Bt_dev = torch.from_numpy(np.ascontiguousarray(B_test)).cuda()
+        At_pin = torch.from_numpy(At_np.view(np.int16) if prob.storage == "bf16" else At_np).pin_memory()
+        Bt_pin = torch.from_numpy(np.ascontiguousarray(B_test)).pin_memory()
+        host_bytes += At_pin.numel() * At_pin.element_size() + Bt_pin.numel() * 8
 
     def step(pp, out=None):
         pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, entries=entries, stream=stream)
         pp.build_basis(prob.lambda_min, prob.lambda_max, stream=stream, **bkw)
+        if A_test is not None:  # losses of every lambda, X never formed
+            dev = out is not None
+            return pp.path_losses(prob.lambdas, At_dev if dev else At_pin, Bt_dev if dev else Bt_pin,
+                                  test_dtype=prob.storage, stream=stream)
         return pp.eval_path(prob.lambdas, out=out, stream=stream)
 
     for _ in range(max(args.warmup, 0)):
@@ -432,14 +450,20 @@ def main():
         te = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         e2e = {"value": job_throughput(world, ke, te), "unit": "paths/s",
                "h2d_bytes_per_step": int(host_bytes + prob.B.nbytes + prob.lambdas.nbytes),
-               "d2h_bytes_per_step": int(Xh.nbytes)}
+               "d2h_bytes_per_step": int(sum(a.nbytes for a in Xh) if isinstance(Xh, tuple) else Xh.nbytes)}
 
     # ---- parity of the timed result against the FP64 oracle (sampled lambdas, rank 0)
     check = None
     note("timed region done")
     if rank == 0 and not args.no_check:
+        if A_test is not None:
+            losses = step(p, X_dev)
+            p.eval_path(prob.lambdas, out=X_dev, stream=stream)
+            torch.cuda.synchronize()
         check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6,
                               eps=args.eps)
+        if A_test is not None:
+            check["losses"] = losses_check(prob, A_test, B_test, X_dev.cpu().numpy(), losses)
 
     # ---- roofline of the dominant kernel (largest device time in the timed region)
     dom = max(stats.items(), key=lambda kv: kv[1][1])
@@ -468,7 +492,10 @@ def main():
             "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
-            "config": {"workload": WORKLOADS.get(args.config, args.config), "jmax": args.jmax,
+            "config": {"workload": WORKLOADS.get(args.config, args.config) + (
+                           f"; plus {args.losses} held-out rows of the same model, a step returns the training "
+                           f"and test losses of every lambda (X not formed)" if args.losses else ""),
+                       "jmax": args.jmax,
                        "storage": prob.storage, "l2": ("inputs larger than L2 (A is 256 MiB)" if args.config == "c2"
                                                        else "see workload"),
                        "params": f"tests/golden/{args.config}_params.json",
@@ -515,6 +542,19 @@ def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
             "oracle_max_rel_dist_to_exact_ridge": max(conv)}
 
 
+def losses_check(prob, A_test, B_test, X, losses):
+    """The device losses against the oracle's losses of the same X at 9 lambdas (relative)."""
+    from oracle import ihsbin as ob
+    from synthetic.configs import bf16_bits_to_f32
+    idx = np.unique(np.linspace(0, len(prob.lambdas) - 1, 9).round().astype(int))
+    At = bf16_bits_to_f32(A_test).astype(np.float64) if prob.storage == "bf16" else A_test.astype(np.float64)
+    tr, te = ob.path_losses(oracle_matrix(prob), prob.B, At, B_test, X[idx], prob.lambdas[idx])
+    rel = lambda a, b: float(np.max(np.abs(a - b) / np.abs(b)))
+    return {"max_rel_err_train": rel(losses[0][idx], tr), "max_rel_err_test": rel(losses[1][idx], te),
+            "lambdas_checked": len(idx), "n_test": int(A_test.shape[0]),
+            "test_loss_argmin_lambda": float(prob.lambdas[int(np.argmin(losses[1]))])}
+
+
 def measured_peak(key, fallback):
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
@@ -526,7 +566,8 @@ def measured_peak(key, fallback):
 # Categories whose binding resource is HBM: every step of the recursion streams the live
 # intervals' preconditioner slices (12 bytes per entry), which do not stay in L2; the
 # elementwise steps of the recursion and the slicing / joining kernels move data only.
-HBM_BOUND = ("loop_precond_tc", "loop_precond_update", "loop_slice", "factor_slice", "gram_slice", "gram_combine")
+HBM_BOUND = ("loop_precond_tc", "loop_precond_update", "loop_slice", "factor_slice", "gram_slice", "gram_combine",
+             "loss_slice", "loss_resid")
 
 
 def kernel_peak(name, compute):
@@ -534,7 +575,7 @@ def kernel_peak(name, compute):
     if name in HBM_BOUND:
         pk, how = measured_peak("hbm_gbs", 6800.0)
         return "hbm", pk, f"copy bandwidth (MEASURED_PEAKS.json hbm_gbs), {how}"
-    if name in ("gram_tc_mma", "loop_gram_tc"):  # BF16 tensor-core slice products, inside a long step
+    if name in ("gram_tc_mma", "loop_gram_tc", "loss_image_tc"):  # BF16 tensor-core slice products, inside a long step
         pk, how = measured_peak("bf16_tflops_sustained", 1700.0)
         return "tensor", pk, f"cuBLAS bf16 sustained (MEASURED_PEAKS.json), {how}"
     if compute == "f64":

@@ -290,7 +290,7 @@ IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
  * is also bracketed by CUDA events on the stream it runs on and its device
  * time is added at the call's synchronisation point.  Categories 0 ..
  * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 27
+#define IHSBIN_KCAT_COUNT 31
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,

@@ -763,7 +763,8 @@ static const char* kcat_names[K_NCAT] = {
     "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
     "eval_coef", "eval", "sparse", "gram_slice", "gram_tc_mma", "gram_combine", "loop_slice", "loop_gram_tc",
-    "loop_precond_tc", "factor_slice", "inverse_tc", "trtri_tc", "factor_syrk_tc"};
+    "loop_precond_tc", "factor_slice", "inverse_tc", "trtri_tc", "factor_syrk_tc", "loss_slice", "loss_image_tc",
+    "loss_image", "loss_resid"};
 
 ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");

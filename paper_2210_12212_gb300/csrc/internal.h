@@ -66,7 +66,7 @@ enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
   K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
-  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_NCAT
+  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_LOSS_SLICE, K_LOSS_TC, K_LOSS_IMAGE, K_LOSS_RESID, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -215,6 +215,9 @@ cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int gr
 cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K, int64_t nvec, int groups,
                           int TH, __nv_bfloat16* out, int* e, cudaStream_t st);
 int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int cap);
+// rows of a row-major data matrix (element type elem, row stride ld, K entries), tile height TH
+cudaError_t oz_slice_data_rows(const void* X, int elem, int64_t ld, int64_t K, int64_t nvec, int TH,
+                               __nv_bfloat16* out, int* e, cudaStream_t st);
 // The recursion's elementwise steps with the slicing of their output fused (one CTA per column,
 // the column in D x 8 bytes of shared memory; oz_fused_ok(D) says whether it fits).
 bool oz_fused_ok(int64_t D);
@@ -230,8 +233,9 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);
 cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStream_t st);
+cudaError_t basis_transpose(ihsbin_problem* p, int compute, CBuf W, int64_t d, int64_t nc, CBuf WT, cudaStream_t st);
 cudaError_t csr_basis_image(ihsbin_problem* p, int compute, const int64_t* rp, const int32_t* ci, const void* val,
-                            int64_t n_rows, CBuf W, int64_t d, int64_t nc, CBuf V, cudaStream_t st);
+                            int64_t n_rows, CBuf WT, int64_t nc, CBuf V, cudaStream_t st);
 // training / test losses along the path (device outputs of T doubles, either may be null)
 cudaError_t losses_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, const void* At,
                           int at_elem, int64_t at_ld, int64_t n_test, const double* Bt, double* train_out,

@@ -1977,14 +1977,15 @@ static cudaError_t eval_typed(ihsbin_problem* p, const double* lam_host, const d
 }
 
 // ============================================= losses along the path (Section 6.1), without X
-// For a chunk of lambdas of interval l: ssq[pos][block] = sum over the block's entries (i, r) of
+// For a chunk of lambdas of interval l: ssq[pos][boff + block] = sum over the block's entries (i, r) of
 // (sum_j coef[t][j] V_l[j][r][i] - target[i][r])^2  (target null: plain squares), pos = the lambda's
 // position in the chunk order; the residual in compute precision, its square summed in FP64.
 template <class Mode>
 __global__ void __launch_bounds__(256) k_resid_ssq_chunks(CBuf Vm, int64_t rows, int64_t K, int jc, int64_t gs,
                                                           const int* chunk_l, const int* chunk_t0, const int* chunk_n,
                                                           const int* torder, CBuf coef, const int* jcount,
-                                                          const double* target, double* ssq) {
+                                                          const double* target, double* ssq, int64_t nbt,
+                                                          int64_t boff) {
   __shared__ double red[EVAL_TB][8];
   const int c = blockIdx.y;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -2023,7 +2024,7 @@ __global__ void __launch_bounds__(256) k_resid_ssq_chunks(CBuf Vm, int64_t rows,
   if (threadIdx.x < nq) {
     double s = 0.0;
     for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
-    ssq[(int64_t)(t0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+    ssq[(int64_t)(t0 + threadIdx.x) * nbt + boff + blockIdx.x] = s;
   }
 }
 // out[t] = 1/2 sum_b ssq[pos][b] (+ 1/2 lambda_t sum_b xsq[pos][b]); fixed summation order
@@ -2042,51 +2043,140 @@ __global__ void k_loss_reduce(const double* ssq, const double* xsq, int64_t nb, 
   }
   out[t] = v;
 }
+// V[j][i] = the float-float value of the exact partials of (row i, column j), summed over S splits
+__global__ void k_oz_join_cols(const long long* hi, const long long* lo, int S, int64_t M, int64_t N, const int* ea,
+                               const int* eb, CBuf V) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  const int64_t i = e % M, j = e / M;
+  long long h = 0, w = 0;
+  for (int s = 0; s < S; ++s) {
+    h += hi[(int64_t)s * M * N + e];
+    w += lo[(int64_t)s * M * N + e];
+  }
+  DD::st(V, e, oz_join(h, w, ea[i], eb[j]));
+}
 
-// V = M W for every basis column (l, j, r): M dense n_M x d (row-major, row stride ld, element type ET;
-// transposed view when trans), W = the primal basis (L x jc x K x d).  V: (L jc K) x n_M column-major.
+// The matrix of one loss term, by rows: dense row-major (rows of M), the transposed view of a dense
+// row-major M (its columns), or CSR.  target: rows x K row-major FP64 (null: no target).
+struct LossSrc {
+  int kind = 0;  // 0 dense rows, 1 dense columns, 2 CSR
+  const void* M = nullptr;
+  int elem = ELEM_F64;
+  int64_t ld = 0;
+  const int64_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const void* val = nullptr;
+  int64_t rows = 0;
+  const double* target = nullptr;
+};
+struct LossCtx {
+  CBuf PB;  // the primal basis: ncols columns of length d
+  int64_t d = 0, ncols = 0;
+  CBuf coefc;
+  const int* jcount = nullptr;
+  const int* chunks = nullptr;
+  int nch = 0;
+  int64_t T = 0;
+  // exact-slice images: the basis cut once (tile height 32)
+  __nv_bfloat16* Bs = nullptr;
+  int* eb = nullptr;
+  CBuf PBT;  // transposed basis for CSR rows
+};
+
+constexpr size_t LOSS_CHUNK_BYTES = size_t(2) << 30;  // scratch for one block of rows
+constexpr int64_t LOSS_CHUNK_ROWS = 32768;             // and at most this many rows
+
+// V = M0 PB on the CUDA cores: M0's rows (or, trans, its columns) x the basis columns, column-major
 template <class Mode, int ET>
-static cudaError_t basis_image_dense(ihsbin_problem* p, const void* M, int64_t ld, bool trans, int64_t nM, CBuf PB,
-                                     int64_t d, int64_t ncols, CBuf V, cudaStream_t st) {
-  GemmShape sh{nM, ncols, d, 0};
-  KTimer kt(p, K_EVAL, st, 2.0 * nM * ncols * d, (double)nM * d * (ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2));
-  if (trans)
-    return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{M, ld}, LdCColB<Mode>{PB, d, 0, nullptr},
-                                               EpStoreColMajor<Mode>{V, nM, 0, nullptr}, st);
-  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdAhatRow<Mode, ET>{M, ld}, LdCColB<Mode>{PB, d, 0, nullptr},
-                                             EpStoreColMajor<Mode>{V, nM, 0, nullptr}, st);
-}
-template <class Mode>
-static cudaError_t basis_image_dense_any(ihsbin_problem* p, const void* M, int elem, int64_t ld, bool trans,
-                                         int64_t nM, CBuf PB, int64_t d, int64_t ncols, CBuf V, cudaStream_t st) {
-  if (elem == ELEM_F64) return basis_image_dense<Mode, ELEM_F64>(p, M, ld, trans, nM, PB, d, ncols, V, st);
-  if (elem == ELEM_F32) return basis_image_dense<Mode, ELEM_F32>(p, M, ld, trans, nM, PB, d, ncols, V, st);
-  return basis_image_dense<Mode, ELEM_BF16>(p, M, ld, trans, nM, PB, d, ncols, V, st);
+static cudaError_t image_fma(const GemmShape& sh, const void* M0, int64_t ld, bool trans, CBuf PB, int64_t d, CBuf V,
+                             cudaStream_t st) {
+  const EpStoreColMajor<Mode> ep{V, sh.M, 0, nullptr};
+  const LdCColB<Mode> lb{PB, d, 0, nullptr};
+  if (trans) return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdTrans<Mode, ET>{M0, ld}, lb, ep, st);
+  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdAhatRow<Mode, ET>{M0, ld}, lb, ep, st);
 }
 
-// 1/2 ||V-combination - target||^2 per lambda into out (device, T), plus the ridge term from xsq
+static size_t elem_bytes(int elem) { return elem == ELEM_F64 ? 8 : elem == ELEM_F32 ? 4 : 2; }
+
+// sum of squared residuals of every lambda over the rows of `s` into ssq (T x nbt, positions in the
+// chunk order); rows taken in blocks so that the images fit LOSS_CHUNK_BYTES
 template <class Mode>
-static cudaError_t resid_losses(ihsbin_problem* p, CBuf V, int64_t rows, const double* target, CBuf coefc,
-                                const int* jcount, const int* chunks, int nch, int64_t T, const double* lam_dev,
-                                const double* xsq, int64_t nbx, double* out, double** ssq_out, int64_t* nb_out,
-                                cudaStream_t st) {
+static cudaError_t loss_term(ihsbin_problem* p, const LossSrc& s, LossCtx& c, double** ssq_out, int64_t* nbt_out,
+                             cudaStream_t st) {
+  const int64_t K = p->K, d = c.d, nc = c.ncols;
   const int jc = p->plan.jc;
-  const int64_t K = p->K, gs = (int64_t)jc * K * rows, nb = nblocks(rows * K, 256);
+  const int cm = Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2;
+  const bool tc = Mode::id == 1 && p->plan.loop == IHSBIN_LOOP_SLICES && s.kind == 0;
+  const int64_t dpad = (d + 31) / 32 * 32;
+  int S0 = tc ? oz_pick_split_mnk(std::min<int64_t>(s.rows, 1 << 16), nc, d, 1, 32, 16) : 0;
+  const size_t per_row = (size_t)8 * nc + (tc ? (size_t)16 * S0 * nc + (size_t)12 * dpad + 4 : 0);
+  int64_t nr = std::max<int64_t>(128, (int64_t)(LOSS_CHUNK_BYTES / per_row) / 128 * 128);
+  nr = std::min(std::min(nr, LOSS_CHUNK_ROWS), s.rows);
+  const int64_t nblk_rows = (s.rows + nr - 1) / nr;
+  const int64_t last = s.rows - (nblk_rows - 1) * nr;
+  int64_t nbt = 0;
+  for (int64_t b = 0; b < nblk_rows; ++b) nbt += nblocks((b + 1 < nblk_rows ? nr : last) * K, 256);
   double* ssq = nullptr;
-  CK(prob_alloc(p, (size_t)T * nb * sizeof(double), (void**)&ssq, SCOPE_SCRATCH));
-  {
-    KTimer kt(p, K_EVAL, st, 2.0 * T * rows * K * jc, (double)rows * K * jc * 8 * nch);
-    k_resid_ssq_chunks<Mode><<<dim3((unsigned)nb, (unsigned)nch), 256, 0, st>>>(
-        V, rows, K, jc, gs, chunks + T, chunks + T + nch, chunks + T + 2 * nch, chunks, coefc, jcount, target, ssq);
+  CK(prob_alloc(p, (size_t)c.T * nbt * sizeof(double), (void**)&ssq, SCOPE_SCRATCH));
+  cudaError_t err = cudaSuccess;
+  CBuf V = alloc_cbuf(p, cm, (size_t)nr * nc, SCOPE_SCRATCH, &err);
+  CK(err);
+  __nv_bfloat16* As = nullptr;
+  int* ea = nullptr;
+  long long *hi = nullptr, *lo = nullptr;
+  int Smax = 1;
+  if (tc) {
+    Smax = std::max(oz_pick_split_mnk(nr, nc, d, 1, 32, 16), oz_pick_split_mnk(last, nc, d, 1, 32, 16));
+    CK(prob_alloc(p, oz_vec_elems(nr, d, 128) * 2, (void**)&As, SCOPE_SCRATCH));
+    CK(prob_alloc(p, oz_vec_exps(nr, 128) * 4, (void**)&ea, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)Smax * nr * nc * 8, (void**)&hi, SCOPE_SCRATCH));
+    CK(prob_alloc(p, (size_t)Smax * nr * nc * 8, (void**)&lo, SCOPE_SCRATCH));
+  }
+  const size_t es = elem_bytes(s.elem);
+  int64_t boff = 0;
+  for (int64_t b = 0; b < nblk_rows; ++b) {
+    const int64_t r0 = b * nr, rows = b + 1 < nblk_rows ? nr : last;
+    if (s.kind == 2) {
+      CK(csr_basis_image(p, cm, s.rp + r0, s.ci, s.val, rows, c.PBT, nc, V, st));
+    } else if (tc) {
+      const char* M0 = (const char*)s.M + (size_t)r0 * s.ld * es;
+      {
+        KTimer kt(p, K_LOSS_SLICE, st, 0, (double)rows * d * es + (double)oz_vec_elems(rows, d, 128) * 2);
+        CK(oz_slice_data_rows(M0, s.elem, s.ld, d, rows, 128, As, ea, st));
+      }
+      const int S = oz_pick_split_mnk(rows, nc, d, 1, 32, 16);
+      {
+        OzGemm q;
+        q.As = As; q.ea = ea; q.Bs = c.Bs; q.eb = c.eb;
+        q.M = rows; q.N = nc; q.K = d; q.groups = 1; q.NT = 32; q.ksplit = S;
+        q.ohi = hi; q.olo = lo; q.status = p->status;
+        KTimer kt(p, K_LOSS_TC, st, oz_pair_flops(rows, nc, d),
+                  (double)oz_vec_elems(rows, d, 128) * 2 + (double)oz_vec_elems(nc, d, 32) * 2 + 16.0 * S * rows * nc);
+        CK(oz_gemm(q, st));
+      }
+      KTimer kt(p, K_LOSS_SLICE, st, 0, 16.0 * S * rows * nc + 8.0 * rows * nc);
+      k_oz_join_cols<<<nblocks(rows * nc, 256), 256, 0, st>>>(hi, lo, S, rows, nc, ea, c.eb, V);
+      CK(cudaGetLastError());
+    } else {
+      GemmShape sh{rows, nc, d, 0};
+      KTimer kt(p, K_LOSS_IMAGE, st, 2.0 * rows * nc * d, (double)rows * d * es + 8.0 * rows * nc);
+      const char* M0 = (const char*)s.M + (size_t)r0 * (s.kind == 0 ? s.ld : 1) * es;
+      if (s.elem == ELEM_F64) CK((image_fma<Mode, ELEM_F64>(sh, M0, s.ld, s.kind == 1, c.PB, d, V, st)));
+      else if (s.elem == ELEM_F32) CK((image_fma<Mode, ELEM_F32>(sh, M0, s.ld, s.kind == 1, c.PB, d, V, st)));
+      else CK((image_fma<Mode, ELEM_BF16>(sh, M0, s.ld, s.kind == 1, c.PB, d, V, st)));
+    }
+    const int64_t nb = nblocks(rows * K, 256);
+    KTimer kt(p, K_LOSS_RESID, st, 2.0 * c.T * rows * K * jc, (double)rows * K * jc * 8 * c.nch + 8.0 * rows * K);
+    k_resid_ssq_chunks<Mode><<<dim3((unsigned)nb, (unsigned)c.nch), 256, 0, st>>>(
+        V, rows, K, jc, (int64_t)jc * K * rows, c.chunks + c.T, c.chunks + c.T + c.nch, c.chunks + c.T + 2 * c.nch,
+        c.chunks, c.coefc, c.jcount, s.target ? s.target + r0 * K : nullptr, ssq, nbt, boff);
     CK(cudaGetLastError());
+    boff += nb;
   }
-  if (ssq_out) {  // keep the per-block sums (the squared norms of x)
-    *ssq_out = ssq;
-    *nb_out = nb;
-    return cudaSuccess;
-  }
-  k_loss_reduce<<<nblocks(T, 128), 128, 0, st>>>(ssq, xsq, nb, nbx, chunks, T, lam_dev, out);
-  return cudaGetLastError();
+  *ssq_out = ssq;
+  *nbt_out = nbt;
+  return cudaSuccess;
 }
 
 template <class Mode>
@@ -2094,41 +2184,78 @@ static cudaError_t losses_typed(ihsbin_problem* p, const double* lam_host, const
                                 const void* At, int at_elem, int64_t at_ld, int64_t n_test, const double* Bt,
                                 double* train_out, double* test_out, cudaStream_t st) {
   const Plan& pl = p->plan;
-  const int64_t K = p->K, d = p->d, ncols = (int64_t)pl.L * pl.jc * K;
-  const CBuf PB = p->dual ? p->W : p->Ut;  // the primal basis: (L x jc x K) columns of length d
-  CBuf coefc;
-  int* jcount = nullptr;
-  CK(coef_table<Mode>(p, lam_dev, T, &coefc, &jcount, st));
-  int* chunks = nullptr;
-  int nch = 0;
-  CK(lambda_chunks(p, lam_host, T, &chunks, &nch, st));
-  cudaError_t err = cudaSuccess;
+  const int64_t K = p->K, d = p->d;
   const int cm = Mode::id == 0 ? IHSBIN_COMPUTE_F64 : IHSBIN_COMPUTE_F32X2;
-  if (train_out) {
-    // ||x(lambda)||^2 from the basis itself, then A W and the residuals against B
-    double* xsq = nullptr;
-    int64_t nbx = 0;
-    CK(resid_losses<Mode>(p, PB, d, nullptr, coefc, jcount, chunks, nch, T, lam_dev, nullptr, 0, nullptr, &xsq, &nbx, st));
-    const Tall& A = p->A;
-    const int64_t n = p->n;
-    CBuf V = alloc_cbuf(p, cm, (size_t)ncols * n, SCOPE_SCRATCH, &err);
+  LossCtx c;
+  c.PB = p->dual ? p->W : p->Ut;  // (L x jc x K) columns of length d
+  c.d = d;
+  c.ncols = (int64_t)pl.L * pl.jc * K;
+  c.T = T;
+  CK(coef_table<Mode>(p, lam_dev, T, &c.coefc, (int**)&c.jcount, st));
+  int* chunks = nullptr;
+  CK(lambda_chunks(p, lam_host, T, &chunks, &c.nch, st));
+  c.chunks = chunks;
+  const Tall& A = p->A;
+  LossSrc tr;  // the training rows: A itself (A_hat over-determined, A_hat^T for the dual)
+  tr.rows = p->n;
+  tr.target = p->B;
+  if (A.layout == IHSBIN_CSR) {
+    tr.kind = 2;
+    tr.rp = p->dual ? A.rpT : A.rp;
+    tr.ci = p->dual ? A.ciT : A.ci;
+    tr.val = p->dual ? A.valT : A.val;
+    tr.elem = A.elem;
+  } else {
+    tr.kind = p->dual ? 1 : 0;
+    tr.M = A.A;
+    tr.elem = A.elem;
+    tr.ld = A.ld;
+  }
+  LossSrc te;
+  te.kind = 0;
+  te.M = At;
+  te.elem = at_elem;
+  te.ld = at_ld;
+  te.rows = n_test;
+  te.target = Bt;
+  const bool slices = Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES &&
+                      ((train_out && tr.kind == 0) || (test_out && te.kind == 0));
+  if (slices) {
+    CK(prob_alloc(p, oz_vec_elems(c.ncols, d, 32) * 2, (void**)&c.Bs, SCOPE_SCRATCH));
+    CK(prob_alloc(p, oz_vec_exps(c.ncols, 32) * 4, (void**)&c.eb, SCOPE_SCRATCH));
+    KTimer kt(p, K_LOSS_SLICE, st, 0, 8.0 * c.ncols * d + (double)oz_vec_elems(c.ncols, d, 32) * 2);
+    CK(oz_slice_vecs(c.PB, 0, 0, d, d, c.ncols, 1, 32, c.Bs, c.eb, st));
+  }
+  if (train_out && tr.kind == 2) {
+    cudaError_t err = cudaSuccess;
+    c.PBT = alloc_cbuf(p, cm, (size_t)c.ncols * d, SCOPE_SCRATCH, &err);
     CK(err);
-    if (A.layout == IHSBIN_CSR) {
-      // rows of A: CSR(A_hat) over-determined, CSR(A_hat^T) for the dual
-      CK(csr_basis_image(p, cm, p->dual ? A.rpT : A.rp, p->dual ? A.ciT : A.ci, p->dual ? A.valT : A.val, n, PB, d,
-                         ncols, V, st));
-    } else {
-      CK(basis_image_dense_any<Mode>(p, A.A, A.elem, A.ld, p->dual, n, PB, d, ncols, V, st));
+    CK(basis_transpose(p, cm, c.PB, d, c.ncols, c.PBT, st));
+  }
+  if (train_out) {
+    // ||x(lambda)||^2 from the basis itself, then the residuals against B
+    double *xsq = nullptr, *ssq = nullptr;
+    int64_t nbx = nblocks(d * K, 256), nbt = 0;
+    CK(prob_alloc(p, (size_t)T * nbx * sizeof(double), (void**)&xsq, SCOPE_SCRATCH));
+    {
+      KTimer kt(p, K_LOSS_RESID, st, 2.0 * T * d * K * pl.jc, (double)d * K * pl.jc * 8 * c.nch);
+      k_resid_ssq_chunks<Mode><<<dim3((unsigned)nbx, (unsigned)c.nch), 256, 0, st>>>(
+          c.PB, d, K, pl.jc, (int64_t)pl.jc * K * d, chunks + T, chunks + T + c.nch, chunks + T + 2 * c.nch, chunks,
+          c.coefc, c.jcount, nullptr, xsq, nbx, 0);
+      CK(cudaGetLastError());
     }
-    CK(resid_losses<Mode>(p, V, n, p->B, coefc, jcount, chunks, nch, T, lam_dev, xsq, nbx, train_out, nullptr,
-                          nullptr, st));
+    CK(loss_term<Mode>(p, tr, c, &ssq, &nbt, st));
+    KTimer kt(p, K_LOSS_RESID, st, 0, 8.0 * T * (nbt + nbx));
+    k_loss_reduce<<<nblocks(T, 128), 128, 0, st>>>(ssq, xsq, nbt, nbx, chunks, T, lam_dev, train_out);
+    CK(cudaGetLastError());
   }
   if (test_out) {
-    CBuf V = alloc_cbuf(p, cm, (size_t)ncols * n_test, SCOPE_SCRATCH, &err);
-    CK(err);
-    CK(basis_image_dense_any<Mode>(p, At, at_elem, at_ld, false, n_test, PB, d, ncols, V, st));
-    CK(resid_losses<Mode>(p, V, n_test, Bt, coefc, jcount, chunks, nch, T, lam_dev, nullptr, 0, test_out, nullptr,
-                          nullptr, st));
+    double* ssq = nullptr;
+    int64_t nbt = 0;
+    CK(loss_term<Mode>(p, te, c, &ssq, &nbt, st));
+    KTimer kt(p, K_LOSS_RESID, st, 0, 8.0 * T * nbt);
+    k_loss_reduce<<<nblocks(T, 128), 128, 0, st>>>(ssq, nullptr, nbt, 0, chunks, T, lam_dev, test_out);
+    CK(cudaGetLastError());
   }
   return cudaSuccess;
 }

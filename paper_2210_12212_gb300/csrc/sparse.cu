@@ -294,23 +294,24 @@ __global__ void k_csr_dual_map(const int64_t* rp, const int32_t* ci, const void*
   }
 }
 
-// V[c][i] = sum_e val[e] W[c][ci[e]] for the rows i of a CSR matrix (n_rows x d) and the nc basis
-// columns W (column c at c * d): the training loss's image of the primal basis.
+// WT[k][c] = W[c][k] for nc columns of length d (the CSR image kernel's operand layout)
+cudaError_t basis_transpose(ihsbin_problem* p, int compute, CBuf W, int64_t d, int64_t nc, CBuf WT, cudaStream_t st) {
+  KTimer kt(p, K_LOSS_IMAGE, st, 0, 16.0 * d * nc);
+  if (compute == IHSBIN_COMPUTE_F64) k_transpose_basis<F64><<<nblk(d * nc, 256), 256, 0, st>>>(W, d, nc, WT);
+  else k_transpose_basis<DD><<<nblk(d * nc, 256), 256, 0, st>>>(W, d, nc, WT);
+  return cudaGetLastError();
+}
+
+// V[c][i] = sum_e val[e] W[c][ci[e]] for the n_rows rows of a CSR matrix (row_ptr rp, absolute
+// offsets into ci / val) and nc basis columns given transposed (WT[k][c]): a loss's image of the basis.
 cudaError_t csr_basis_image(ihsbin_problem* p, int compute, const int64_t* rp, const int32_t* ci, const void* val,
-                            int64_t n_rows, CBuf W, int64_t d, int64_t nc, CBuf V, cudaStream_t st) {
-  cudaError_t err = cudaSuccess;
-  CBuf WT = alloc_cbuf(p, compute, (size_t)d * nc, SCOPE_SCRATCH, &err);
-  if (err != cudaSuccess) return err;
+                            int64_t n_rows, CBuf WT, int64_t nc, CBuf V, cudaStream_t st) {
   const Tall& A = p->A;
-  KTimer kt(p, K_EVAL, st, 2.0 * A.nnz * nc, A.nnz * 8.0 + 8.0 * nc * n_rows);
+  const double es = A.elem == ELEM_F64 ? 8 : A.elem == ELEM_F32 ? 4 : 2;
+  KTimer kt(p, K_LOSS_IMAGE, st, 0, 8.0 * nc * n_rows + (es + 4) * (double)A.nnz * n_rows / std::max<int64_t>(1, p->n));
   const unsigned g = nblk(n_rows * 32, 256);
-  if (compute == IHSBIN_COMPUTE_F64) {
-    k_transpose_basis<F64><<<nblk(d * nc, 256), 256, 0, st>>>(W, d, nc, WT);
-    k_csr_dual_map<F64><<<g, 256, 0, st>>>(rp, ci, val, A.elem, n_rows, nc, WT, V);
-  } else {
-    k_transpose_basis<DD><<<nblk(d * nc, 256), 256, 0, st>>>(W, d, nc, WT);
-    k_csr_dual_map<DD><<<g, 256, 0, st>>>(rp, ci, val, A.elem, n_rows, nc, WT, V);
-  }
+  if (compute == IHSBIN_COMPUTE_F64) k_csr_dual_map<F64><<<g, 256, 0, st>>>(rp, ci, val, A.elem, n_rows, nc, WT, V);
+  else k_csr_dual_map<DD><<<g, 256, 0, st>>>(rp, ci, val, A.elem, n_rows, nc, WT, V);
   return cudaGetLastError();
 }
 

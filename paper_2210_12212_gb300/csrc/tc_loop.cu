@@ -529,6 +529,59 @@ __global__ void __launch_bounds__(128) k_oz_slice_vecs(CBuf X, int64_t gs, int64
   }
 }
 
+// Rows of a row-major data matrix (element type ET, row stride ld), K entries each: the A operand of
+// a product with the data.  FP32 / BF16 entries are their own high word (low word 0); an FP64 entry
+// is split into its nearest float and the float of the remainder.  One CTA of 128 threads per row
+// (padded to NTL * TH); layout as k_oz_slice_cols with tile height TH.
+template <int ET>
+__device__ __forceinline__ void data_hl(const void* X, int64_t i, float& h, float& l) {
+  if (ET == ELEM_F64) {
+    const double x = ((const double*)X)[i];
+    h = (float)x;
+    l = (float)(x - (double)h);
+  } else if (ET == ELEM_F32) {
+    h = ((const float*)X)[i];
+    l = 0.f;
+  } else {
+    h = __uint_as_float((uint32_t)((const uint16_t*)X)[i] << 16);
+    l = 0.f;
+  }
+}
+template <int ET>
+__global__ void __launch_bounds__(128) k_oz_slice_data_rows(const void* X, int64_t ld, int64_t K, int64_t nvec, int TH,
+                                                            int NTL, int KB, __nv_bfloat16* out, int* e) {
+  __shared__ float red[4];
+  const int64_t v = blockIdx.x;
+  const bool valid = v < nvec;
+  const int64_t base = (valid ? v : 0) * ld;
+  float m = 0.f;
+  if (valid)
+    for (int64_t k = threadIdx.x; k < K; k += 128) {
+      float h, l;
+      data_hl<ET>(X, base + k, h, l);
+      const float a = fabsf(h);
+      m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+    }
+  m = block_max128(m, red);
+  const int ev = oz_exp(m);
+  const bool live = valid && ev != OZ_NONFINITE;
+  if (threadIdx.x == 0) e[v] = ev;
+  const int tile = (int)(v / TH), nl = (int)(v - (int64_t)tile * TH);
+  const int64_t bblk = (int64_t)TH * OZ_BK;
+  for (int c = threadIdx.x; c < KB * 4; c += 128) {
+    const int kb = c >> 2, kc = c & 3;
+    float h[8], l[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int64_t k = (int64_t)c * 8 + q;
+      h[q] = l[q] = 0.f;
+      if (live && k < K) data_hl<ET>(X, base + k, h[q], l[q]);
+    }
+    store_digits(h, l, ev, live, out + (((int64_t)tile * KB + kb) * OZ_S) * bblk +
+                                    ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+  }
+}
+
 // Block-wide slicing of one column held in shared memory (hi[D], lo[D]) into tile-height-NT
 // layout position (group 0): column c, tile c / NT.  Every thread of the CTA takes part.
 constexpr int OZ_FUSED_THREADS = 512;
@@ -799,6 +852,17 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
   k_update_oz_slice<<<(unsigned)((int64_t)live * ncol), OZ_FUSED_THREADS, smem, st>>>(Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol,
                                                                          D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn,
                                                                          oz_kb(D), Us, eu);
+  return cudaGetLastError();
+}
+
+cudaError_t oz_slice_data_rows(const void* X, int elem, int64_t ld, int64_t K, int64_t nvec, int TH,
+                               __nv_bfloat16* out, int* e, cudaStream_t st) {
+  const int NTL = (int)((nvec + TH - 1) / TH);
+  const unsigned grid = (unsigned)(NTL * TH);
+  const int KB = (int)((K + OZ_BK - 1) / OZ_BK);
+  if (elem == ELEM_F64) k_oz_slice_data_rows<ELEM_F64><<<grid, 128, 0, st>>>(X, ld, K, nvec, TH, NTL, KB, out, e);
+  else if (elem == ELEM_F32) k_oz_slice_data_rows<ELEM_F32><<<grid, 128, 0, st>>>(X, ld, K, nvec, TH, NTL, KB, out, e);
+  else k_oz_slice_data_rows<ELEM_BF16><<<grid, 128, 0, st>>>(X, ld, K, nvec, TH, NTL, KB, out, e);
   return cudaGetLastError();
 }
 

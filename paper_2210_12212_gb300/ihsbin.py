@@ -82,7 +82,7 @@ EXPORTED = [
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
     "ihsbin_path_losses",
 ]
-KCAT_COUNT = 27
+KCAT_COUNT = 31
 
 
 def load(path: Optional[str] = None):

@@ -30,13 +30,13 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)))
 
 
-def _run(ctx, prob, A_test, B_test, lambdas, k=30, compute="f32x2", train=True):
+def _run(ctx, prob, A_test, B_test, lambdas, k=30, compute="f32x2", train=True, loop="auto"):
     from paper_2210_12212_gb300 import ihsbin as ihs
     L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
     r1, r2, kk = default_params(prob, L, k)
     gp = gpu_problem(ihs, ctx, prob)
     gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
-    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute=compute)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute=compute, loop=loop)
     X = gp.eval_path(lambdas)
     tr, te = gp.path_losses(lambdas, A_test, B_test, test_dtype=prob.storage if A_test is not None else None,
                             train=train)
@@ -66,6 +66,24 @@ def test_losses_match_oracle(ctx, name, n_test, k):
     lam = prob.lambdas
     X, tr, te, plan = _run(ctx, prob, A_test, B_test, lam, k)
     assert tr.shape == te.shape == (len(lam),)
+    _check(prob, A_test, B_test, lam, X, tr, te, plan)
+
+
+def test_losses_tensor_core_images_match_cuda_core_images(ctx):
+    """The exact-slice images (tensor cores) against the float-float GEMM of the CUDA cores."""
+    prob, A_test, B_test = make_split("c2_small", 700, seed=0)
+    lam = prob.lambdas
+    _, tr_s, te_s, _ = _run(ctx, prob, A_test, B_test, lam, 40, loop="slices")
+    _, tr_f, te_f, _ = _run(ctx, prob, A_test, B_test, lam, 40, loop="fma")
+    assert _rel(tr_s, tr_f) <= 1e-10
+    assert _rel(te_s, te_f) <= 1e-10
+
+
+def test_losses_many_row_blocks(ctx):
+    """More training and test rows than one block of the image (32768 rows): ragged last blocks, K=2."""
+    prob, A_test, B_test = make_split("c4_small", 33001, seed=3, n=70001, d=40, K=2, storage="f32")
+    lam = prob.lambdas
+    X, tr, te, plan = _run(ctx, prob, A_test, B_test, lam, 30)
     _check(prob, A_test, B_test, lam, X, tr, te, plan)
 
 
