@@ -280,6 +280,44 @@ IHSBIN_API ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lam
                                  ihsbin_dtype b_test_dtype, int b_test_on_device, double* train_loss,
                                  double* test_loss, void* stream);
 
+/* Adaptive sketch dimension (Section 5.1, Algorithm 4).  Newton-sketch steps with an
+ * Armijo line search on the ridge problem at lambda:
+ *   f(x) = 1/2 x^T (A_hat^T A_hat + lambda I) x - c^T x   (c = A_hat^T B; the dual of
+ *   Section 5.2, A_hat = A^T and c = B, when n < d), summed over the K columns,
+ *   d_k = P_S grad f(x_k), P_S = ((S A_hat)^T S A_hat + lambda I)^-1,
+ *   delta_k = <d_k, grad f(x_k)>,  tau_k = gamma1^j with the smallest j >= 0 such that
+ *   f(x_k - tau d_k) <= f(x_k) - gamma2 tau delta_k,  x_{k+1} = x_k - tau_k d_k;
+ * when delta_{k+1} >= gamma3 delta_k the sketch dimension doubles (while 2m <= m_max) and a
+ * new sketch is drawn with seed + (number of doublings), d_{k+1} and delta_{k+1} recomputed
+ * with it.  Stops when delta_k <= eps delta_0 or after max_iter steps. */
+typedef struct {
+  ihsbin_sketch_desc sketch; /* kind, initial m, s, seed, entries                              */
+  double lambda;             /* > 0: the shift (normally lambda_min of the path)               */
+  double eps;                /* relative stop on the decrement; <= 0 selects 1e-10             */
+  double gamma1, gamma2;     /* Armijo backtracking factor and constant in (0,1); <= 0: 0.5, 0.25 */
+  double gamma3;             /* doubling threshold on delta_{k+1} / delta_k; <= 0: 0.5         */
+  int32_t max_iter;          /* <= 0 selects 100                                               */
+  int64_t m_max;             /* <= 0: the row count of A_hat (its power-of-two padding for SRHT) */
+  ihsbin_compute compute;    /* arithmetic of the iteration (the factor, P_S and the products)  */
+} ihsbin_adaptive_desc;
+
+typedef struct {
+  int64_t m;                 /* the final sketch dimension                                     */
+  int32_t iterations, doublings;
+  double delta0, delta;      /* first and last decrement                                       */
+} ihsbin_adaptive_result;
+
+/* Runs Algorithm 4 on the problem and leaves it sketched with the final S (as after
+ * ihsbin_sketch with the final m and seed), ready for ihsbin_build_basis; any basis is
+ * discarded.  Optional host outputs (NULL to skip): delta_trace / m_trace / step_trace of
+ * trace_cap entries (delta_k and the m in force for k = 0..iterations, tau_k for k <
+ * iterations; entries past trace_cap are dropped), x_out the final iterate (D x K row-major
+ * FP64, the dual variable for n < d).  Synchronous on `stream`.  Errors: INVALID_ARG for bad
+ * parameters, the sketch's own errors, NOT_SPD from a factor. */
+IHSBIN_API ihsbin_status ihsbin_adaptive_sketch(ihsbin_problem* p, const ihsbin_adaptive_desc* desc,
+                                     ihsbin_adaptive_result* res, double* delta_trace, int64_t* m_trace,
+                                     double* step_trace, int32_t trace_cap, double* x_out, void* stream);
+
 /* Device time (ms) of the phases of the last sketch / build_basis / eval_path
  * calls: [0] sketch, [1] factor+inverse, [2] Gram+rhs, [3] basis loop, [4] eval. */
 IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
@@ -290,7 +328,7 @@ IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
  * is also bracketed by CUDA events on the stream it runs on and its device
  * time is added at the call's synchronisation point.  Categories 0 ..
  * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 31
+#define IHSBIN_KCAT_COUNT 32
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,

@@ -38,12 +38,13 @@ void free_list(ihsbin_problem* p, std::vector<DevBuf>& v) {
   v.clear();
 }
 
-struct ScratchScope {  // frees the call's scratch allocations when the call returns
+struct ScratchScope {  // frees the call's scratch allocations when the call returns (nests)
   ihsbin_problem* p;
   std::vector<DevBuf> bufs;
-  explicit ScratchScope(ihsbin_problem* pp) : p(pp) { g_scratch = &bufs; }
+  std::vector<DevBuf>* saved;
+  explicit ScratchScope(ihsbin_problem* pp) : p(pp), saved(g_scratch) { g_scratch = &bufs; }
   ~ScratchScope() {
-    g_scratch = nullptr;
+    g_scratch = saved;
     free_list(p, bufs);
   }
 };
@@ -759,12 +760,142 @@ ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64
   return check_status(p, st, "path_losses");
 }
 
+ihsbin_status ihsbin_adaptive_sketch(ihsbin_problem* p, const ihsbin_adaptive_desc* desc, ihsbin_adaptive_result* res,
+                                     double* delta_trace, int64_t* m_trace, double* step_trace, int32_t trace_cap,
+                                     double* x_out, void* stream) {
+  if (!p || !desc || !res) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: NULL argument");
+  const double lam = desc->lambda;
+  if (!(lam > 0) || !std::isfinite(lam)) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: lambda must be positive");
+  const double eps = desc->eps > 0 ? desc->eps : 1e-10;
+  const double g1 = desc->gamma1 > 0 ? desc->gamma1 : 0.5, g2 = desc->gamma2 > 0 ? desc->gamma2 : 0.25;
+  const double g3 = desc->gamma3 > 0 ? desc->gamma3 : 0.5;
+  if (!(g1 < 1) || !(g2 < 1)) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: gamma1 and gamma2 must lie in (0,1)");
+  if (desc->compute != IHSBIN_COMPUTE_F64 && desc->compute != IHSBIN_COMPUTE_F32X2)
+    return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: unknown compute mode");
+  if (trace_cap < 0) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: negative trace_cap");
+  const int max_iter = desc->max_iter > 0 ? desc->max_iter : 100;
+  int64_t Np = 1;
+  while (Np < p->A.N) Np <<= 1;
+  const int64_t m_max = desc->m_max > 0 ? desc->m_max : (desc->sketch.kind == IHSBIN_SK_SRHT ? Np : p->A.N);
+  cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
+  ihsbin_sketch_desc sk = desc->sketch;
+  const uint64_t seed0 = sk.seed;
+  ihsbin_status s = ihsbin_sketch(p, &sk, stream);
+  if (s != IHSBIN_OK) return s;
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "adaptive_sketch");
+  CallStream cs(st);
+  ScratchScope scratch(p);
+  // a one-interval plan at lambda for the factor and the Gram kernels
+  Plan pl;
+  pl.L = 1;
+  pl.edges = {lam, lam};
+  pl.lam0 = {lam};
+  pl.tau = {1.0};
+  pl.k = {1};
+  pl.jcount = {1};
+  pl.compute = desc->compute;
+  pl.product = IHSBIN_PRODUCT_GRAM;
+  pl.gram = (p->A.layout == IHSBIN_DENSE_ROWMAJOR && p->A.elem != ELEM_F64) ? IHSBIN_GRAM_SLICES : IHSBIN_GRAM_FMA;
+  pl.loop = desc->compute == IHSBIN_COMPUTE_F32X2 ? IHSBIN_LOOP_SLICES : IHSBIN_LOOP_FMA;
+  pl.factor = desc->compute == IHSBIN_COMPUTE_F32X2 ? IHSBIN_FACTOR_SLICES : IHSBIN_FACTOR_FMA;
+  p->plan = pl;
+  const int64_t D = p->A.D, K = p->K;
+  AdaptiveBufs b;
+  auto cb = [&](size_t n) { return alloc_cbuf(p, desc->compute, n, SCOPE_SCRATCH, &e); };
+  b.G = cb((size_t)D * D);
+  b.P = cb((size_t)D * D);
+  b.c = cb((size_t)D * K);
+  b.x = cb((size_t)D * K);
+  b.g = cb((size_t)D * K);
+  b.d = cb((size_t)D * K);
+  b.hd = cb((size_t)D * K);
+  if (e == cudaSuccess) e = prob_alloc(p, 8, (void**)&b.lam_dev, SCOPE_SCRATCH);
+  if (e == cudaSuccess) e = prob_alloc(p, 8 * 256, (void**)&b.part, SCOPE_SCRATCH);
+  if (e == cudaSuccess) e = prob_alloc(p, 16, (void**)&b.dots, SCOPE_SCRATCH);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b.lam_dev, &lam, 8, cudaMemcpyHostToDevice, st);
+  auto finish = [&](ihsbin_status r) {
+    p->plan = Plan{};
+    p->G = p->Pinv = CBuf{};
+    p->built = false;
+    return r;
+  };
+  if (e == cudaSuccess) e = adaptive_setup(p, b, st);
+  if (e == cudaSuccess) e = adaptive_precond(p, b, st);
+  if (e == cudaSuccess) e = adaptive_direction(p, b, st);
+  double dots[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dots, b.dots, 16, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return finish(cuda_fail(e, "adaptive_sketch"));
+  if ((s = check_status(p, st, "adaptive_sketch")) != IHSBIN_OK) return finish(s);
+  double delta = dots[0];
+  const double delta0 = delta;
+  int64_t m = sk.m;
+  int k = 0, r = 0;
+  auto record = [&](int idx, double dl, int64_t mm) {
+    if (idx < trace_cap) {
+      if (delta_trace) delta_trace[idx] = dl;
+      if (m_trace) m_trace[idx] = mm;
+    }
+  };
+  record(0, delta, m);
+  while (delta > eps * delta0 && k < max_iter) {
+    // f(x - t d) - f(x) = -t delta + t^2/2 <d, (G + lam I) d>: the Armijo test reduces to
+    // t <d, (G + lam I) d> <= 2 (1 - gamma2) delta
+    if ((e = adaptive_curvature(p, b, lam, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dots, b.dots, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return finish(cuda_fail(e, "adaptive_sketch"));
+    const double q = dots[1];
+    int j = 0;
+    while (std::pow(g1, j) * q > 2.0 * (1.0 - g2) * delta) {
+      if (++j > 200) return finish(fail(IHSBIN_ERR_NOT_SPD, "adaptive_sketch: Armijo search found no step"));
+    }
+    const double t = std::pow(g1, j);
+    if (k < trace_cap && step_trace) step_trace[k] = t;
+    if ((e = adaptive_step(p, b, t, st)) != cudaSuccess || (e = adaptive_direction(p, b, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dots, b.dots, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+      return finish(cuda_fail(e, "adaptive_sketch"));
+    double dnew = dots[0];
+    if (dnew >= g3 * delta && 2 * m <= m_max) {
+      m *= 2;
+      ++r;
+      sk.m = m;
+      sk.seed = seed0 + (uint64_t)r;
+      if ((s = ihsbin_sketch(p, &sk, stream)) != IHSBIN_OK) return finish(s);
+      p->plan = pl;
+      if ((e = adaptive_precond(p, b, st)) != cudaSuccess || (e = adaptive_direction(p, b, st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dots, b.dots, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return finish(cuda_fail(e, "adaptive_sketch"));
+      if ((s = check_status(p, st, "adaptive_sketch")) != IHSBIN_OK) return finish(s);
+      dnew = dots[0];
+    }
+    delta = dnew;
+    ++k;
+    record(k, delta, m);
+  }
+  if (x_out) {
+    double* xd = nullptr;
+    if ((e = prob_alloc(p, (size_t)D * K * 8, (void**)&xd, SCOPE_SCRATCH)) != cudaSuccess ||
+        (e = adaptive_export_x(p, b, xd, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(x_out, xd, (size_t)D * K * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+      return finish(cuda_fail(e, "adaptive_sketch"));
+  }
+  if ((s = check_status(p, st, "adaptive_sketch")) != IHSBIN_OK) return finish(s);
+  res->m = m;
+  res->iterations = k;
+  res->doublings = r;
+  res->delta0 = delta0;
+  res->delta = delta;
+  return finish(IHSBIN_OK);
+}
+
 static const char* kcat_names[K_NCAT] = {
     "sketch_draw", "sketch_apply", "sketch_gram", "factor_shift", "factor_potrf", "factor_trsm", "factor_syrk",
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
     "eval_coef", "eval", "sparse", "gram_slice", "gram_tc_mma", "gram_combine", "loop_slice", "loop_gram_tc",
     "loop_precond_tc", "factor_slice", "inverse_tc", "trtri_tc", "factor_syrk_tc", "loss_slice", "loss_image_tc",
-    "loss_image", "loss_resid"};
+    "loss_image", "loss_resid", "adaptive_step"};
 
 ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");

@@ -66,7 +66,7 @@ enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
   K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
-  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_LOSS_SLICE, K_LOSS_TC, K_LOSS_IMAGE, K_LOSS_RESID, K_NCAT
+  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_LOSS_SLICE, K_LOSS_TC, K_LOSS_IMAGE, K_LOSS_RESID, K_ADAPTIVE, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
@@ -236,6 +236,19 @@ cudaError_t csr_dual_map(ihsbin_problem* p, int compute, int64_t ncol, cudaStrea
 cudaError_t basis_transpose(ihsbin_problem* p, int compute, CBuf W, int64_t d, int64_t nc, CBuf WT, cudaStream_t st);
 cudaError_t csr_basis_image(ihsbin_problem* p, int compute, const int64_t* rp, const int32_t* ci, const void* val,
                             int64_t n_rows, CBuf WT, int64_t nc, CBuf V, cudaStream_t st);
+// Algorithm 4's device state (D x K column-major vectors in the compute mode's format)
+struct AdaptiveBufs {
+  CBuf G, c, P, x, g, d, hd;
+  double* lam_dev = nullptr;  // the shift lambda (one double)
+  double* part = nullptr;     // inner-product partial sums
+  double* dots = nullptr;     // [0] = <d, g>, [1] = <d, (G + lam I) d>
+};
+cudaError_t adaptive_setup(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st);      // G, c; x = 0, g = -c
+cudaError_t adaptive_precond(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st);    // P = (G_S + lam I)^-1
+cudaError_t adaptive_direction(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st);  // d = P g, dots[0]
+cudaError_t adaptive_curvature(ihsbin_problem* p, AdaptiveBufs& b, double lam, cudaStream_t st);  // hd, dots[1]
+cudaError_t adaptive_step(ihsbin_problem* p, AdaptiveBufs& b, double t, cudaStream_t st);  // x -= t d, g -= t hd
+cudaError_t adaptive_export_x(ihsbin_problem* p, AdaptiveBufs& b, double* out_dev, cudaStream_t st);
 // training / test losses along the path (device outputs of T doubles, either may be null)
 cudaError_t losses_device(ihsbin_problem* p, const double* lam_host, const double* lam_dev, int64_t T, const void* At,
                           int at_elem, int64_t at_ld, int64_t n_test, const double* Bt, double* train_out,

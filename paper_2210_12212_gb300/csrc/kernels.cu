@@ -1874,6 +1874,173 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   return cudaSuccess;
 }
 
+// ============================================= adaptive sketch dimension (Section 5.1, Algorithm 4)
+// Newton-sketch steps on f(x) = 1/2 x^T (G + lam I) x - c^T x (G = A_hat^T A_hat, D x K iterate,
+// column-major) in the compute mode's arithmetic; the host takes the Armijo and doubling decisions
+// from the two inner products each step leaves in FP64.
+
+// part[b] = sum over block b's entries of a_e b_e (each product rounded to FP64); fixed tree order
+template <class Mode>
+__global__ void __launch_bounds__(256) k_dot_partial(CBuf a, CBuf b, int64_t n, double* part) {
+  __shared__ double red[8];
+  double v = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x; e < n; e += (int64_t)gridDim.x * 256)
+    v += Mode::to_d(Mode::mul(Mode::ld(a, e), Mode::ld(b, e)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    part[blockIdx.x] = s;
+  }
+}
+__global__ void k_sum_parts(const double* part, int nb, double* out) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    *out = s;
+  }
+}
+// y += alpha x (alpha an FP64 scalar), or y = alpha x when assign
+template <class Mode>
+__global__ void k_axpy(CBuf x, double alpha, CBuf y, int64_t n, int assign) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const typename Mode::V t = Mode::mul(Mode::from_d(alpha), Mode::ld(x, e));
+  Mode::st(y, e, assign ? t : Mode::add(Mode::ld(y, e), t));
+}
+template <class Mode>
+__global__ void k_to_rowmajor_f64(CBuf x, int64_t D, int64_t K, double* out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over D x K, row-major output
+  if (e >= D * K) return;
+  const int64_t i = e / K, r = e - i * K;
+  out[e] = Mode::to_d(Mode::ld(x, r * D + i));
+}
+
+constexpr int DOT_BLOCKS = 256;
+
+template <class Mode>
+static cudaError_t dot_into(CBuf a, CBuf b, int64_t n, double* part, double* out, cudaStream_t st) {
+  const int nb = (int)std::min<int64_t>(DOT_BLOCKS, nblocks(n, 256));
+  k_dot_partial<Mode><<<nb, 256, 0, st>>>(a, b, n, part);
+  CK(cudaGetLastError());
+  k_sum_parts<<<1, 32, 0, st>>>(part, nb, out);
+  return cudaGetLastError();
+}
+template <class Mode>
+static cudaError_t sym_apply(CBuf M, CBuf X, int64_t D, int64_t K, CBuf Y, cudaStream_t st) {
+  GemmShape sh{D, K, D, 0};
+  return launch_gemm<Mode, 64, 32, 16, 4, 2>(sh, 1, LdCMatA<Mode>{M, D, 0, nullptr}, LdCColB<Mode>{X, D, 0, nullptr},
+                                             EpStoreColMajor<Mode>{Y, D, 0, nullptr}, st);
+}
+
+template <class Mode, int ET>
+static cudaError_t adaptive_setup_typed(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  const Tall& A = p->A;
+  const int64_t D = A.D, K = p->K;
+  const int cm = p->plan.compute;
+  p->G = b.G;
+  if (A.layout == IHSBIN_CSR) CK(csr_gram(p, cm, st));
+  else if (p->plan.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, st));
+  else CK((gram_dense<Mode, ET>(p, st)));
+  if (A.layout == IHSBIN_CSR && !p->dual) {
+    CK(csr_rhs(p, cm, b.c, st));
+  } else if (p->dual) {
+    KTimer kt(p, K_RHS, st, 0, (double)D * K * 16);
+    k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(p->B, D, K, b.c);
+    CK(cudaGetLastError());
+  } else {
+    CK((rhs_dense<Mode, ET>(p, b.c, st)));
+  }
+  p->G = CBuf{};
+  // x = 0, g = grad f(0) = -c
+  KTimer kt(p, K_ADAPTIVE, st, 0, 24.0 * D * K);
+  k_axpy<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(b.c, 0.0, b.x, D * K, 1);
+  k_axpy<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(b.c, -1.0, b.g, D * K, 1);
+  return cudaGetLastError();
+}
+
+template <class Mode>
+static cudaError_t adaptive_precond_typed(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  const int64_t D = p->A.D;
+  cudaError_t err = cudaSuccess;
+  const int cm = p->plan.compute;
+  CBuf H = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_SCRATCH, &err);
+  CBuf Wm = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_SCRATCH, &err);
+  const int64_t nblk = (D + NB - 1) / NB;
+  CBuf dinv = alloc_cbuf(p, cm, (size_t)nblk * NB * NB, SCOPE_SCRATCH, &err);
+  CK(err);
+  p->Pinv = b.P;
+  err = factor_and_invert<Mode>(p, H, Wm, dinv, b.lam_dev, st);
+  p->Pinv = CBuf{};
+  return err;
+}
+
+template <class Mode>
+static cudaError_t adaptive_direction_typed(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  const int64_t D = p->A.D, K = p->K;
+  KTimer kt(p, K_ADAPTIVE, st, 2.0 * D * D * K + 2.0 * D * K, 8.0 * D * D + 24.0 * D * K);
+  CK(sym_apply<Mode>(b.P, b.g, D, K, b.d, st));
+  return dot_into<Mode>(b.d, b.g, D * K, b.part, b.dots, st);
+}
+
+template <class Mode>
+static cudaError_t adaptive_curvature_typed(ihsbin_problem* p, AdaptiveBufs& b, double lam, cudaStream_t st) {
+  const int64_t D = p->A.D, K = p->K;
+  KTimer kt(p, K_ADAPTIVE, st, 2.0 * D * D * K + 4.0 * D * K, 8.0 * D * D + 40.0 * D * K);
+  CK(sym_apply<Mode>(b.G, b.d, D, K, b.hd, st));
+  k_axpy<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(b.d, lam, b.hd, D * K, 0);
+  CK(cudaGetLastError());
+  return dot_into<Mode>(b.d, b.hd, D * K, b.part, b.dots + 1, st);
+}
+
+template <class Mode>
+static cudaError_t adaptive_step_typed(ihsbin_problem* p, AdaptiveBufs& b, double t, cudaStream_t st) {
+  const int64_t D = p->A.D, K = p->K;
+  KTimer kt(p, K_ADAPTIVE, st, 4.0 * D * K, 48.0 * D * K);
+  k_axpy<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(b.d, -t, b.x, D * K, 0);
+  k_axpy<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(b.hd, -t, b.g, D * K, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t adaptive_setup(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  const int et = p->A.elem;
+  if (p->plan.compute == IHSBIN_COMPUTE_F64) {
+    if (et == ELEM_F64) return adaptive_setup_typed<F64, ELEM_F64>(p, b, st);
+    if (et == ELEM_F32) return adaptive_setup_typed<F64, ELEM_F32>(p, b, st);
+    return adaptive_setup_typed<F64, ELEM_BF16>(p, b, st);
+  }
+  if (et == ELEM_F64) return adaptive_setup_typed<DD, ELEM_F64>(p, b, st);
+  if (et == ELEM_F32) return adaptive_setup_typed<DD, ELEM_F32>(p, b, st);
+  return adaptive_setup_typed<DD, ELEM_BF16>(p, b, st);
+}
+cudaError_t adaptive_precond(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  return p->plan.compute == IHSBIN_COMPUTE_F64 ? adaptive_precond_typed<F64>(p, b, st)
+                                               : adaptive_precond_typed<DD>(p, b, st);
+}
+cudaError_t adaptive_direction(ihsbin_problem* p, AdaptiveBufs& b, cudaStream_t st) {
+  return p->plan.compute == IHSBIN_COMPUTE_F64 ? adaptive_direction_typed<F64>(p, b, st)
+                                               : adaptive_direction_typed<DD>(p, b, st);
+}
+cudaError_t adaptive_curvature(ihsbin_problem* p, AdaptiveBufs& b, double lam, cudaStream_t st) {
+  return p->plan.compute == IHSBIN_COMPUTE_F64 ? adaptive_curvature_typed<F64>(p, b, lam, st)
+                                               : adaptive_curvature_typed<DD>(p, b, lam, st);
+}
+cudaError_t adaptive_step(ihsbin_problem* p, AdaptiveBufs& b, double t, cudaStream_t st) {
+  return p->plan.compute == IHSBIN_COMPUTE_F64 ? adaptive_step_typed<F64>(p, b, t, st)
+                                               : adaptive_step_typed<DD>(p, b, t, st);
+}
+cudaError_t adaptive_export_x(ihsbin_problem* p, AdaptiveBufs& b, double* out_dev, cudaStream_t st) {
+  const int64_t D = p->A.D, K = p->K;
+  if (p->plan.compute == IHSBIN_COMPUTE_F64)
+    k_to_rowmajor_f64<F64><<<nblocks(D * K, 256), 256, 0, st>>>(b.x, D, K, out_dev);
+  else
+    k_to_rowmajor_f64<DD><<<nblocks(D * K, 256), 256, 0, st>>>(b.x, D, K, out_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t build_basis_device(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev) {
   const int cm = p->plan.compute, et = p->A.elem;
   if (p->A.layout == IHSBIN_CSR && p->plan.product != IHSBIN_PRODUCT_GRAM) return cudaErrorNotSupported;

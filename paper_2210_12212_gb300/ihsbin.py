@@ -61,6 +61,17 @@ class PathDesc(C.Structure):
                 ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int)]
 
 
+class AdaptiveDesc(C.Structure):
+    _fields_ = [("sketch", SketchDesc), ("lam", C.c_double), ("eps", C.c_double), ("gamma1", C.c_double),
+                ("gamma2", C.c_double), ("gamma3", C.c_double), ("max_iter", C.c_int32), ("m_max", C.c_int64),
+                ("compute", C.c_int)]
+
+
+class AdaptiveResult(C.Structure):
+    _fields_ = [("m", C.c_int64), ("iterations", C.c_int32), ("doublings", C.c_int32), ("delta0", C.c_double),
+                ("delta", C.c_double)]
+
+
 class Request(C.Structure):
     _fields_ = [("A", Matrix), ("B", C.c_void_p), ("K", C.c_int64), ("ldb", C.c_int64), ("b_dtype", C.c_int),
                 ("b_on_device", C.c_int), ("sketch", SketchDesc), ("path", PathDesc), ("lambdas", C.c_void_p),
@@ -80,9 +91,9 @@ EXPORTED = [
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
-    "ihsbin_path_losses",
+    "ihsbin_path_losses", "ihsbin_adaptive_sketch",
 ]
-KCAT_COUNT = 31
+KCAT_COUNT = 32
 
 
 def load(path: Optional[str] = None):
@@ -122,6 +133,7 @@ def load(path: Optional[str] = None):
         "ihsbin_serve": [vp, C.POINTER(ServeConfig), vp, i64, vp, vp, vp],
         "ihsbin_gram_export": [vp, vp],
         "ihsbin_path_losses": [vp, vp, i64, C.POINTER(Matrix), vp, i64, C.c_int, C.c_int, vp, vp, vp],
+        "ihsbin_adaptive_sketch": [vp, C.POINTER(AdaptiveDesc), C.POINTER(AdaptiveResult), vp, vp, vp, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -245,6 +257,30 @@ class Problem:
         pd.loop = LOOP[loop]
         pd.factor = FACTOR[factor]
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
+
+    def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",
+                        eps: float = 0.0, gamma1: float = 0.0, gamma2: float = 0.0, gamma3: float = 0.0,
+                        max_iter: int = 0, m_max: int = 0, compute: str = "f32x2", trace_cap: int = 256,
+                        want_x: bool = False, stream=None):
+        """Algorithm 4: returns dict(m, iterations, doublings, delta0, delta, deltas, ms, steps[, x]);
+        the problem is left sketched with the final m."""
+        sd = SketchDesc(SKETCH_KIND[kind], m0, s, seed, DTYPE[entries])
+        ad = AdaptiveDesc(sd, lam, eps, gamma1, gamma2, gamma3, max_iter, m_max, COMPUTE[compute])
+        res = AdaptiveResult()
+        dl = np.zeros(trace_cap)
+        ms = np.zeros(trace_cap, dtype=np.int64)
+        st = np.zeros(trace_cap)
+        D = min(self.n, self.d)
+        x = np.empty((D, self.K)) if want_x else None
+        _check(_lib.ihsbin_adaptive_sketch(self.h, C.byref(ad), C.byref(res), _ptr(dl), _ptr(ms), _ptr(st),
+                                           trace_cap, _ptr(x), _stream(stream)))
+        it = res.iterations
+        out = dict(m=res.m, iterations=it, doublings=res.doublings, delta0=res.delta0, delta=res.delta,
+                   deltas=dl[:min(it + 1, trace_cap)].copy(), ms=ms[:min(it + 1, trace_cap)].copy(),
+                   steps=st[:min(it, trace_cap)].copy())
+        if want_x:
+            out["x"] = x
+        return out
 
     def eval_path(self, lambdas, out=None, x_dtype: str = "f64", stream=None):
         """Returns X (T x d x K) as a numpy array, or fills `out` (a CUDA tensor) in place."""
