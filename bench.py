@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--requests", type=int, default=128, help="serving workload (c5): number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
+    ap.add_argument("--adaptive", type=int, default=0, metavar="M0",
+                    help="a step starts with Algorithm 4 from sketch dimension M0 at lambda_min (the path then "
+                         "runs on the m it settles on, parameters from the sketch as with --auto)")
     ap.add_argument("--losses", type=int, default=0, metavar="N_TEST",
                     help="validation workload: N_TEST held-out rows drawn with the training rows; a step "
                          "returns the training and test losses of every lambda (Section 6.1) instead of X")
@@ -342,6 +345,8 @@ def main():
     else:
         prob = make_problem(args.config, seed=0)
     note(f"workload {args.config} generated")
+    if args.adaptive:
+        args.auto = True
     par = None if args.auto else load_params(args.config[:-1] if args.config == "c3t" else args.config)
     if args.impl == "reference":
         reference_arm(args, prob, par)
@@ -392,8 +397,15 @@ def main():
         Bt_pin = torch.from_numpy(np.ascontiguousarray(B_test)).pin_memory()
         host_bytes += At_pin.numel() * At_pin.element_size() + Bt_pin.numel() * 8
 
+    adapt = {}
+
     def step(pp, out=None):
-        pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, entries=entries, stream=stream)
+        if args.adaptive:
+            adapt.update(pp.adaptive_sketch(prob.sketch, args.adaptive, prob.lambda_min, s=prob.s,
+                                            seed=prob.sketch_seed, entries=entries, compute=args.compute,
+                                            stream=stream))
+        else:
+            pp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, entries=entries, stream=stream)
         pp.build_basis(prob.lambda_min, prob.lambda_max, stream=stream, **bkw)
         if A_test is not None:  # losses of every lambda, X never formed
             dev = out is not None
@@ -460,8 +472,14 @@ def main():
             losses = step(p, X_dev)
             p.eval_path(prob.lambdas, out=X_dev, stream=stream)
             torch.cuda.synchronize()
-        check = parity_sample(prob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6,
+        pprob = prob
+        if args.adaptive:  # the path ran on the sketch Algorithm 4 left behind
+            import dataclasses
+            pprob = dataclasses.replace(prob, m=int(adapt["m"]), sketch_seed=prob.sketch_seed + int(adapt["doublings"]))
+        check = parity_sample(pprob, par, X_dev.cpu().numpy(), tol=1e-9 if args.compute == "f64" else 1e-6,
                               eps=args.eps)
+        if args.adaptive:
+            check["adaptive"] = adaptive_check(prob, args.adaptive, adapt)
         if A_test is not None:
             check["losses"] = losses_check(prob, A_test, B_test, X_dev.cpu().numpy(), losses)
 
@@ -494,11 +512,14 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
             "config": {"workload": WORKLOADS.get(args.config, args.config) + (
                            f"; plus {args.losses} held-out rows of the same model, a step returns the training "
-                           f"and test losses of every lambda (X not formed)" if args.losses else ""),
+                           f"and test losses of every lambda (X not formed)" if args.losses else "") + (
+                           f"; the sketch dimension chosen by Algorithm 4 from m0={args.adaptive} at lambda_min "
+                           f"inside each step" if args.adaptive else ""),
                        "jmax": args.jmax,
                        "storage": prob.storage, "l2": ("inputs larger than L2 (A is 256 MiB)" if args.config == "c2"
                                                        else "see workload"),
-                       "params": f"tests/golden/{args.config}_params.json",
+                       "params": (f"tests/golden/{args.config}_params.json" if par is not None else
+                                  "from the sketch (rho from d_e, k from Theorem 4 at eps)"),
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
             "phase_ms": phases,
@@ -540,6 +561,19 @@ def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
         conv.append(float(np.linalg.norm(ref[t] - xs) / np.linalg.norm(ref[t])))
     return {"max_rel_err_vs_oracle": max(err), "lambdas_checked": len(idx), "pass": max(err) <= tol,
             "oracle_max_rel_dist_to_exact_ridge": max(conv)}
+
+
+def adaptive_check(prob, m0, g):
+    """Algorithm 4 on the device against the oracle's run: the m and step sequences (exact) and the
+    decrements relative to the first."""
+    from oracle import adaptive as oa
+    o = oa.adaptive_for_problem(oracle_matrix(prob), prob.B, prob.sketch, m0, prob.s, prob.sketch_seed,
+                                prob.lambda_min, bf16_entries=prob.storage == "bf16")
+    n = min(len(o.delta), len(g["deltas"]))
+    return {"m0": m0, "m": int(g["m"]), "iterations": int(g["iterations"]), "doublings": int(g["doublings"]),
+            "m_sequence_equal": list(map(int, g["ms"])) == o.ms, "steps_equal": list(g["steps"]) == o.steps,
+            "max_rel_err_delta": float(np.max(np.abs(np.asarray(g["deltas"][:n]) - np.asarray(o.delta[:n])))
+                                       / o.delta[0])}
 
 
 def losses_check(prob, A_test, B_test, X, losses):

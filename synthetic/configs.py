@@ -21,6 +21,16 @@ at sizes the FP64 oracle finishes in seconds):
           K=64 and ||E||_F = 0.01 ||A X*||_F, Gaussian sketch m=4096 in BF16,
           T=500 lambdas in [1e-4, 1e-2] * ||A||_2^2.
 * ``c5``  serving mix: request shapes drawn per request seed.
+* ``ar1`` / ``ar1u``  the paper's random data (Section 6.1): rows of A drawn
+          from N(0, Sigma^2 / sqrt(n d)) with the AR(1) correlation
+          Sigma_ij = 0.99^|i-j|, v* ~ N(0, I/d), b = A v* + N(0, 0.02^2), CountSketch
+          (s = 1), lambdas in [1, 100]; over-determined 20000 x 4000 with m = 1600
+          and under-determined 4000 x 20000 with m = 2400 (the shapes of the
+          paper's random over- and under-determined experiments), FP32 storage.
+* ``gkernel``  matrix-valued kernel ridge regression (Section 6.1, the CIFAR-10
+          experiment's form): A_ij = exp(-||f_i - f_j||^2 / (2h)), h = 1000, on
+          synthetic class-structured features in [0,1]^3072, B = one-hot labels of 10
+          classes, n = d = 8192, Gaussian sketch m = 4096, lambdas in [0.1, 10].
 """
 from __future__ import annotations
 
@@ -175,6 +185,46 @@ def _csr_uniform(rng, n, d, per_row, chunk=1 << 17):
     return row_ptr, cols_out, vals
 
 
+def _ar1_rows(rng, n, d, alpha, chunk=1 << 12):
+    """n rows a_i = (n d)^(-1/4) Sigma z_i with Sigma_ij = alpha^|i-j| (so Cov(a_i) = Sigma^2 / sqrt(n d)):
+    Sigma z = F + G - z with the forward and backward AR(1) filters F_j = alpha F_{j-1} + z_j,
+    G_j = alpha G_{j+1} + z_j (O(n d) instead of the d x d product)."""
+    A = np.empty((n, d), dtype=np.float32)
+    scale = (float(n) * d) ** -0.25
+    for r0 in range(0, n, chunk):
+        r1 = min(n, r0 + chunk)
+        Zt = rng.standard_normal((d, r1 - r0))  # column j of the rows' block is row j here
+        F = np.empty_like(Zt)
+        Gb = np.empty_like(Zt)
+        F[0] = Zt[0]
+        for j in range(1, d):
+            F[j] = alpha * F[j - 1] + Zt[j]
+        Gb[d - 1] = Zt[d - 1]
+        for j in range(d - 2, -1, -1):
+            Gb[j] = alpha * Gb[j + 1] + Zt[j]
+        A[r0:r1] = (scale * (F + Gb - Zt)).T
+    return A
+
+
+def _kernel_features(rng, n, p, classes):
+    """Class-structured features in [0, 1]^p: f_i = clip(mu_{y_i} + 0.15 z_i), class means mu_c ~ U[0,1]^p."""
+    mu = rng.uniform(0.0, 1.0, size=(classes, p))
+    y = rng.integers(0, classes, size=n)
+    f = np.clip(mu[y] + 0.15 * rng.standard_normal((n, p)), 0.0, 1.0)
+    return f, y
+
+
+def _gauss_kernel(F1, F2, h, chunk=2048):
+    """exp(-||f_i - g_j||^2 / (2h)) in FP64 (the constant (2 pi h)^(-p/2) of Section 6.1 is dropped), FP32 out."""
+    out = np.empty((F1.shape[0], F2.shape[0]), dtype=np.float32)
+    n2 = np.sum(F2 * F2, axis=1)
+    for r0 in range(0, F1.shape[0], chunk):
+        X = F1[r0:r0 + chunk]
+        d2 = np.sum(X * X, axis=1)[:, None] + n2[None, :] - 2.0 * (X @ F2.T)
+        out[r0:r0 + chunk] = np.exp(-np.maximum(d2, 0.0) / (2.0 * h))
+    return out
+
+
 def _csr_matvec(row_ptr, col, val, n, d):
     rows = np.repeat(np.arange(n), np.diff(row_ptr))
     v64 = val.astype(np.float64)
@@ -197,6 +247,13 @@ CONFIGS = {
                m=8192, s=8, T=1000, lrange=(1e-4, 1e-2), noise=0.1),
     "c4": dict(kind="powerlaw", n=262144, d=2048, K=64, expo=1.0, storage="bf16",
                sketch="gaussian", m=4096, s=1, T=500, lrange=(1e-4, 1e-2), noise_rel=0.01),
+    # Section 6.1's random data and the kernel form of its CIFAR-10 experiment
+    "ar1": dict(kind="ar1", n=20000, d=4000, K=1, alpha=0.99, sigma=0.02, storage="f32", sketch="countsketch",
+                m=1600, s=1, T=100, lrange_abs=(1.0, 100.0)),
+    "ar1u": dict(kind="ar1", n=4000, d=20000, K=1, alpha=0.99, sigma=0.02, storage="f32", sketch="countsketch",
+                 m=2400, s=1, T=100, lrange_abs=(1.0, 100.0)),
+    "gkernel": dict(kind="gkernel", n=8192, d=8192, K=10, p=3072, h=1000.0, storage="f32", sketch="gaussian",
+                    m=4096, s=1, T=100, lrange_abs=(0.1, 10.0)),
     # structure-preserving small variants (ragged against 64-wide tiles)
     "c1_small": dict(kind="powerlaw", n=300, d=37, K=1, expo=0.8, storage="f64", sketch="gaussian",
                      m=80, s=1, T=23, lrange=(1e-3, 1e1), noise=0.1),
@@ -206,6 +263,12 @@ CONFIGS = {
                      sketch="countsketch", m=400, s=4, T=60, lrange=(1e-4, 1e-2), noise=0.1),
     "c4_small": dict(kind="powerlaw", n=2048, d=72, K=5, expo=1.0, storage="bf16",
                      sketch="gaussian", m=160, s=1, T=30, lrange=(1e-4, 1e-2), noise_rel=0.01),
+    "ar1_small": dict(kind="ar1", n=2000, d=400, K=1, alpha=0.99, sigma=0.02, storage="f32", sketch="countsketch",
+                      m=160, s=1, T=30, lrange_abs=(1.0, 100.0)),
+    "ar1u_small": dict(kind="ar1", n=400, d=2000, K=1, alpha=0.99, sigma=0.02, storage="f32", sketch="countsketch",
+                       m=240, s=1, T=30, lrange_abs=(1.0, 100.0)),
+    "gkernel_small": dict(kind="gkernel", n=600, d=600, K=10, p=3072, h=1000.0, storage="f32", sketch="gaussian",
+                          m=300, s=1, T=30, lrange_abs=(0.1, 10.0)),
 }
 
 
@@ -262,11 +325,18 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
     elif cfg["kind"] == "csr":
         layout = "csr"
         row_ptr, col, val = _csr_uniform(rng, n, d, cfg["per_row"])
+    elif cfg["kind"] == "ar1":
+        A = _ar1_rows(rng, n, d, cfg["alpha"])
+        Af = A
+    elif cfg["kind"] == "gkernel":
+        return _kernel_problem(name, cfg, seed, n_test=0)[0]
     else:
         raise ValueError(cfg["kind"])
 
-    # planted solution and right-hand side (float64 on the host)
+    # planted solution and right-hand side (float64 on the host); Section 6.1 draws v* ~ N(0, I/d)
     x_star = rng.standard_normal((d, K))
+    if cfg["kind"] == "ar1":
+        x_star /= np.sqrt(d)
     if layout == "csr":
         mv, rmv = _csr_matvec(row_ptr, col, val, n, d)
         Ax = np.stack([mv(x_star[:, r]) for r in range(K)], axis=1)
@@ -278,7 +348,9 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
             Ax[r0:r1] = bf16_bits_to_f32(A[r0:r1]).astype(np.float64) @ x_star
     else:
         Ax = Af.astype(np.float64) @ x_star
-    if "noise" in cfg:
+    if "sigma" in cfg:
+        B = Ax + cfg["sigma"] * rng.standard_normal((n, K))
+    elif "noise" in cfg:
         B = Ax + cfg["noise"] * rng.standard_normal((n, K))
     else:
         E = rng.standard_normal((n, K))
@@ -298,8 +370,12 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
         del A32
     else:
         A64 = A.astype(np.float64)
-        norm2_sq = spectral_norm_sq(lambda v: A64 @ v, lambda w: A64.T @ w, d, 200, seed)
-    lmin, lmax = cfg["lrange"][0] * norm2_sq, cfg["lrange"][1] * norm2_sq
+        norm2_sq = spectral_norm_sq(lambda v: A64 @ v, lambda w: A64.T @ w, d,
+                                    200 if n * d <= (1 << 24) else 40, seed)
+    if "lrange_abs" in cfg:  # the paper's absolute lambda range
+        lmin, lmax = cfg["lrange_abs"]
+    else:
+        lmin, lmax = cfg["lrange"][0] * norm2_sq, cfg["lrange"][1] * norm2_sq
     lambdas = lambda_grid(lmin, lmax, cfg["T"])
     p = Problem(name=name, n=n, d=d, K=K, layout=layout, storage=cfg["storage"], A=A,
                 row_ptr=row_ptr, col_idx=col, val=val, B=B, x_star=x_star, sketch=cfg["sketch"],
@@ -312,11 +388,36 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
     return p
 
 
+def _kernel_problem(name, cfg, seed, n_test):
+    """Kernel ridge regression data: n training and n_test test feature vectors with labels;
+    A = k(train, train) (n x n), A_test = k(test, train), B / B_test one-hot (K classes)."""
+    rng = np.random.default_rng(seed)
+    n, K = cfg["n"], cfg["K"]
+    f, y = _kernel_features(rng, n + n_test, cfg["p"], K)
+    A = _gauss_kernel(f[:n], f[:n], cfg["h"])
+    onehot = np.eye(K)[y]
+    A64 = A.astype(np.float64)
+    norm2_sq = spectral_norm_sq(lambda v: A64 @ v, lambda w: A64.T @ w, n, 40, seed)
+    lmin, lmax = cfg["lrange_abs"]
+    p = Problem(name=name, n=n, d=n, K=K, layout="dense", storage=cfg["storage"], A=A, row_ptr=None,
+                col_idx=None, val=None, B=np.ascontiguousarray(onehot[:n]), x_star=np.zeros((n, K)),
+                sketch=cfg["sketch"], m=cfg["m"], s=cfg["s"], sketch_seed=seed, lambda_min=lmin,
+                lambda_max=lmax, lambdas=lambda_grid(lmin, lmax, cfg["T"]), norm2_sq=norm2_sq)
+    if n_test == 0:
+        return p, None, None
+    return p, _gauss_kernel(f[n:], f[:n], cfg["h"]), np.ascontiguousarray(onehot[n:])
+
+
 def make_split(name: str, n_test: int, seed: int = 0, **overrides):
     """A held-out split as in Section 6 (part of the data kept as the test set): the workload is drawn
     with n + n_test rows from one model and split by rows.  Returns (train Problem, A_test, B_test):
     A_test dense (n_test x d, the training problem's storage type; CSR test rows are densified),
     B_test (n_test x K) float64."""
+    if CONFIGS[name]["kind"] == "gkernel":  # test rows: the kernel between new points and the training points
+        cfg = dict(CONFIGS[name])
+        cfg.update(overrides)
+        cfg["d"] = cfg["n"]
+        return _kernel_problem(name, cfg, seed, n_test)
     n = overrides.pop("n", CONFIGS[name]["n"])
     full = make_problem(name, seed=seed, n=n + n_test, **overrides)
     B_test = np.ascontiguousarray(full.B[n:])
