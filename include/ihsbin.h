@@ -181,6 +181,11 @@ typedef struct {
   ihsbin_gram gram;
   ihsbin_loop loop;
   ihsbin_factor factor;
+  double sigma_d2;  /* >= 0: a known lower bound on the smallest eigenvalue of A_hat^T A_hat (the remark
+                     * after Theorem 4); > 0 centres interval [lo, hi] at
+                     * lam0 = sqrt((hi + s)(lo + s)) - s, takes tau = 2 (lam0 + s) / ((lo + s)/rho1 + (hi + s)/rho2)
+                     * and, for auto k, Theorem 4's rate with kt = rho1 (hi + s) / (rho2 (lo + s)); 0 is the
+                     * default rule (lam0 = sqrt(lo hi)) */
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;

@@ -75,36 +75,43 @@ def rho_gaussian(rho: float):
     return (1.0 + r) ** 2, (1.0 - r) ** 2
 
 
-def step_size(lo: float, hi: float, rho1: float, rho2: float) -> float:
-    """Theorem 4 (proof): alpha = 2 lam0 / (lo/rho1 + hi/rho2) with lam0 = sqrt(lo hi)."""
-    lam0 = math.sqrt(lo * hi)
-    return 2.0 * lam0 / (lo / rho1 + hi / rho2)
+def center(lo: float, hi: float, sigma_d2: float = 0.0) -> float:
+    """lam0 of the interval [lo, hi]: sqrt(lo hi) (Section 4.2); with a known sigma_d^2 (the smallest
+    eigenvalue of A^T A; the remark after Theorem 4) sqrt((hi + s)(lo + s)) - s."""
+    return math.sqrt((hi + sigma_d2) * (lo + sigma_d2)) - sigma_d2
+
+
+def step_size(lo: float, hi: float, rho1: float, rho2: float, sigma_d2: float = 0.0) -> float:
+    """Theorem 4 (proof): alpha = 2 lam0 / (lo/rho1 + hi/rho2) with lam0 = sqrt(lo hi); with sigma_d^2
+    (the proof's equation for alpha / (lam0 + sigma_d^2)): 2 (lam0 + s) / ((lo + s)/rho1 + (hi + s)/rho2)."""
+    lam0 = center(lo, hi, sigma_d2)
+    return 2.0 * (lam0 + sigma_d2) / ((lo + sigma_d2) / rho1 + (hi + sigma_d2) / rho2)
 
 
 def make_plan(lmin: float, lmax: float, rho1: Sequence[float], rho2: Sequence[float],
-              k: Sequence[int], L: int = 0) -> Plan:
+              k: Sequence[int], L: int = 0, sigma_d2: float = 0.0) -> Plan:
     if L <= 0:
         L = num_intervals(lmin, lmax)
     edges = interval_edges(lmin, lmax, L)
-    lam0 = np.sqrt(edges[:-1] * edges[1:])
+    lam0 = np.array([center(edges[l], edges[l + 1], sigma_d2) for l in range(L)])
     r1 = np.broadcast_to(np.asarray(rho1, dtype=float), (L,))
     r2 = np.broadcast_to(np.asarray(rho2, dtype=float), (L,))
-    tau = np.array([step_size(edges[l], edges[l + 1], r1[l], r2[l]) for l in range(L)])
+    tau = np.array([step_size(edges[l], edges[l + 1], r1[l], r2[l], sigma_d2) for l in range(L)])
     kk = np.broadcast_to(np.asarray(k, dtype=np.int64), (L,)).copy()
     return Plan(lmin, lmax, L, edges, lam0, tau, kk)
 
 
-def theorem4_k(rho1: float, rho2: float, lo: float, hi: float, eps: float) -> int:
-    """Theorem 4: the error contracts by (kt-1)/(kt+1) per step, kt = rho1 hi / (rho2 lo);
-    the smallest k with ((kt-1)/(kt+1))^k <= eps (capped at 20000)."""
-    kt = rho1 * hi / (rho2 * lo)
+def theorem4_k(rho1: float, rho2: float, lo: float, hi: float, eps: float, sigma_d2: float = 0.0) -> int:
+    """Theorem 4: the error contracts by (kt-1)/(kt+1) per step, kt = rho1 hi / (rho2 lo) (with sigma_d^2:
+    rho1 (hi + s) / (rho2 (lo + s))); the smallest k with ((kt-1)/(kt+1))^k <= eps (capped at 20000)."""
+    kt = rho1 * (hi + sigma_d2) / (rho2 * (lo + sigma_d2))
     rate = (kt - 1.0) / (kt + 1.0)
     k = math.ceil(math.log(eps) / math.log(rate)) if rate > 0 else 1
     return int(min(max(k, 1), 20000))
 
 
 def auto_plan(GS: np.ndarray, m: int, lmin: float, lmax: float, eps: float = 1e-7, L: int = 0,
-              rho_cap: float = 0.95) -> Plan:
+              rho_cap: float = 0.95, sigma_d2: float = 0.0) -> Plan:
     """Parameters from the sketch alone: rho_l = min(d_e/m, rho_cap) with the effective dimension of
     Section 4.2 estimated from the sketched Hessian, d_e = tr(G_S (G_S + lam0 I)^-1)
     = D - lam0 tr((G_S + lam0 I)^-1) (||D||_2 taken as 1); rho1/rho2 by the Gaussian-sketch theorem;
@@ -112,7 +119,7 @@ def auto_plan(GS: np.ndarray, m: int, lmin: float, lmax: float, eps: float = 1e-
     if L <= 0:
         L = num_intervals(lmin, lmax)
     edges = interval_edges(lmin, lmax, L)
-    lam0 = np.sqrt(edges[:-1] * edges[1:])
+    lam0 = np.array([center(edges[l], edges[l + 1], sigma_d2) for l in range(L)])
     D = GS.shape[0]
     r1, r2, ks = [], [], []
     for l in range(L):
@@ -122,8 +129,8 @@ def auto_plan(GS: np.ndarray, m: int, lmin: float, lmax: float, eps: float = 1e-
         a, b = rho_gaussian(rho)
         r1.append(a)
         r2.append(b)
-        ks.append(theorem4_k(a, b, edges[l], edges[l + 1], eps))
-    return make_plan(lmin, lmax, r1, r2, ks, L=L)
+        ks.append(theorem4_k(a, b, edges[l], edges[l + 1], eps, sigma_d2))
+    return make_plan(lmin, lmax, r1, r2, ks, L=L, sigma_d2=sigma_d2)
 
 
 def interval_of(lam: float, plan: Plan) -> int:

@@ -86,9 +86,10 @@ void finalize_plan(ihsbin_problem* p, const double* trP) {
       pl.rho1[l] = (1.0 + std::sqrt(r)) * (1.0 + std::sqrt(r));
       pl.rho2[l] = (1.0 - std::sqrt(r)) * (1.0 - std::sqrt(r));
     }
-    pl.tau[l] = 2.0 * pl.lam0[l] / (lo / pl.rho1[l] + hi / pl.rho2[l]);
+    const double s2 = pl.sigma_d2;
+    pl.tau[l] = 2.0 * (pl.lam0[l] + s2) / ((lo + s2) / pl.rho1[l] + (hi + s2) / pl.rho2[l]);
     if (pl.auto_k) {
-      const double kt = pl.rho1[l] * hi / (pl.rho2[l] * lo);
+      const double kt = pl.rho1[l] * (hi + s2) / (pl.rho2[l] * (lo + s2));
       const double rate = (kt - 1.0) / (kt + 1.0);
       double k = rate > 0 ? std::ceil(std::log(pl.eps) / std::log(rate)) : 1.0;
       pl.k[l] = (int32_t)std::min(std::max(k, 1.0), 20000.0);
@@ -474,6 +475,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   if (!(d->lambda_min > 0) || !(d->lambda_max >= d->lambda_min) || !std::isfinite(d->lambda_max))
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: need 0 < lambda_min <= lambda_max < inf");
   if (d->L < 0 || d->jmax < 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: negative L or jmax");
+  if (!(d->sigma_d2 >= 0) || !std::isfinite(d->sigma_d2))
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: sigma_d2 must be finite and >= 0");
   if (d->compute != IHSBIN_COMPUTE_F64 && d->compute != IHSBIN_COMPUTE_F32X2)
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown compute mode");
   Plan pl;
@@ -495,9 +498,10 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.eps = d->eps > 0 ? d->eps : 1e-7;
   pl.rho1.resize(L);
   pl.rho2.resize(L);
+  pl.sigma_d2 = d->sigma_d2;
   for (int l = 0; l < L; ++l) {
     const double lo = pl.edges[l], hi = pl.edges[l + 1];
-    pl.lam0[l] = std::sqrt(lo * hi);
+    pl.lam0[l] = pl.sigma_d2 > 0 ? std::sqrt((hi + pl.sigma_d2) * (lo + pl.sigma_d2)) - pl.sigma_d2 : std::sqrt(lo * hi);
     double r1, r2;
     if (d->rho1 && d->rho2) {
       r1 = d->rho1[l];

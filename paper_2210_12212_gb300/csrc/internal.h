@@ -53,6 +53,7 @@ struct Plan {
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
+  double sigma_d2 = 0.0;  // known smallest eigenvalue bound (0: the default centring)
   std::vector<double> rho1, rho2;
 };
 

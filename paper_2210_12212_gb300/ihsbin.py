@@ -58,7 +58,7 @@ class PathDesc(C.Structure):
                 ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
                 ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
-                ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int)]
+                ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int), ("sigma_d2", C.c_double)]
 
 
 class AdaptiveDesc(C.Structure):
@@ -238,7 +238,7 @@ class Problem:
                     rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
                     eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", loop: str = "auto",
-                    factor: str = "auto", stream=None):
+                    factor: str = "auto", sigma_d2: float = 0.0, stream=None):
         """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
         gram / loop / factor select the Gram kernel, the recursion's product kernel and the inverse's
         product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
@@ -256,6 +256,7 @@ class Problem:
         pd.gram = GRAM[gram]
         pd.loop = LOOP[loop]
         pd.factor = FACTOR[factor]
+        pd.sigma_d2 = sigma_d2
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",

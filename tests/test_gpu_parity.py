@@ -262,3 +262,38 @@ def test_bf16_gaussian_sketch_entries(ctx, compute):
     res = ob.ihs_bin_path(oracle_A(prob), prob.B, "gaussian", prob.m, 1, 21, plan, prob.lambdas, bf16_sketch=True)
     assert rel_err_max(Xg, res.X) <= TOL[compute]
     gp.close()
+
+
+@pytest.mark.parametrize("compute", ["f64", "f32x2"])
+def test_known_sigma_d_rule(ctx, compute):
+    """The remark after Theorem 4: interval centres and steps from a known smallest eigenvalue
+    (A = U diag(1/k) V^T, so sigma_d^2 = 1/d^2), fixed and sketch-derived parameters."""
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small("c2_small")
+    s2 = 1.0 / prob.d ** 2
+    L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
+    r1, r2, kk = default_params(prob, L, 40)
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute=compute, sigma_d2=s2)
+    Xg = gp.eval_path(prob.lambdas)
+    got = gp.plan()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L, sigma_d2=s2)
+    np.testing.assert_allclose(got["lam0"], plan.lam0, rtol=1e-14)
+    np.testing.assert_allclose(got["tau"], plan.tau, rtol=1e-14)
+    assert np.all(got["lam0"] < np.sqrt(plan.edges[:-1] * plan.edges[1:]))
+    res = ob.ihs_bin_path(oracle_A(prob), prob.B, prob.sketch, prob.m, prob.s, prob.sketch_seed, plan, prob.lambdas)
+    assert rel_err_max(Xg, res.X) <= TOL[compute]
+    # sketch-derived rho and Theorem 4's k with the refined rate
+    gp.build_basis(prob.lambda_min, prob.lambda_max, k=None, k_default=0, eps=1e-6, auto_rho=True,
+                   compute=compute, sigma_d2=s2)
+    Xa = gp.eval_path(prob.lambdas)
+    got = gp.plan()
+    gp.close()
+    SA = osk.apply_srht(oracle_A(prob), prob.m, prob.sketch_seed)
+    ap = ob.auto_plan(SA.T @ SA, prob.m, prob.lambda_min, prob.lambda_max, eps=1e-6, sigma_d2=s2)
+    np.testing.assert_allclose(got["tau"], ap.tau, rtol=1e-9)
+    assert np.abs(got["k"] - ap.k).max() <= 1
+    ap.k = np.asarray(got["k"])
+    res = ob.ihs_bin_path(oracle_A(prob), prob.B, prob.sketch, prob.m, prob.s, prob.sketch_seed, ap, prob.lambdas)
+    assert rel_err_max(Xa, res.X) <= TOL[compute]

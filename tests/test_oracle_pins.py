@@ -331,6 +331,46 @@ def test_theorem4_contraction_bound_holds_with_exact_rhos():
             assert worst_ratio(GS, tau_printed) > 1.0 > bound
 
 
+def test_known_sigma_d_rule_bound_holds_and_tightens():
+    # Remark after Theorem 4: with sigma_d^2 = the smallest eigenvalue of A^T A, lam0 =
+    # sqrt((lmax + s)(lmin + s)) - s and alpha = 2 (lam0 + s) / ((lmin + s)/rho1 + (lmax + s)/rho2),
+    # the energy error contracts per step by at most ((kh-1)/(kh+1))^2, kh = rho1 (lmax + s) / (rho2 (lmin + s)),
+    # with rho1/rho2 the extreme generalised eigenvalues of (G_S + lam0 I, G + lam0 I)
+    rng = np.random.default_rng(21)
+    A = rng.standard_normal((200, 10)) * (1 + np.arange(10)) ** -0.5
+    b = A @ rng.standard_normal(10) + 0.1 * rng.standard_normal(200)
+    G, c = A.T @ A, A.T @ b
+    s2 = np.linalg.eigvalsh(G).min()
+    lmin, lmax = 0.5, 2.0
+    for sig in (s2, 0.5 * s2):
+        lam0 = ob.center(lmin, lmax, sig)
+        assert abs((lam0 + sig) ** 2 - (lmin + sig) * (lmax + sig)) <= 1e-12 * (lmax + sig) ** 2
+        for m in (14, 20, 40):
+            SA = sk.apply_gaussian(A, m, 31)
+            GS = SA.T @ SA
+            gam = sla.eigh(GS + lam0 * np.eye(10), G + lam0 * np.eye(10), eigvals_only=True)
+            r1, r2 = gam.max() * (1 + 1e-9), gam.min() / (1 + 1e-9)
+            tau = ob.step_size(lmin, lmax, r1, r2, sig)
+            P = ob.precond(GS, lam0)
+            worst = 0.0
+            for lam in np.linspace(lmin, lmax, 9):
+                H = G + lam * np.eye(10)
+                xs = np.linalg.solve(H, c)
+                x = np.zeros(10)
+                prev = 0.5 * (x - xs) @ H @ (x - xs)
+                for _ in range(12):
+                    x = x - tau * P.solve(G @ x - c + lam * x)
+                    cur = 0.5 * (x - xs) @ H @ (x - xs)
+                    worst = max(worst, cur / prev)
+                    prev = cur
+            kh = r1 * (lmax + sig) / (r2 * (lmin + sig))
+            kt = r1 * lmax / (r2 * lmin)
+            assert worst <= ((kh - 1) / (kh + 1)) ** 2 < ((kt - 1) / (kt + 1)) ** 2
+    # sigma_d^2 = 0 is the default rule
+    assert ob.center(lmin, lmax, 0.0) == math.sqrt(lmin * lmax)
+    assert ob.step_size(lmin, lmax, 2.0, 0.5, 0.0) == 2 * math.sqrt(lmin * lmax) / (lmin / 2.0 + lmax / 0.5)
+
+
 def test_theorem4_k_meets_its_rate():
     # the chosen k is the first with rate^k <= eps
     lo, hi, r1, r2, eps = 1.0, 1.6, 2.0, 0.3, 1e-7
