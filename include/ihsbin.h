@@ -393,10 +393,10 @@ IHSBIN_API ihsbin_status ihsbin_serve(ihsbin_ctx* ctx, const ihsbin_serve_config
  *
  * GS (D x D, row-major FP64, device) = SA^T SA for SA (m x D, row-major FP64,
  * device) -- the same matrix ihsbin_sketch forms from its sketch.  Callers
- * that cannot call cudaMalloc where they need it (code running under stream
- * capture into a CUDA graph, where cudaMalloc is not capturable; latency-bound
- * callers that cannot absorb an allocation's device synchronisation; hosts
- * whose memory pool forbids library allocations) use this entry point: it
+ * that cannot call cudaMalloc where they need it (latency-bound callers that
+ * cannot absorb the device-wide synchronisation an allocation or free may
+ * cause; hosts that hand all device memory to their own pool or fixed arena and
+ * forbid allocations by libraries) use this entry point: it
  * calls no cudaMalloc, cudaFree or allocating library routine.  Its split-K
  * partial sums live in one file-scope device array of
  * IHSBIN_NOALLOC_SCRATCH_BYTES (16 MiB), which every GPU that loads the

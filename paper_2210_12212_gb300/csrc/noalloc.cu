@@ -2,11 +2,12 @@
 // computed without any device allocation.
 //
 // Who needs it: callers that cannot call cudaMalloc at the point where they
-// need G_S -- code that runs while a stream is being captured into a CUDA graph
-// (cudaMalloc is not a capturable operation), callers on a latency budget that
-// cannot absorb cudaMalloc/cudaFree (both may synchronise the device), and
-// hosts that hand all device memory to their own pool and forbid allocations
-// by libraries.  The regular path (ihsbin_sketch) allocates its split-K
+// need G_S -- callers on a latency budget that cannot absorb cudaMalloc or
+// cudaFree (either may synchronise the whole device and stall other streams),
+// and hosts that hand all device memory to their own pool (a framework's
+// caching allocator, a fixed arena sized at start-up) and forbid allocations
+// by libraries, so that a library allocation would fail or break the pool's
+// accounting.  The regular path (ihsbin_sketch) allocates its split-K
 // partial sums per call; this variant keeps them in one file-scope device
 // array instead.
 //

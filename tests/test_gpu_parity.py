@@ -281,7 +281,9 @@ def test_known_sigma_d_rule(ctx, compute):
     plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L, sigma_d2=s2)
     np.testing.assert_allclose(got["lam0"], plan.lam0, rtol=1e-14)
     np.testing.assert_allclose(got["tau"], plan.tau, rtol=1e-14)
-    assert np.all(got["lam0"] < np.sqrt(plan.edges[:-1] * plan.edges[1:]))
+    # sqrt((hi+s)(lo+s)) - s lies between the geometric and arithmetic means of the edges (AM-GM)
+    lo, hi = plan.edges[:-1], plan.edges[1:]
+    assert np.all(got["lam0"] > np.sqrt(lo * hi)) and np.all(got["lam0"] < 0.5 * (lo + hi))
     res = ob.ihs_bin_path(oracle_A(prob), prob.B, prob.sketch, prob.m, prob.s, prob.sketch_seed, plan, prob.lambdas)
     assert rel_err_max(Xg, res.X) <= TOL[compute]
     # sketch-derived rho and Theorem 4's k with the refined rate

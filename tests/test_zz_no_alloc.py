@@ -1,8 +1,9 @@
 """The allocation-free sketched-Gram entry point against the regular one (GPU).
 
 ihsbin_sketch_gram_noalloc serves callers that cannot allocate device memory
-(for example code running under CUDA-graph stream capture); it keeps its
-split-K partial sums in a static device array shared by all calls.  This file
+(a host whose own pool owns all device memory, or a latency-bound caller that
+cannot absorb the synchronisation of cudaMalloc/cudaFree); it keeps its split-K
+partial sums in a static device array shared by all calls.  This file
 is collected last so that a failure here does not hide any other test.
 """
 import numpy as np
