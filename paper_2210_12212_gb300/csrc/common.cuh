@@ -84,6 +84,29 @@ __device__ __forceinline__ float scale_pow2(float x, int k) {
 // Exact-slice products (tc_loop.cu) leave, per output entry, the exact integers
 //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6
 // of the weight accumulators; the entry is 2^(e_row + e_col - 38) hi + 2^(e_row + e_col - 62) lo.
+// Sum of the n exact int64 partials of the k-splits at off, off + stride, ... (two arrays): the
+// loads go out four splits at a time, so a consumer waits for one memory round trip per four
+// splits instead of one per split, with few registers held (bandwidth-bound consumers keep
+// their occupancy).  Integer addition is exact, so the order does not matter.
+__device__ __forceinline__ void oz_sum_splits(const long long* __restrict__ a, const long long* __restrict__ b, int n,
+                                              int64_t stride, int64_t off, long long& sa, long long& sb) {
+  sa = 0;
+  sb = 0;
+  for (int s0 = 0; s0 < n; s0 += 4) {
+    long long va[4], vb[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const bool in = s0 + q < n;
+      va[q] = in ? __ldg(a + (int64_t)(s0 + q) * stride + off) : 0LL;
+      vb[q] = in ? __ldg(b + (int64_t)(s0 + q) * stride + off) : 0LL;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      sa += va[q];
+      sb += vb[q];
+    }
+  }
+}
 constexpr int OZ_EXP_NONFINITE = 1 << 20;  // row/column exponent marking an Inf/NaN entry
 __device__ __forceinline__ dd oz_join(long long hi, long long lo, int erow, int ecol) {
   if (erow == OZ_EXP_NONFINITE || ecol == OZ_EXP_NONFINITE) return dd{__int_as_float(0x7fc00000), 0.f};

@@ -228,6 +228,7 @@ __global__ void k_reduce_sym(CBuf part, int S, int64_t D, CBuf out) {
   int64_t i = e / D, j = e % D;
   if (i > j) return;
   typename Mode::V v = Mode::ld(part, j * D + i);
+#pragma unroll 4
   for (int s = 1; s < S; ++s) v = Mode::add(v, Mode::ld(part, ((int64_t)s * D + j) * D + i));
   Mode::st(out, i * D + j, v);
   Mode::st(out, j * D + i, v);
@@ -239,6 +240,7 @@ __global__ void k_reduce_cols(CBuf part, int S, int64_t M, int64_t N, CBuf out) 
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * N) return;
   typename Mode::V v = Mode::ld(part, e);
+#pragma unroll 4
   for (int s = 1; s < S; ++s) v = Mode::add(v, Mode::ld(part, (int64_t)s * M * N + e));
   Mode::st(out, e, v);
 }
@@ -563,52 +565,146 @@ __global__ void __launch_bounds__(1024) k_srht_select(const uint64_t* key, int64
 // address bits [b0, b0 + q) of the row index, for a tile of w columns.  The
 // first level reads A_hat (applying the signs D and the zero padding); the
 // last level writes only the kept rows, scaled by 1/sqrt(m), into SA.
+// The Hadamard transform runs on exact integers: each column c of D A is converted once to
+// int64 fixed point, v = round(a 2^k_c), with k_c chosen from the column's largest magnitude so
+// that |v| < 2^(61 - pbits); the pbits butterfly stages can then at most double it pbits times,
+// and every addition is exact (no FP64 arithmetic, a slow pipe here).  The only rounding is the
+// conversion, at 2^-(62 - pbits) of the column's maximum; the kept rows are converted back
+// to FP64 and scaled by 2^-k_c / sqrt(m).
+constexpr int FWHT_NONFINITE = -(1 << 30);  // k_c of a column holding an Inf or NaN
+
+// cmax[c] = bits of max_r |A[r][c]| as FP64 (non-negative doubles order like their bit patterns;
+// a NaN is larger than every finite value and Inf).  cmax must be zero on entry.
+__global__ void k_fwht_colmax(const void* A, int elem, int64_t N, int64_t D, int64_t ld, int64_t rows_per_block,
+                              unsigned long long* cmax) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D) return;
+  const int64_t r0 = (int64_t)blockIdx.y * rows_per_block;
+  const int64_t r1 = r0 + rows_per_block < N ? r0 + rows_per_block : N;
+  unsigned long long m = 0;
+  if (elem == ELEM_F64) {
+    const unsigned long long* a = (const unsigned long long*)A;
+    for (int64_t r = r0; r < r1; ++r) {
+      const unsigned long long b = a[r * ld + c] & 0x7fffffffffffffffull;
+      m = b > m ? b : m;
+    }
+  } else {
+    unsigned mf = 0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const unsigned b = (elem == ELEM_F32 ? __float_as_uint(((const float*)A)[r * ld + c])
+                                           : ((unsigned)((const uint16_t*)A)[r * ld + c]) << 16) & 0x7fffffffu;
+      mf = b > mf ? b : mf;
+    }
+    m = (unsigned long long)__double_as_longlong((double)__uint_as_float(mf));
+  }
+  if (m) atomicMax(cmax + c, m);
+}
+
+// k_c from the column maximum: |a| <= cmax < 2^e, so |a 2^k| < 2^(61 - pbits) with k = 61 - pbits - e.
+__global__ void k_fwht_shift(const unsigned long long* cmax, int64_t D, int pbits, int* kc) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= D) return;
+  const unsigned long long b = cmax[c];
+  const int E = (int)((b >> 52) & 0x7ff);
+  int k;
+  if (E == 0x7ff) k = FWHT_NONFINITE;
+  else if (b == 0) k = 0;
+  else k = 61 - pbits - (E == 0 ? -1022 : E - 1022);
+  kc[c] = k;
+}
+
+// round(x 2^k) for a finite FP32 x with |x 2^k| < 2^62 (ties away from zero), integer operations only
+__device__ __forceinline__ long long f32_to_fixed(float x, int k) {
+  const unsigned u = __float_as_uint(x);
+  const int ex = (int)((u >> 23) & 0xff);
+  if (ex == 0xff) return 0;
+  const unsigned long long mant = ex ? ((u & 0x7fffffu) | 0x800000u) : (u & 0x7fffffu);
+  const int sh = (ex ? ex - 150 : -149) + k;  // |x| 2^k = mant 2^sh
+  unsigned long long mag;
+  if (sh >= 0) mag = mant << sh;
+  else if (sh > -63) mag = (mant + (1ull << (-sh - 1))) >> (-sh);
+  else mag = 0;
+  return (u >> 31) ? -(long long)mag : (long long)mag;
+}
+
+__device__ __forceinline__ long long load_fixed(const void* A, int elem, int64_t i, int k) {
+  if (k == FWHT_NONFINITE) return 0;
+  if (elem == ELEM_F32) return f32_to_fixed(((const float*)A)[i], k);
+  if (elem == ELEM_BF16) return f32_to_fixed(bf16_to_f(((const uint16_t*)A)[i]), k);
+  const double x = ((const double*)A)[i];
+  return isfinite(x) ? __double2ll_rn(ldexp(x, k)) : 0;
+}
+
+// One level of the transform over the q address bits [b0, b0 + q) of the padded rows: a CTA holds
+// the G = 2^q rows of one group (the other bits fixed) for w columns in shared memory and applies
+// the q butterfly stages, two at a time (radix 4) and a last single stage when q is odd.  The
+// first level reads D A (rows >= N are zero), the last writes the kept rows of S A.
 __global__ void k_fwht_level(const void* A, int elem, int64_t N, int64_t D, int64_t ld, const int8_t* dsign,
-                             const double* Yin, double* Yout, int64_t Np, int b0, int q, int w, bool first,
-                             bool last, const int* rowmap, double scale, double* SA) {
-  extern __shared__ double sm[];
+                             const long long* Yin, long long* Yout, int64_t Np, int b0, int q, int w, bool first,
+                             bool last, const int* rowmap, const int* kc, double scale, double* SA) {
+  extern __shared__ long long smi[];
   const int G = 1 << q;
-  const int64_t ngroups = Np >> q;
   const int64_t grp = blockIdx.y;   // group id: the bits outside [b0, b0+q)
   const int64_t c0 = (int64_t)blockIdx.x * w;
   const int64_t lowmask = ((int64_t)1 << b0) - 1;
   const int64_t base = (grp & lowmask) | ((grp >> b0) << (b0 + q));
-  (void)ngroups;
+  (void)Np;
   auto row_of = [&](int t) -> int64_t { return base | ((int64_t)t << b0); };
   for (int e = threadIdx.x; e < G * w; e += blockDim.x) {
-    int t = e / w, cc = e % w;
-    int64_t r = row_of(t), c = c0 + cc;
-    double v = 0.0;
+    const int t = e / w, cc = e % w;
+    const int64_t r = row_of(t), c = c0 + cc;
+    long long v = 0;
     if (c < D) {
       if (first) {
-        if (r < N) v = load_elem_d(A, elem, r * ld + c) * (double)dsign[r];
+        if (r < N) {
+          v = load_fixed(A, elem, r * ld + c, kc[c]);
+          if (dsign[r] < 0) v = -v;
+        }
       } else {
         v = Yin[r * D + c];
       }
     }
-    sm[t * w + cc] = v;
+    smi[t * w + cc] = v;
   }
   __syncthreads();
-  for (int h = 1; h < G; h <<= 1) {
+  int h = 1;
+  for (; 4 * h <= G; h <<= 2) {  // stages h and 2h together
+    for (int e = threadIdx.x; e < (G / 4) * w; e += blockDim.x) {
+      const int gi = e / w, cc = e % w;
+      const int i0 = (gi & (h - 1)) | ((gi & ~(h - 1)) << 2);
+      long long* x = smi + cc;
+      const long long x0 = x[i0 * w], x1 = x[(i0 + h) * w], x2 = x[(i0 + 2 * h) * w], x3 = x[(i0 + 3 * h) * w];
+      const long long y0 = x0 + x1, y1 = x0 - x1, y2 = x2 + x3, y3 = x2 - x3;
+      x[i0 * w] = y0 + y2;
+      x[(i0 + h) * w] = y1 + y3;
+      x[(i0 + 2 * h) * w] = y0 - y2;
+      x[(i0 + 3 * h) * w] = y1 - y3;
+    }
+    __syncthreads();
+  }
+  if (h < G) {  // q odd: the last stage alone
     for (int e = threadIdx.x; e < (G / 2) * w; e += blockDim.x) {
-      int pr = e / w, cc = e % w;
-      int lo = (pr / h) * (2 * h) + (pr % h);
-      int hi = lo + h;
-      double a = sm[lo * w + cc], b = sm[hi * w + cc];
-      sm[lo * w + cc] = a + b;
-      sm[hi * w + cc] = a - b;
+      const int pr = e / w, cc = e % w;
+      const int lo = (pr / h) * (2 * h) + (pr % h), hi = lo + h;
+      const long long a = smi[lo * w + cc], b = smi[hi * w + cc];
+      smi[lo * w + cc] = a + b;
+      smi[hi * w + cc] = a - b;
     }
     __syncthreads();
   }
   for (int e = threadIdx.x; e < G * w; e += blockDim.x) {
-    int t = e / w, cc = e % w;
-    int64_t r = row_of(t), c = c0 + cc;
+    const int t = e / w, cc = e % w;
+    const int64_t r = row_of(t), c = c0 + cc;
     if (c >= D) continue;
     if (last) {
-      int k = rowmap[r];
-      if (k >= 0) SA[(int64_t)k * D + c] = sm[t * w + cc] * scale;
+      const int k = rowmap[r];
+      if (k >= 0) {
+        const int sh = kc[c];
+        SA[(int64_t)k * D + c] = sh == FWHT_NONFINITE ? __longlong_as_double(0x7ff8000000000000ll)
+                                                      : ldexp((double)smi[t * w + cc], -sh) * scale;
+      }
     } else {
-      Yout[r * D + c] = sm[t * w + cc];
+      Yout[r * D + c] = smi[t * w + cc];
     }
   }
 }
@@ -635,6 +731,25 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
   }
   CK(cudaGetLastError());
   const double scale = 1.0 / std::sqrt((double)m);
+  // column scales of the fixed-point transform
+  unsigned long long* cmax = nullptr;
+  int* kc = nullptr;
+  CK(prob_alloc(p, D * sizeof(unsigned long long), (void**)&cmax, SCOPE_SCRATCH));
+  CK(prob_alloc(p, D * sizeof(int), (void**)&kc, SCOPE_SCRATCH));
+  CK(cudaMemsetAsync(cmax, 0, D * sizeof(unsigned long long), st));
+  {
+    const double es = A.elem == ELEM_F64 ? 8 : A.elem == ELEM_F32 ? 4 : 2;
+    KTimer kt(p, K_SKETCH_APPLY, st, 0, (double)N * D * es);
+    const int64_t rpb = 256;
+    dim3 grid(nblocks(D, 128), (unsigned)((N + rpb - 1) / rpb));
+    k_fwht_colmax<<<grid, 128, 0, st>>>(A.A, A.elem, N, D, A.ld, rpb, cmax);
+  }
+  CK(cudaGetLastError());
+  {
+    KTimer kt(p, K_SKETCH_APPLY, st, 0, (double)D * 12);
+    k_fwht_shift<<<nblocks(D, 256), 256, 0, st>>>(cmax, D, pbits, kc);
+  }
+  CK(cudaGetLastError());
   // split the pbits address bits into levels of at most 12 bits
   std::vector<std::pair<int, int>> levels;
   if (pbits == 0) levels.push_back({0, 0});
@@ -646,19 +761,19 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
     levels.push_back({done, q});
     done += q;
   }
-  double* Y0 = nullptr;
-  double* Y1 = nullptr;
+  long long* Y0 = nullptr;
+  long long* Y1 = nullptr;
   if (levels.size() > 1) {
-    CK(prob_alloc(p, Np * D * sizeof(double), (void**)&Y0, SCOPE_SCRATCH));
-    if (levels.size() > 2) CK(prob_alloc(p, Np * D * sizeof(double), (void**)&Y1, SCOPE_SCRATCH));
+    CK(prob_alloc(p, Np * D * sizeof(long long), (void**)&Y0, SCOPE_SCRATCH));
+    if (levels.size() > 2) CK(prob_alloc(p, Np * D * sizeof(long long), (void**)&Y1, SCOPE_SCRATCH));
   }
-  const double* yin = nullptr;
-  double* yout = Y0;
+  const long long* yin = nullptr;
+  long long* yout = Y0;
   for (size_t l = 0; l < levels.size(); ++l) {
     int b0 = levels[l].first, q = levels[l].second;
     int G = 1 << q;
     int w = std::max(1, std::min(32, 6144 / G));
-    size_t smem = (size_t)G * w * sizeof(double);
+    size_t smem = (size_t)G * w * sizeof(long long);
     dim3 grid(nblocks(D, w), (unsigned)(Np >> q));
     bool first = (l == 0), last = (l + 1 == levels.size());
     if (smem > 48 * 1024)
@@ -668,7 +783,7 @@ cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st) {
     const double wr = last ? (double)m * D * 8 : (double)Np * D * 8;
     KTimer kt(p, K_SKETCH_APPLY, st, (double)Np * D * q, rd + wr);
     k_fwht_level<<<grid, 256, smem, st>>>(A.A, A.elem, N, D, A.ld, p->sk_sign, yin, yout, Np, b0, q, w, first, last,
-                                           rowmap, scale, p->SA);
+                                           rowmap, kc, scale, p->SA);
     CK(cudaGetLastError());
     yin = yout;
     yout = (yout == Y0) ? Y1 : Y0;
@@ -1336,6 +1451,7 @@ struct LdR {
     T u = Mode::ld(U, o);
     const int64_t yo = (int64_t)g * ys + col * D + k;
     T y = Mode::ld(Y, yo);
+#pragma unroll 4
     for (int s = 1; s < ny; ++s) y = Mode::add(y, Mode::ld(Y, s * ny_stride + yo));
     T r = Mode::mul(Mode::from_d(tau[l]), Mode::add(y, Mode::mul(lm, u)));
     if (j > 0) r = Mode::add(r, Mode::mul(lm, Mode::ld(U, o - K * D)));
@@ -1378,6 +1494,7 @@ __global__ void k_make_R(CBuf Y, int ny, int64_t ny_stride, CBuf U, int live, in
   } else {
     const int64_t yo = ((int64_t)g * nold + col) * D + k;
     typename Mode::V y = Mode::ld(Y, yo);
+#pragma unroll 4
     for (int s = 1; s < ny; ++s) y = Mode::add(y, Mode::ld(Y, s * ny_stride + yo));
     r = Mode::mul(Mode::from_d(tau[l]), Mode::add(y, Mode::mul(lm, Mode::ld(U, o))));
     if (j > 0) r = Mode::add(r, Mode::mul(lm, Mode::ld(U, o - K * D)));
@@ -1395,6 +1512,7 @@ __global__ void k_update(CBuf Z, int S, int live, int64_t ncol, int64_t D, int64
   const int64_t col = (e / D) % ncol, row = e % D;
   const int64_t zo = ((int64_t)g * ncol + col) * D + row;
   typename Mode::V z = Mode::ld(Z, zo);
+#pragma unroll 4
   for (int s = 1; s < S; ++s) z = Mode::add(z, Mode::ld(Z, (int64_t)s * live * ncol * D + zo));
   const int64_t o = (int64_t)perm[g] * gs + col * D + row;
   const int64_t j = col / K;

@@ -149,6 +149,9 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
+  // launched with programmatic serialization: everything above overlapped the predecessor
+  tc::pdl_wait();
+  tc::pdl_trigger();
   const uint32_t tmem = tmem_base;
   volatile int* abort_v = &abort_flag;
 
@@ -582,6 +585,46 @@ __global__ void __launch_bounds__(128) k_oz_slice_data_rows(const void* X, int64
   }
 }
 
+// As k_oz_slice_vecs for short vectors (K <= 256: at most 32 chunks of 8 entries): one warp per
+// vector, four vectors per CTA, the largest magnitude by a warp reduction.  Same digits and
+// exponents as the one-CTA-per-vector kernel.
+__global__ void __launch_bounds__(128) k_oz_slice_vecs_warp(CBuf X, int64_t gs, int64_t off, int64_t vstride,
+                                                            int64_t K, int64_t nvec, int TH, int NTL, int KB,
+                                                            __nv_bfloat16* out, int* e) {
+  const int lane = threadIdx.x & 31;
+  const int64_t v = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int g = blockIdx.y;
+  if (v >= (int64_t)NTL * TH) return;  // whole warps only
+  const bool valid = v < nvec;
+  const int64_t base = (int64_t)g * gs + off + (valid ? v : 0) * vstride;
+  const float* xh = (const float*)X.p0 + base;
+  const float* xl = (const float*)X.p1 + base;
+  const int c = lane;                  // this lane's chunk of 8 entries
+  const bool has = c < KB * 4;
+  float h[8], l[8];
+  float m = 0.f;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t k = (int64_t)c * 8 + q;
+    const bool in = valid && has && k < K;
+    h[q] = in ? xh[k] : 0.f;
+    l[q] = in ? xl[k] : 0.f;
+    const float a = fabsf(h[q]);
+    m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int ev = oz_exp(m);
+  const bool live = valid && ev != OZ_NONFINITE;
+  if (lane == 0) e[(int64_t)g * NTL * TH + v] = ev;
+  if (!has) return;
+  const int tile = (int)(v / TH), nl = (int)(v - (int64_t)tile * TH);
+  const int64_t bblk = (int64_t)TH * OZ_BK;
+  const int kb = c >> 2, kc = c & 3;
+  store_digits(h, l, ev, live, out + ((((int64_t)g * NTL + tile) * KB + kb) * OZ_S) * bblk +
+                                  ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
+}
+
 // Block-wide slicing of one column held in shared memory (hi[D], lo[D]) into tile-height-NT
 // layout position (group 0): column c, tile c / NT.  Every thread of the CTA takes part.
 constexpr int OZ_FUSED_THREADS = 512;
@@ -634,6 +677,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_make_R_oz_slice(const long
                                                          int* er) {
   extern __shared__ float colbuf[];  // hi[D], lo[D]
   __shared__ float red[OZ_FUSED_THREADS / 32];
+  tc::pdl_wait();
+  tc::pdl_trigger();
   float* bh = colbuf;
   float* bl = colbuf + D;
   const int64_t c = blockIdx.x, per = (int64_t)NTL * NT;
@@ -651,11 +696,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_make_R_oz_slice(const long
         r = dd_mul(lm, DD::ld(U, o - K * D));
       } else {
         const int64_t cc = (int64_t)g * nold + col, yo = cc * D + k;
-        long long h = Yhi[yo], w = Ylo[yo];
-        for (int s = 1; s < ny; ++s) {
-          h += Yhi[s * ny_stride + yo];
-          w += Ylo[s * ny_stride + yo];
-        }
+        long long h, w;
+        oz_sum_splits(Yhi, Ylo, ny, ny_stride, yo, h, w);
         r = dd_mul(tl, dd_add(oz_join(h, w, eg[k], eu[cc]), dd_mul(lm, DD::ld(U, o))));
         if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
       }
@@ -680,6 +722,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long
                                                          int live_next, int NTn, int KB, __nv_bfloat16* Us, int* eu) {
   extern __shared__ float colbuf[];
   __shared__ float red[OZ_FUSED_THREADS / 32];
+  tc::pdl_wait();
+  tc::pdl_trigger();
   float* bh = colbuf;
   float* bl = colbuf + D;
   const int g = (int)(blockIdx.x / ncol);
@@ -689,11 +733,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long
   const int ec = er[(int64_t)g * er_gs + col];
   for (int64_t row = threadIdx.x; row < D; row += OZ_FUSED_THREADS) {
     const int64_t zo = ((int64_t)g * ncol + col) * D + row;
-    long long h = Zhi[zo], w = Zlo[zo];
-    for (int s = 1; s < S; ++s) {
-      h += Zhi[s * ss + zo];
-      w += Zlo[s * ss + zo];
-    }
+    long long h, w;
+    oz_sum_splits(Zhi, Zlo, S, ss, zo, h, w);
     const dd z = oz_join(h, w, ep[(int64_t)l * ep_gs + row], ec);
     const int64_t o = (int64_t)l * gs + col * D + row;
     dd u = (j < i) ? DD::ld(Uin, o) : DD::zero();
@@ -727,8 +768,7 @@ cudaError_t launch_oz(const OzArgs& a, cudaStream_t st) {
   CK(cudaFuncSetAttribute(k_oz_mma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const int64_t items = (int64_t)a.NTL * a.MT * a.groups * a.ksplit;
   const unsigned grid = (unsigned)std::min<int64_t>(items, sm_count());  // one CTA per SM (shared memory)
-  k_oz_mma<NT><<<grid, C::THREADS, C::SMEM, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_mma<NT>, dim3(grid), dim3(C::THREADS), C::SMEM, st, a);
 }
 
 }  // namespace
@@ -813,8 +853,14 @@ cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm
 cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K, int64_t nvec, int groups,
                           int TH, __nv_bfloat16* out, int* e, cudaStream_t st) {
   const int NTL = (int)((nvec + TH - 1) / TH);
+  const int KB = (int)((K + OZ_BK - 1) / OZ_BK);
+  if (KB * 4 <= 32) {
+    dim3 grid((unsigned)((NTL * TH + 3) / 4), (unsigned)groups);
+    k_oz_slice_vecs_warp<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
+    return cudaGetLastError();
+  }
   dim3 grid((unsigned)(NTL * TH), (unsigned)groups);
-  k_oz_slice_vecs<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out, e);
+  k_oz_slice_vecs<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
   return cudaGetLastError();
 }
 
@@ -838,9 +884,9 @@ cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, 
   const int NTL = (int)((nnew + NT - 1) / NT);
   const int smem = (int)(D * 8);
   if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_make_R_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_make_R_oz_slice<<<(unsigned)((int64_t)live * NTL * NT), OZ_FUSED_THREADS, smem, st>>>(
-      Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau, lam0, gs, NT, NTL, oz_kb(D), Rs, er);
-  return cudaGetLastError();
+  return launch_pdl(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT)), dim3(OZ_FUSED_THREADS), smem, st,
+                    Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau, lam0, gs, NT, NTL, oz_kb(D), Rs,
+                    er);
 }
 
 cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
@@ -849,10 +895,9 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
                             int* eu, cudaStream_t st) {
   const int smem = (int)(D * 8);
   if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  k_update_oz_slice<<<(unsigned)((int64_t)live * ncol), OZ_FUSED_THREADS, smem, st>>>(Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol,
-                                                                         D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn,
-                                                                         oz_kb(D), Us, eu);
-  return cudaGetLastError();
+  return launch_pdl(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Zhi,
+                    Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn, oz_kb(D),
+                    Us, eu);
 }
 
 cudaError_t oz_slice_data_rows(const void* X, int elem, int64_t ld, int64_t K, int64_t nvec, int TH,
