@@ -57,6 +57,8 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   static_assert((BM * BK) % NT == 0 && (BK * BN) % NT == 0, "tile/thread mismatch");
   constexpr int LA_PER = BM * BK / NT;
   constexpr int LB_PER = BK * BN / NT;
+  pdl_wait();  // launched with programmatic serialization (launch_gemm)
+  pdl_trigger();
 
   const int g = blockIdx.z / sh.ksplit;
   const int sp = blockIdx.z % sh.ksplit;
@@ -166,8 +168,8 @@ template <class Mode, int BM, int BN, int BK, int TM, int TN, class LA, class LB
 inline cudaError_t launch_gemm(GemmShape sh, int groups, LA la, LB lb, EP ep, cudaStream_t st) {
   if (sh.M <= 0 || sh.N <= 0 || groups <= 0) return cudaSuccess;
   dim3 grid((unsigned)((sh.N + BN - 1) / BN), (unsigned)((sh.M + BM - 1) / BM), (unsigned)(groups * sh.ksplit));
-  gemm_kernel<Mode, BM, BN, BK, TM, TN, LA, LB, EP><<<grid, (BM / TM) * (BN / TN), 0, st>>>(sh, la, lb, ep);
-  return cudaGetLastError();
+  return launch_pdl(gemm_kernel<Mode, BM, BN, BK, TM, TN, LA, LB, EP>, grid, dim3((BM / TM) * (BN / TN)), 0, st, sh, la,
+                    lb, ep);
 }
 
 }  // namespace ihsbin

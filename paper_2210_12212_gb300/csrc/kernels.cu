@@ -816,6 +816,8 @@ constexpr int NB = 32;
 // column) and store the inverse of the resulting lower-triangular block.
 template <class Mode>
 __global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, CBuf dinv, int* status) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   using V = typename Mode::V;
   const int l = blockIdx.x;
   const int64_t off = (int64_t)l * D * D;
@@ -1094,6 +1096,8 @@ struct EpStoreRowMajor {  // out[g * gs + i * ld + j]
 __global__ void k_oz_store_wblock(const long long* hi, const long long* lo, int S, int64_t M, int64_t N, int L,
                                   const int* ex, int64_t exg, const int* ey, int64_t eyg, int64_t D, int64_t R0,
                                   int64_t J0, CBuf W) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)L * M * N) return;
   const int64_t i = e % M, j = (e / M) % N, g = e / (M * N);
@@ -1154,9 +1158,8 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
     }
     {
       KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * nR * B * (16.0 * S + 8));
-      k_oz_store_wblock<<<nblocks((int64_t)L * nR * B, 256), 256, 0, st>>>(
-          hi, lo, S, nR, B, L, ex, (int64_t)oz_vec_exps(nR, 128), ey, (int64_t)oz_vec_exps(B, 32), D, R0, J0, Wm);
-      CK(cudaGetLastError());
+      CK(launch_pdl(k_oz_store_wblock, dim3(nblocks((int64_t)L * nR * B, 256)), dim3(256), 0, st, hi, lo, S, nR, B, L,
+                    ex, (int64_t)oz_vec_exps(nR, 128), ey, (int64_t)oz_vec_exps(B, 32), D, R0, J0, Wm));
     }
   }
   return cudaSuccess;
@@ -1168,6 +1171,8 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
 // as an exact-slice product on the tensor cores (symmetric: tiles touching i <= j).
 __global__ void k_oz_sub_sym(const long long* hi, const long long* lo, int S, int64_t M, int L, const int* ea,
                              int64_t eag, const int* eb, int64_t ebg, int64_t D, int64_t c1, CBuf H) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)L * M * M) return;
   const int64_t i = e % M, j = (e / M) % M, g = e / (M * M);
@@ -1217,14 +1222,15 @@ static cudaError_t panel_update(ihsbin_problem* p, CBuf H, const PanelUpdate& u,
     CK(oz_gemm(q, st));
   }
   KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * M * M * (16.0 + 16.0));
-  k_oz_sub_sym<<<nblocks((int64_t)L * M * M, 256), 256, 0, st>>>(u.hi, u.lo, 1, M, L, u.ea, (int64_t)oz_vec_exps(M, 128),
-                                                                 u.eb, (int64_t)oz_vec_exps(M, 32), D, c1, H);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_sub_sym, dim3(nblocks((int64_t)L * M * M, 256)), dim3(256), 0, st, u.hi, u.lo, 1, M, L, u.ea,
+                    (int64_t)oz_vec_exps(M, 128), u.eb, (int64_t)oz_vec_exps(M, 32), D, c1, H);
 }
 
 // P_l[i][j] = P_l[j][i] (i <= j) from the exact partials of W_l^T W_l on the tensor cores
 __global__ void k_oz_store_sym(const long long* hi, const long long* lo, int S, int64_t D, int L, const int* ea,
                                int64_t ea_gs, const int* eb, int64_t eb_gs, CBuf P) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)L * D * D) return;
   const int64_t l = e / (D * D), rr = e - l * D * D, j = rr / D, i = rr - j * D;
@@ -1269,9 +1275,8 @@ static cudaError_t inverse_slices(ihsbin_problem* p, CBuf Wm, cudaStream_t st) {
     CK(oz_gemm(q, st));
   }
   KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * D * D * (16 + 16));
-  k_oz_store_sym<<<nblocks((int64_t)L * D * D, 256), 256, 0, st>>>(hi, lo, 1, D, L, ea, (int64_t)oz_vec_exps(D, 128), eb,
-                                                                 (int64_t)oz_vec_exps(D, 32), p->Pinv);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_store_sym, dim3(nblocks((int64_t)L * D * D, 256)), dim3(256), 0, st, hi, lo, 1, D, L, ea,
+                    (int64_t)oz_vec_exps(D, 128), eb, (int64_t)oz_vec_exps(D, 32), p->Pinv);
 }
 
 template <class Mode>
@@ -1292,7 +1297,7 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
   for (int kb = 0; kb < nblk; ++kb) {
     {
       KTimer kt(p, K_FACTOR_POTRF, st, (double)L * NB * NB * NB * 2.0 / 3.0, (double)L * NB * NB * cs * 3);
-      k_potrf_diag<Mode><<<L, 256, 0, st>>>(H, D, kb, dinv, p->status);
+      CK(launch_pdl(k_potrf_diag<Mode>, dim3(L), dim3(256), 0, st, H, D, kb, dinv, p->status));
     }
     CK(cudaGetLastError());
     const int64_t r0 = (int64_t)(kb + 1) * NB;

@@ -150,8 +150,8 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
   __syncthreads();
   tc::fence_after_sync();
   // launched with programmatic serialization: everything above overlapped the predecessor
-  tc::pdl_wait();
-  tc::pdl_trigger();
+  pdl_wait();
+  pdl_trigger();
   const uint32_t tmem = tmem_base;
   volatile int* abort_v = &abort_flag;
 
@@ -369,6 +369,8 @@ __device__ __forceinline__ void store_digits(const float (&hi)[8], const float (
 // 128 mt .. +127, k = 32 kb .. +31; element (r, kk) at byte (r/8)*512 + (kk/8)*128 + (r%8)*16 + (kk%8)*2.
 __global__ void __launch_bounds__(128) k_oz_slice_rows(CBuf X, int64_t D, int64_t gs, int MT, int KB,
                                                        __nv_bfloat16* out, int* ea) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   __shared__ float red[4];
   const int64_t i = blockIdx.x;
   const int g = blockIdx.y;
@@ -452,6 +454,8 @@ __global__ void __launch_bounds__(128) k_oz_slice_cols(CBuf X, int64_t D, int64_
 // Layout as k_oz_slice_cols with tile height TH.
 __global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int64_t gs,
                                                           int TH, int NTL, int KB, __nv_bfloat16* out, int* e) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   __shared__ float red[8][33];
   __shared__ int ex[32];
   const int x = threadIdx.x, y = threadIdx.y, g = blockIdx.y;
@@ -499,6 +503,8 @@ __global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, in
 __global__ void __launch_bounds__(128) k_oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int64_t K,
                                                        int64_t nvec, int TH, int NTL, int KB, __nv_bfloat16* out,
                                                        int* e) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   __shared__ float red[4];
   const int64_t v = blockIdx.x;
   const int g = blockIdx.y;
@@ -591,6 +597,8 @@ __global__ void __launch_bounds__(128) k_oz_slice_data_rows(const void* X, int64
 __global__ void __launch_bounds__(128) k_oz_slice_vecs_warp(CBuf X, int64_t gs, int64_t off, int64_t vstride,
                                                             int64_t K, int64_t nvec, int TH, int NTL, int KB,
                                                             __nv_bfloat16* out, int* e) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
   const int lane = threadIdx.x & 31;
   const int64_t v = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
   const int g = blockIdx.y;
@@ -677,8 +685,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_make_R_oz_slice(const long
                                                          int* er) {
   extern __shared__ float colbuf[];  // hi[D], lo[D]
   __shared__ float red[OZ_FUSED_THREADS / 32];
-  tc::pdl_wait();
-  tc::pdl_trigger();
+  pdl_wait();
+  pdl_trigger();
   float* bh = colbuf;
   float* bl = colbuf + D;
   const int64_t c = blockIdx.x, per = (int64_t)NTL * NT;
@@ -722,8 +730,8 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long
                                                          int live_next, int NTn, int KB, __nv_bfloat16* Us, int* eu) {
   extern __shared__ float colbuf[];
   __shared__ float red[OZ_FUSED_THREADS / 32];
-  tc::pdl_wait();
-  tc::pdl_trigger();
+  pdl_wait();
+  pdl_trigger();
   float* bh = colbuf;
   float* bl = colbuf + D;
   const int g = (int)(blockIdx.x / ncol);
@@ -747,6 +755,14 @@ __global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long
   if (g >= live_next) return;  // uniform over the CTA
   __syncthreads();
   slice_smem_column(bh, bl, D, (int64_t)g * ncol + col, NTn, KB, red, Us, eu);
+}
+
+// The recursion alternates these kernels with k_oz_mma, which takes almost all of an SM's shared
+// memory; giving them the same L1 / shared-memory split spares the SM a reconfiguration (a drain)
+// at every switch.
+template <typename K>
+cudaError_t same_carveout(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
@@ -785,8 +801,7 @@ size_t oz_cols_exps(int64_t ncolg, int NT) { return (size_t)((ncolg + NT - 1) / 
 
 cudaError_t oz_slice_rows(CBuf X, int64_t D, int groups, int64_t gs, __nv_bfloat16* out, int* ea, cudaStream_t st) {
   dim3 grid((unsigned)(oz_mt(D) * 128), (unsigned)groups);
-  k_oz_slice_rows<<<grid, 128, 0, st>>>(X, D, gs, oz_mt(D), oz_kb(D), out, ea);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_slice_rows, grid, dim3(128), 0, st, X, D, gs, oz_mt(D), oz_kb(D), out, ea);
 }
 
 cudaError_t oz_slice_cols(CBuf X, int64_t D, int ngroups, int64_t ncolg, int NT, int64_t cpg, int64_t gs,
@@ -856,12 +871,10 @@ cudaError_t oz_slice_vecs(CBuf X, int64_t gs, int64_t off, int64_t vstride, int6
   const int KB = (int)((K + OZ_BK - 1) / OZ_BK);
   if (KB * 4 <= 32) {
     dim3 grid((unsigned)((NTL * TH + 3) / 4), (unsigned)groups);
-    k_oz_slice_vecs_warp<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
-    return cudaGetLastError();
+    return launch_pdl(k_oz_slice_vecs_warp, grid, dim3(128), 0, st, X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
   }
   dim3 grid((unsigned)(NTL * TH), (unsigned)groups);
-  k_oz_slice_vecs<<<grid, 128, 0, st>>>(X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_slice_vecs, grid, dim3(128), 0, st, X, gs, off, vstride, K, nvec, TH, NTL, KB, out, e);
 }
 
 int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int cap) {
@@ -883,6 +896,7 @@ cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, 
                             __nv_bfloat16* Rs, int* er, cudaStream_t st) {
   const int NTL = (int)((nnew + NT - 1) / NT);
   const int smem = (int)(D * 8);
+  CK(same_carveout(k_make_R_oz_slice));
   if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_make_R_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return launch_pdl(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT)), dim3(OZ_FUSED_THREADS), smem, st,
                     Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau, lam0, gs, NT, NTL, oz_kb(D), Rs,
@@ -894,6 +908,7 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
                             CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
                             int* eu, cudaStream_t st) {
   const int smem = (int)(D * 8);
+  CK(same_carveout(k_update_oz_slice));
   if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   return launch_pdl(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Zhi,
                     Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn, oz_kb(D),
@@ -920,8 +935,8 @@ cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int gr
                              __nv_bfloat16* out, int* e, cudaStream_t st) {
   const int NTL = (int)((nvec + TH - 1) / TH);
   dim3 grid((unsigned)((NTL * TH + 31) / 32), (unsigned)groups), blk(32, 8);
-  k_oz_slice_matcols<<<grid, blk, 0, st>>>(X, ld, K, nvec, gs, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out, e);
-  return cudaGetLastError();
+  return launch_pdl(k_oz_slice_matcols, grid, blk, 0, st, X, ld, K, nvec, gs, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out,
+                    e);
 }
 
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max) {
