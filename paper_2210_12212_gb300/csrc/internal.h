@@ -200,6 +200,12 @@ struct OzGemm {
   bool a_shared = false;
   const __nv_bfloat16* Bs = nullptr;
   const int* eb = nullptr;
+  bool b_shared = false;  // one B for every group
+  // pair mode: group 2q multiplies A group q of As (a_perm) and group 2q + 1 A group q of As2
+  // (a_perm2), both by B group q
+  int pair = 0;
+  const __nv_bfloat16* As2 = nullptr;
+  const int* a_perm2 = nullptr;
   int64_t M = 0, N = 0, K = 0;
   int groups = 1, NT = 32, ksplit = 1, tri = 0, sym = 0;
   long long* ohi = nullptr;  // exact partials, entry ((s * groups + g) * N + j) * M + i
@@ -207,6 +213,14 @@ struct OzGemm {
   int* status = nullptr;
 };
 cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st);
+// the recursion's update in the two-product form (partials of M_q U and P_l U from a pair-mode product)
+cudaError_t oz_update_mw_slice(const long long* Phi, const long long* Plo, int S, const int* em, const int* ep,
+                               int live, int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout, CBuf Ut,
+                               const int* perm, const double* tau, const double* lam0, int64_t gs, const int* eu_in,
+                               int live_next, __nv_bfloat16* Us, int* eu, cudaStream_t st);
+// M_q = P_l (G + lam0_l I) from the exact partials of G P_l
+cudaError_t oz_make_M(const long long* hi, const long long* lo, int S, int64_t D, int T, const int* eg, const int* epc,
+                      int64_t epc_gs, const int* perm, const double* lam0, CBuf P, CBuf M, cudaStream_t st);
 size_t oz_vec_elems(int64_t nvec, int64_t K, int TH);  // slices of nvec vectors of length K, tile height TH
 size_t oz_vec_exps(int64_t nvec, int TH);
 // vectors = the columns of row-major float-float matrices (K rows, row stride ld, group stride gs)

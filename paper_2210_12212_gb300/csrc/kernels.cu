@@ -1620,6 +1620,12 @@ struct OzLoop {
   int* eb = nullptr;                  // its column exponents (the step's U columns)
   int* er = nullptr;                  // column exponents of R (fused path)
   long long *Yhi = nullptr, *Ylo = nullptr, *Zhi = nullptr, *Zlo = nullptr;  // exact split partials
+  // two-product form of the recursion (from step mform_from on): M_q = P_l (G + lam0_l I) for the
+  // intervals order[0 .. Tm-1], rows sliced; column exponents alternate between eb and eb2
+  int mform_from = 0;
+  const __nv_bfloat16* Ms = nullptr;
+  const int* em = nullptr;
+  int* eb2 = nullptr;
 };
 
 template <class Mode, int ET>
@@ -1650,6 +1656,35 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     const int64_t nnew = (int64_t)std::min(i + 1, J) * K;
     const int64_t ys = nold * D;
     const int64_t mt = (D + 63) / 64;
+    int live_next = 0;
+    if (i + 1 < pl.kmax)
+      while (live_next < L && pl.k[order[live_next]] > i + 1) ++live_next;
+    if (oz.mform_from > 0 && i >= oz.mform_from) {
+      // two-product form: [M_q U_q, P_l U_q] for every live interval in one launch, then the update
+      // (ncol = nold = nnew = jmax K columns, tile height 16)
+      const int64_t ncol = nold;
+      const int ks = oz_pick_split(D, ncol, 2 * live, 16, SPLIT_MAX);
+      const int parity = (i - oz.mform_from) & 1;
+      int* eu_in = parity ? oz.eb2 : oz.eb;
+      int* eu_out = parity ? oz.eb : oz.eb2;
+      {
+        OzGemm q;
+        q.As = oz.Ms; q.As2 = oz.Ps; q.a_perm2 = perm_dev; q.pair = 1;
+        q.Bs = oz.Bs;
+        q.M = D; q.N = ncol; q.K = D; q.groups = 2 * live; q.NT = 16; q.ksplit = ks;
+        q.ohi = oz.Zhi; q.olo = oz.Zlo; q.status = p->status;
+        KTimer kt(p, K_LOOP_P_TC, st, 2.0 * oz_pair_flops(D, ncol, D) * live,
+                  (double)2 * live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, ncol, 16) * 2) + 32.0 * ks * D * ncol * live);
+        CK(oz_gemm(q, st));
+      }
+      {
+        KTimer kt(p, K_LOOP_P, st, 0, (double)live * ncol * D * (32.0 * ks + 24 + 12));
+        CK(oz_update_mw_slice(oz.Zhi, oz.Zlo, ks, oz.em, oz.ep, live, ncol, D, K, Uin, Uout, p->Ut, perm_dev, tau_dev,
+                              lam0_dev, gs, eu_in, live_next, oz.Bs, eu_out, st));
+      }
+      std::swap(Uin, Uout);
+      continue;
+    }
     int ny = 1;
     const bool fused = oz.on && pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D);
     if (pl.product == IHSBIN_PRODUCT_GRAM && oz.on) {
@@ -1731,10 +1766,9 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       }
       if (fused) {
         // the intervals still running at the next step take their new columns' slices now
-        int live_next = 0;
-        if (i + 1 < pl.kmax)
-          while (live_next < L && pl.k[order[live_next]] > i + 1) ++live_next;
-        const int NTn = live_next > 0 ? oz_tile_n(nnew * live_next) : 16;
+        // (tile height 16 when the next step takes the two-product form)
+        const int NTn = (live_next > 0 && !(oz.mform_from > 0 && i + 1 >= oz.mform_from)) ? oz_tile_n(nnew * live_next)
+                                                                                       : 16;
         KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24 + 12));
         CK(oz_update_slice(oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er, (int64_t)oz_cols_exps(nnew, NT),
                            live, nnew, D, K, i, Uin, Uout, p->Ut, perm_dev, gs, live_next, NTn, oz.Bs, oz.eb, st));
@@ -1939,6 +1973,25 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     CK(prob_alloc(p, (size_t)bcols * ((D + 31) / 32) * 6 * 32 * 2, (void**)&Bs, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * 4, (void**)&eb, SCOPE_SCRATCH));
     CK(prob_alloc(p, (size_t)bcols * 4, (void**)&oz.er, SCOPE_SCRATCH));
+    // The two-product form of the recursion (basis_loop) for the longest intervals: from the first
+    // step at or after the truncation (all intervals then hold jmax K columns, a multiple of the
+    // tile height 16) at which at most MFORM_LIVE intervals are still running.  It spends one D^3
+    // product per interval on M_q = P_l (G + lam0_l I) and saves two of the four launches of every
+    // later step.
+    constexpr int MFORM_LIVE = 6;
+    int mform_from = 0, Tm = 0;
+    if (pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D) && pl.jmax > 0 && ((int64_t)pl.jmax * K) % 16 == 0) {
+      for (int i = std::max(pl.jmax, 2); i < pl.kmax; ++i) {
+        int live = 0;
+        while (live < L && pl.k[order[live]] > i) ++live;
+        if (live == 0) break;
+        if (live <= MFORM_LIVE) {
+          mform_from = i;
+          Tm = live;
+          break;
+        }
+      }
+    }
     // the largest split partials of any step, replaying the recursion's (live, columns, splits)
     size_t ymax = 1, zmax = 1;
     {
@@ -1948,6 +2001,10 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
         while (live < L && pl.k[order[live]] > i) ++live;
         if (live == 0) break;
         const int64_t nold = (int64_t)std::min(i, J) * K, nnew = (int64_t)std::min(i + 1, J) * K;
+        if (mform_from > 0 && i >= mform_from) {
+          zmax = std::max(zmax, (size_t)oz_pick_split(D, nold, 2 * live, 16, SPLIT_MAX) * 2 * live * nold * D);
+          continue;
+        }
         const int64_t ncat = nold * live;
         if (pl.product == IHSBIN_PRODUCT_GRAM)
           ymax = std::max(ymax, (size_t)oz_pick_split(D, ncat, 1, oz_tile_n(ncat), SPLIT_MAX) * ncat * D);
@@ -1976,6 +2033,48 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     oz.ep = ep;
     oz.Bs = Bs;
     oz.eb = eb;
+    if (mform_from > 0) {
+      // M_q = P_l G + lam0_l P_l for l = order[q], q < Tm: the exact-slice product G P_l (A = the
+      // rows of G, shared; B = the columns of P_l), joined with lam0_l P_l, then cut by rows
+      __nv_bfloat16 *Pc = nullptr, *Ms = nullptr;
+      int *epc = nullptr, *em = nullptr;
+      long long *mh = nullptr, *ml = nullptr;
+      const size_t vcol = oz_vec_elems(D, D, 32), vexp = oz_vec_exps(D, 32);
+      const int ks = oz_pick_split_mnk(D, D, D, Tm, 32, SPLIT_MAX);
+      CK(prob_alloc(p, vcol * 2 * Tm, (void**)&Pc, SCOPE_SCRATCH));
+      CK(prob_alloc(p, vexp * 4 * Tm, (void**)&epc, SCOPE_SCRATCH));
+      CK(prob_alloc(p, (size_t)ks * Tm * D * D * 8, (void**)&mh, SCOPE_SCRATCH));
+      CK(prob_alloc(p, (size_t)ks * Tm * D * D * 8, (void**)&ml, SCOPE_SCRATCH));
+      CK(prob_alloc(p, oz_rows_elems(D) * 2 * Tm, (void**)&Ms, SCOPE_SCRATCH));
+      CK(prob_alloc(p, oz_rows_exps(D) * 4 * Tm, (void**)&em, SCOPE_SCRATCH));
+      CK(prob_alloc(p, (size_t)bcols * 4, (void**)&oz.eb2, SCOPE_SCRATCH));
+      CBuf Mb = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)Tm * D * D, SCOPE_SCRATCH, &err);
+      CK(err);
+      {
+        KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)Tm * D * D * 8 + (double)Tm * vcol * 2);
+        CK(oz_slice_cols(p->Pinv, D, Tm, D, 32, D, D * D, perm_dev, Pc, epc, st));
+      }
+      {
+        OzGemm q;
+        q.As = oz.Gs; q.a_shared = true; q.Bs = Pc;
+        q.M = D; q.N = D; q.K = D; q.groups = Tm; q.NT = 32; q.ksplit = ks;
+        q.ohi = mh; q.olo = ml; q.status = p->status;
+        KTimer kt(p, K_INVERSE_TC, st, oz_pair_flops(D, D, D) * Tm,
+                  (double)oz_rows_elems(D) * 2 + (double)Tm * vcol * 2 + 16.0 * ks * Tm * D * D);
+        CK(oz_gemm(q, st));
+      }
+      {
+        KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)Tm * D * D * (16.0 * ks + 16));
+        CK(oz_make_M(mh, ml, ks, D, Tm, oz.eg, epc, (int64_t)vexp, perm_dev, lam0_dev, p->Pinv, Mb, st));
+      }
+      {
+        KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)Tm * D * D * 8 + (double)Tm * oz_rows_elems(D) * 2);
+        CK(oz_slice_rows(Mb, D, Tm, D * D, Ms, em, st));
+      }
+      oz.Ms = Ms;
+      oz.em = em;
+      oz.mform_from = mform_from;
+    }
   }
   CK((basis_loop<Mode, ET>(p, c, U0, U1, Y, Z, R, Wtmp, perm_dev, tau_dev, lam0_dev, order, oz, st)));
 

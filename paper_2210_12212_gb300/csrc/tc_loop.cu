@@ -86,6 +86,11 @@ struct OzArgs {
   int groups, ksplit, kbper;
   int tri;               // OZ_TRI_* flags: zero blocks of triangular operands skipped per tile
   int sym;               // 1: only tiles that touch i <= j (symmetric result)
+  // pair mode: group 2q takes A group q of As (a_perm), group 2q + 1 takes A group q of As2
+  // (a_perm2); both multiply B group q
+  int pair;
+  const __nv_bfloat16* As2;
+  const int* a_perm2;
   long long* ohi;        // exact partials (weights 0..3 / 4..6), entry ((s * groups + g) * N + j) * M + i
   long long* olo;
   int* status;
@@ -105,8 +110,8 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
   const int items = a.NTL * a.MT * a.groups * a.ksplit;
 
   struct Item {
-    int nt, mt, g, sp, ag, kb0, nkb;
-    bool skip;
+    int nt, mt, g, sp, ag, bg, kb0, nkb;
+    bool skip, a2;
   };
   auto decode = [&](int item) {
     Item w;
@@ -116,7 +121,10 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
     r /= a.MT;
     w.sp = r % a.ksplit;
     w.g = r / a.ksplit;
-    w.ag = a.a_perm ? a.a_perm[w.g] : w.g;
+    w.a2 = a.pair && (w.g & 1);
+    w.bg = a.pair ? (w.g >> 1) : w.g;
+    const int* pm = w.a2 ? a.a_perm2 : a.a_perm;
+    w.ag = pm ? pm[w.bg] : w.bg;
     w.kb0 = w.sp * a.kbper;
     int kb1 = min(a.KB, w.kb0 + a.kbper);
     if (a.tri & OZ_TRI_GE_ROW) w.kb0 = max(w.kb0, (w.mt * 128) / OZ_BK);         // k >= the tile's first row
@@ -162,9 +170,9 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
         const Item w = decode(item);
         const __nv_bfloat16* gA =
-            a.As + (int64_t)w.ag * a.a_gstride + ((int64_t)w.mt * a.KB + w.kb0) * (OZ_S * OZ_ABLK);
+            (w.a2 ? a.As2 : a.As) + (int64_t)w.ag * a.a_gstride + ((int64_t)w.mt * a.KB + w.kb0) * (OZ_S * OZ_ABLK);
         const __nv_bfloat16* gB =
-            a.Bs + (int64_t)w.g * a.b_gstride + ((int64_t)w.nt * a.KB + w.kb0) * (OZ_S * C::BBLK);
+            a.Bs + (int64_t)w.bg * a.b_gstride + ((int64_t)w.nt * a.KB + w.kb0) * (OZ_S * C::BBLK);
         for (int it = 0; it < w.nkb; ++it, ++q) {
           const uint32_t st = q % C::STAGES, rnd = q / C::STAGES;
           if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
@@ -765,6 +773,75 @@ cudaError_t same_carveout(K kernel) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
+// The recursion in the two-product form (intervals with M_q = P_l (G + lam0_l I) formed):
+//   u_{i+1,j} = u_{i,j} - tau_l M_q u_{i,j} - lam0_l P_l u_{i,j-1}   (no second term for j = 0),
+// the same polynomial as R = tau (G u_j + lam0 u_j) + lam0 u_{j-1}, u_j <- u_j - P_l R, with
+// both products taken over the step's old columns in one launch (pair mode: group 2q holds
+// M_q U_q, group 2q + 1 holds P_l U_q).  One CTA per column (q, col) of the ncol columns of
+// each live interval (every column exists: the basis is truncated to ncol = jmax K columns);
+// the new column is cut into the next step's slices (tile height 16, column q ncol + col).
+__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_mw_slice(const long long* Phi, const long long* Plo, int S,
+                                                         const int* em, const int* ep, int64_t e_gs, int live,
+                                                         int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout,
+                                                         CBuf Ut, const int* perm, const double* tau,
+                                                         const double* lam0, int64_t gs, const int* eu_in,
+                                                         int live_next, int KB, __nv_bfloat16* Us, int* eu) {
+  extern __shared__ float colbuf[];
+  __shared__ float red[OZ_FUSED_THREADS / 32];
+  pdl_wait();
+  pdl_trigger();
+  float* bh = colbuf;
+  float* bl = colbuf + D;
+  const int q = (int)(blockIdx.x / ncol);
+  const int64_t col = blockIdx.x - (int64_t)q * ncol;
+  const int l = perm[q];
+  const bool has_w = col >= K;  // j >= 1
+  const int64_t ss = 2 * (int64_t)live * ncol * D;           // stride of the k-splits
+  const int64_t zo = ((int64_t)(2 * q) * ncol + col) * D;     // M_q u_j
+  const int64_t wo = ((int64_t)(2 * q + 1) * ncol + col - K) * D;  // P_l u_{j-1}
+  const int ez = eu_in[(int64_t)q * ncol + col];
+  const int ew = has_w ? eu_in[(int64_t)q * ncol + col - K] : 0;
+  const dd tl = dd_from_double(tau[l]), lm = dd_from_double(lam0[l]);
+  for (int64_t row = threadIdx.x; row < D; row += OZ_FUSED_THREADS) {
+    long long h, w;
+    oz_sum_splits(Phi, Plo, S, ss, zo + row, h, w);
+    dd t = dd_mul(tl, oz_join(h, w, em[(int64_t)q * e_gs + row], ez));
+    if (has_w) {
+      oz_sum_splits(Phi, Plo, S, ss, wo + row, h, w);
+      t = dd_add(t, dd_mul(lm, oz_join(h, w, ep[(int64_t)l * e_gs + row], ew)));
+    }
+    const int64_t o = (int64_t)l * gs + col * D + row;
+    const dd u = dd_sub(DD::ld(Uin, o), t);
+    DD::st(Uout, o, u);
+    DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
+    bh[row] = u.hi;
+    bl[row] = u.lo;
+  }
+  if (q >= live_next) return;  // uniform over the CTA
+  __syncthreads();
+  slice_smem_column(bh, bl, D, (int64_t)q * ncol + col, 16, KB, red, Us, eu);
+}
+
+// M_q = P_l (G + lam0_l I), l = perm[q], from the exact partials of G P_l (A = the rows of G,
+// B = the columns of P_l; P_l and G are symmetric, so entry (i, j) of G P_l is entry (j, i) of
+// P_l G): M_q[j][i] = (G P_l)[i][j] + lam0_l P_l[j][i], row-major, float-float.
+__global__ void k_oz_make_M(const long long* hi, const long long* lo, int S, int64_t D, int T, const int* eg,
+                            const int* epc, int64_t epc_gs, const int* perm, const double* lam0, CBuf P, CBuf M) {
+  pdl_wait();  // launched with programmatic serialization
+  pdl_trigger();
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)T * D * D) return;
+  const int64_t q = e / (D * D), r = e - q * D * D, j = r / D, i = r - j * D;
+  long long h = 0, w = 0;
+  for (int s = 0; s < S; ++s) {
+    h += hi[(int64_t)s * T * D * D + e];
+    w += lo[(int64_t)s * T * D * D + e];
+  }
+  const int l = perm[q];
+  const dd v = oz_join(h, w, eg[i], epc[q * epc_gs + j]);
+  DD::st(M, e, dd_add(v, dd_mul(dd_from_double(lam0[l]), DD::ld(P, (int64_t)l * D * D + r))));
+}
+
 inline int oz_kb(int64_t D) { return (int)((D + OZ_BK - 1) / OZ_BK); }
 inline int oz_mt(int64_t D) { return (int)((D + 127) / 128); }
 
@@ -834,7 +911,7 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   a.ea = q.ea;
   a.ea_gstride = q.a_shared ? 0 : (int64_t)oz_vec_exps(q.M, 128);
   a.Bs = q.Bs;
-  a.b_gstride = (int64_t)oz_vec_elems(q.N, q.K, q.NT);
+  a.b_gstride = q.b_shared ? 0 : (int64_t)oz_vec_elems(q.N, q.K, q.NT);
   a.eb = q.eb;
   a.eb_gstride = (int64_t)oz_vec_exps(q.N, q.NT);
   a.KB = KB;
@@ -848,6 +925,10 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   if (a.ksplit != q.ksplit || a.kbper > OZ_KB_MAX) return cudaErrorInvalidValue;
   a.tri = q.tri;
   a.sym = q.sym;
+  a.pair = q.pair;
+  a.As2 = q.As2;
+  a.a_perm2 = q.a_perm2;
+  if (q.pair && (q.groups & 1)) return cudaErrorInvalidValue;
   a.ohi = q.ohi;
   a.olo = q.olo;
   a.status = q.status;
@@ -913,6 +994,25 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
   return launch_pdl(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Zhi,
                     Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn, oz_kb(D),
                     Us, eu);
+}
+
+cudaError_t oz_update_mw_slice(const long long* Phi, const long long* Plo, int S, const int* em, const int* ep,
+                               int live, int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout, CBuf Ut,
+                               const int* perm, const double* tau, const double* lam0, int64_t gs, const int* eu_in,
+                               int live_next, __nv_bfloat16* Us, int* eu, cudaStream_t st) {
+  const int smem = (int)(D * 8);
+  CK(same_carveout(k_update_mw_slice));
+  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_mw_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  return launch_pdl(k_update_mw_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Phi, Plo,
+                    S, em, ep, (int64_t)oz_rows_exps(D), live, ncol, D, K, Uin, Uout, Ut, perm, tau, lam0, gs, eu_in,
+                    live_next, oz_kb(D), Us, eu);
+}
+
+cudaError_t oz_make_M(const long long* hi, const long long* lo, int S, int64_t D, int T, const int* eg, const int* epc,
+                      int64_t epc_gs, const int* perm, const double* lam0, CBuf P, CBuf M, cudaStream_t st) {
+  const int64_t n = (int64_t)T * D * D;
+  return launch_pdl(k_oz_make_M, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, st, hi, lo, S, D, T, eg, epc, epc_gs,
+                    perm, lam0, P, M);
 }
 
 cudaError_t oz_slice_data_rows(const void* X, int elem, int64_t ld, int64_t K, int64_t nvec, int TH,
