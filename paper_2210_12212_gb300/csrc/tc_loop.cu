@@ -37,6 +37,9 @@
 #include "internal.h"
 #include "tc.cuh"
 
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
 namespace ihsbin {
 namespace {
 
@@ -641,185 +644,238 @@ __global__ void __launch_bounds__(128) k_oz_slice_vecs_warp(CBuf X, int64_t gs, 
                                   ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
 }
 
-// Block-wide slicing of one column held in shared memory (hi[D], lo[D]) into tile-height-NT
-// layout position (group 0): column c, tile c / NT.  Every thread of the CTA takes part.
-constexpr int OZ_FUSED_THREADS = 512;
+// ---- The recursion's per-column kernels (right-hand sides, updates) with the next product's
+// slicing fused.  A column of D rows is handled by a cluster of CL <= 8 CTAs: CTA r of the cluster
+// owns the whole k-blocks [r KBC, (r + 1) KBC) of 32 rows (KBC = ceil(KB / CL)), one row per
+// thread, so the loads of a row's split partials all go out together and a column spreads over
+// CL SMs.  The column's largest magnitude (its slicing exponent) is reduced across the cluster
+// through distributed shared memory; each CTA then cuts its own k-blocks.
+constexpr int OZ_COL_THREADS_MAX = 512;
 
-__device__ __forceinline__ float block_max_fused(float v, float* red) {  // blockDim.x = OZ_FUSED_THREADS
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-  __syncthreads();
-  float m = red[0];
-#pragma unroll
-  for (int w = 1; w < OZ_FUSED_THREADS / 32; ++w) m = fmaxf(m, red[w]);
-  return m;
+struct ColPart {
+  int64_t c;       // column (cluster) index
+  int64_t r0, r1;  // rows [r0, r1) of this CTA
+  int rank, CL;
+};
+
+__device__ __forceinline__ ColPart col_part(int64_t D, int KBC) {
+  cg::cluster_group cl = cg::this_cluster();
+  ColPart p;
+  p.rank = (int)cl.block_rank();
+  p.CL = (int)cl.num_blocks();
+  p.c = blockIdx.x / p.CL;
+  p.r0 = (int64_t)p.rank * KBC * OZ_BK;
+  p.r1 = min(D, p.r0 + (int64_t)KBC * OZ_BK);
+  if (p.r1 < p.r0) p.r1 = p.r0;
+  return p;
 }
 
-__device__ __forceinline__ void slice_smem_column(const float* hi, const float* lo, int64_t D, int64_t c, int NT, int KB,
-                                                  float* red, __nv_bfloat16* out, int* e) {
+// Sum of n exact int64 split partials of up to two entries (offsets o1, o2; the second only when
+// two is true): eight splits of every array per round, all loads of a round issued together.
+__device__ __forceinline__ void oz_sum_splits2(const long long* __restrict__ a, const long long* __restrict__ b, int n,
+                                               int64_t stride, int64_t o1, int64_t o2, bool two, long long& s1a,
+                                               long long& s1b, long long& s2a, long long& s2b) {
+  s1a = s1b = s2a = s2b = 0;
+  for (int s0 = 0; s0 < n; s0 += 8) {
+    long long v1a[8], v1b[8], v2a[8], v2b[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool in = s0 + q < n;
+      const int64_t so = (int64_t)(s0 + q) * stride;
+      v1a[q] = in ? __ldg(a + so + o1) : 0LL;
+      v1b[q] = in ? __ldg(b + so + o1) : 0LL;
+      v2a[q] = (in && two) ? __ldg(a + so + o2) : 0LL;
+      v2b[q] = (in && two) ? __ldg(b + so + o2) : 0LL;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      s1a += v1a[q];
+      s1b += v1b[q];
+      s2a += v2a[q];
+      s2b += v2b[q];
+    }
+  }
+}
+
+// Cut this CTA's k-blocks of column c (its rows held in hi / lo from offset 0) into the
+// tile-height-NT layout (column c, tile c / NT) with the cluster-wide exponent, written to e[c].
+__device__ void cluster_slice_column(const float* hi, const float* lo, const ColPart& p, int64_t D, int64_t c, int NT,
+                                     int KB, int KBC, float* red, float* smax, __nv_bfloat16* out, int* e) {
+  const int nrow = (int)(p.r1 - p.r0);
   float m = 0.f;
-  for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) {
+  for (int k = threadIdx.x; k < nrow; k += blockDim.x) {
     const float a = fabsf(hi[k]);
     m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
   }
-  m = block_max_fused(m, red);
-  const int ev = oz_exp(m);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, red[w]);
+    *smax = b;
+  }
+  cg::cluster_group cl = cg::this_cluster();
+  cl.sync();
+  float gm = 0.f;
+  for (int r = 0; r < p.CL; ++r) gm = fmaxf(gm, *cl.map_shared_rank(smax, r));
+  cl.sync();  // every CTA has read the others' maxima before any leaves
+  const int ev = oz_exp(gm);
   const bool live = ev != OZ_NONFINITE;
-  if (threadIdx.x == 0) e[c] = ev;
+  if (p.rank == 0 && threadIdx.x == 0) e[c] = ev;
   const int tile = (int)(c / NT), nl = (int)(c - (int64_t)tile * NT);
   const int64_t bblk = (int64_t)NT * OZ_BK;
-  for (int ch = threadIdx.x; ch < KB * 4; ch += OZ_FUSED_THREADS) {
-    const int kb = ch >> 2, kc = ch & 3;
+  for (int ch = threadIdx.x; ch < KBC * 4; ch += blockDim.x) {
+    const int kb = p.rank * KBC + (ch >> 2), kc = ch & 3;
+    if (kb >= KB) continue;
     float h[8], l[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const int64_t k = (int64_t)ch * 8 + q;
-      h[q] = (live && k < D) ? hi[k] : 0.f;
-      l[q] = (live && k < D) ? lo[k] : 0.f;
+      const int k = ch * 8 + q;  // row p.r0 + k
+      const bool in = live && p.r0 + k < D;
+      h[q] = in ? hi[k] : 0.f;
+      l[q] = in ? lo[k] : 0.f;
     }
     store_digits(h, l, ev, live, out + (((int64_t)tile * KB + kb) * OZ_S) * bblk +
                                    ((nl >> 3) * 512 + kc * 128 + (nl & 7) * 16) / 2, bblk);
   }
 }
 
-// The recursion's right-hand sides R (as k_make_R_oz) with their slicing fused: one CTA per
-// column of R, padded to NTL x NT per live interval; R stays in shared memory.
-__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo, int ny,
-                                                         int64_t ny_stride, const int* eg, const int* eu, CBuf U,
-                                                         int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
-                                                         const int* perm, const double* tau, const double* lam0,
-                                                         int64_t gs, int NT, int NTL, int KB, __nv_bfloat16* Rs,
-                                                         int* er) {
-  extern __shared__ float colbuf[];  // hi[D], lo[D]
-  __shared__ float red[OZ_FUSED_THREADS / 32];
+// The recursion's right-hand sides R (as k_make_R_oz) with their slicing fused: one cluster per
+// column of R, padded to NTL x NT per live interval.
+__global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo,
+                                                            int ny, int64_t ny_stride, const int* eg, const int* eu,
+                                                            CBuf U, int64_t nold, int64_t nnew, int64_t D, int64_t K,
+                                                            int inew, const int* perm, const double* tau,
+                                                            const double* lam0, int64_t gs, int NT, int NTL, int KB,
+                                                            int KBC, __nv_bfloat16* Rs, int* er) {
+  extern __shared__ float colbuf[];  // hi[KBC 32], lo[KBC 32]
+  __shared__ float red[OZ_COL_THREADS_MAX / 32];
+  __shared__ float smax;
   pdl_wait();
   pdl_trigger();
+  const ColPart pt = col_part(D, KBC);
   float* bh = colbuf;
-  float* bl = colbuf + D;
-  const int64_t c = blockIdx.x, per = (int64_t)NTL * NT;
-  const int g = (int)(c / per);
-  const int64_t col = c - g * per;
+  float* bl = colbuf + KBC * OZ_BK;
+  const int64_t per = (int64_t)NTL * NT;
+  const int g = (int)(pt.c / per);
+  const int64_t col = pt.c - g * per;
   const bool valid = col < nnew;
   if (valid) {
     const int l = perm[g];
     const int64_t j = col / K;
     const dd lm = dd_from_double(lam0[l]), tl = dd_from_double(tau[l]);
-    for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) {
+    for (int64_t k = pt.r0 + threadIdx.x; k < pt.r1; k += blockDim.x) {
       const int64_t o = (int64_t)l * gs + col * D + k;
       dd r;
       if (j == inew) {
         r = dd_mul(lm, DD::ld(U, o - K * D));
       } else {
         const int64_t cc = (int64_t)g * nold + col, yo = cc * D + k;
-        long long h, w;
-        oz_sum_splits(Yhi, Ylo, ny, ny_stride, yo, h, w);
+        long long h, w, h2, w2;
+        oz_sum_splits2(Yhi, Ylo, ny, ny_stride, yo, yo, false, h, w, h2, w2);
         r = dd_mul(tl, dd_add(oz_join(h, w, eg[k], eu[cc]), dd_mul(lm, DD::ld(U, o))));
         if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
       }
-      bh[k] = r.hi;
-      bl[k] = r.lo;
+      bh[k - pt.r0] = r.hi;
+      bl[k - pt.r0] = r.lo;
     }
   } else {
-    for (int64_t k = threadIdx.x; k < D; k += OZ_FUSED_THREADS) bh[k] = bl[k] = 0.f;
+    for (int64_t k = pt.r0 + threadIdx.x; k < pt.r1; k += blockDim.x) bh[k - pt.r0] = bl[k - pt.r0] = 0.f;
   }
   __syncthreads();
   // group g's tiles start at tile g * NTL
-  slice_smem_column(bh, bl, D, (int64_t)g * per + col, NT, KB, red, Rs, er);
+  cluster_slice_column(bh, bl, pt, D, (int64_t)g * per + col, NT, KB, KBC, red, &smax, Rs, er);
 }
 
 // The update of the recursion (as k_update_oz) with the next step's slicing of the new columns
-// fused: one CTA per new column (g, col); for an interval still live at the next step, the new
-// u is cut into the next step's concatenated-column layout (column g * ncol + col, tile NTn).
-__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_oz_slice(const long long* Zhi, const long long* Zlo, int S,
-                                                         const int* ep, int64_t ep_gs, const int* er, int64_t er_gs,
-                                                         int live, int64_t ncol, int64_t D, int64_t K, int i,
-                                                         CBuf Uin, CBuf Uout, CBuf Ut, const int* perm, int64_t gs,
-                                                         int live_next, int NTn, int KB, __nv_bfloat16* Us, int* eu) {
+// fused: one cluster per new column (g, col); for an interval still live at the next step, the
+// new u is cut into the next step's concatenated-column layout (column g * ncol + col, tile NTn).
+__global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_update_oz_slice(const long long* Zhi, const long long* Zlo,
+                                                            int S, const int* ep, int64_t ep_gs, const int* er,
+                                                            int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K,
+                                                            int i, CBuf Uin, CBuf Uout, CBuf Ut, const int* perm,
+                                                            int64_t gs, int live_next, int NTn, int KB, int KBC,
+                                                            __nv_bfloat16* Us, int* eu) {
   extern __shared__ float colbuf[];
-  __shared__ float red[OZ_FUSED_THREADS / 32];
+  __shared__ float red[OZ_COL_THREADS_MAX / 32];
+  __shared__ float smax;
   pdl_wait();
   pdl_trigger();
+  const ColPart pt = col_part(D, KBC);
   float* bh = colbuf;
-  float* bl = colbuf + D;
-  const int g = (int)(blockIdx.x / ncol);
-  const int64_t col = blockIdx.x - (int64_t)g * ncol;
+  float* bl = colbuf + KBC * OZ_BK;
+  const int g = (int)(pt.c / ncol);
+  const int64_t col = pt.c - (int64_t)g * ncol;
   const int l = perm[g];
   const int64_t j = col / K, ss = (int64_t)live * ncol * D;
   const int ec = er[(int64_t)g * er_gs + col];
-  for (int64_t row = threadIdx.x; row < D; row += OZ_FUSED_THREADS) {
+  for (int64_t row = pt.r0 + threadIdx.x; row < pt.r1; row += blockDim.x) {
     const int64_t zo = ((int64_t)g * ncol + col) * D + row;
-    long long h, w;
-    oz_sum_splits(Zhi, Zlo, S, ss, zo, h, w);
+    long long h, w, h2, w2;
+    oz_sum_splits2(Zhi, Zlo, S, ss, zo, zo, false, h, w, h2, w2);
     const dd z = oz_join(h, w, ep[(int64_t)l * ep_gs + row], ec);
     const int64_t o = (int64_t)l * gs + col * D + row;
     dd u = (j < i) ? DD::ld(Uin, o) : DD::zero();
     u = dd_sub(u, z);
     DD::st(Uout, o, u);
     DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
-    bh[row] = u.hi;
-    bl[row] = u.lo;
+    bh[row - pt.r0] = u.hi;
+    bl[row - pt.r0] = u.lo;
   }
-  if (g >= live_next) return;  // uniform over the CTA
+  if (g >= live_next) return;  // uniform over the cluster
   __syncthreads();
-  slice_smem_column(bh, bl, D, (int64_t)g * ncol + col, NTn, KB, red, Us, eu);
-}
-
-// The recursion alternates these kernels with k_oz_mma, which takes almost all of an SM's shared
-// memory; giving them the same L1 / shared-memory split spares the SM a reconfiguration (a drain)
-// at every switch.
-template <typename K>
-cudaError_t same_carveout(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+  cluster_slice_column(bh, bl, pt, D, (int64_t)g * ncol + col, NTn, KB, KBC, red, &smax, Us, eu);
 }
 
 // The recursion in the two-product form (intervals with M_q = P_l (G + lam0_l I) formed):
 //   u_{i+1,j} = u_{i,j} - tau_l M_q u_{i,j} - lam0_l P_l u_{i,j-1}   (no second term for j = 0),
 // the same polynomial as R = tau (G u_j + lam0 u_j) + lam0 u_{j-1}, u_j <- u_j - P_l R, with
 // both products taken over the step's old columns in one launch (pair mode: group 2q holds
-// M_q U_q, group 2q + 1 holds P_l U_q).  One CTA per column (q, col) of the ncol columns of
+// M_q U_q, group 2q + 1 holds P_l U_q).  One cluster per column (q, col) of the ncol columns of
 // each live interval (every column exists: the basis is truncated to ncol = jmax K columns);
 // the new column is cut into the next step's slices (tile height 16, column q ncol + col).
-__global__ void __launch_bounds__(OZ_FUSED_THREADS) k_update_mw_slice(const long long* Phi, const long long* Plo, int S,
-                                                         const int* em, const int* ep, int64_t e_gs, int live,
-                                                         int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout,
-                                                         CBuf Ut, const int* perm, const double* tau,
-                                                         const double* lam0, int64_t gs, const int* eu_in,
-                                                         int live_next, int KB, __nv_bfloat16* Us, int* eu) {
+__global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_update_mw_slice(const long long* Phi, const long long* Plo,
+                                                            int S, const int* em, const int* ep, int64_t e_gs, int live,
+                                                            int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout,
+                                                            CBuf Ut, const int* perm, const double* tau,
+                                                            const double* lam0, int64_t gs, const int* eu_in,
+                                                            int live_next, int KB, int KBC, __nv_bfloat16* Us,
+                                                            int* eu) {
   extern __shared__ float colbuf[];
-  __shared__ float red[OZ_FUSED_THREADS / 32];
+  __shared__ float red[OZ_COL_THREADS_MAX / 32];
+  __shared__ float smax;
   pdl_wait();
   pdl_trigger();
+  const ColPart pt = col_part(D, KBC);
   float* bh = colbuf;
-  float* bl = colbuf + D;
-  const int q = (int)(blockIdx.x / ncol);
-  const int64_t col = blockIdx.x - (int64_t)q * ncol;
+  float* bl = colbuf + KBC * OZ_BK;
+  const int q = (int)(pt.c / ncol);
+  const int64_t col = pt.c - (int64_t)q * ncol;
   const int l = perm[q];
   const bool has_w = col >= K;  // j >= 1
-  const int64_t ss = 2 * (int64_t)live * ncol * D;           // stride of the k-splits
-  const int64_t zo = ((int64_t)(2 * q) * ncol + col) * D;     // M_q u_j
-  const int64_t wo = ((int64_t)(2 * q + 1) * ncol + col - K) * D;  // P_l u_{j-1}
+  const int64_t ss = 2 * (int64_t)live * ncol * D;                  // stride of the k-splits
+  const int64_t zo = ((int64_t)(2 * q) * ncol + col) * D;            // M_q u_j
+  const int64_t wo = ((int64_t)(2 * q + 1) * ncol + col - K) * D;    // P_l u_{j-1}
   const int ez = eu_in[(int64_t)q * ncol + col];
   const int ew = has_w ? eu_in[(int64_t)q * ncol + col - K] : 0;
   const dd tl = dd_from_double(tau[l]), lm = dd_from_double(lam0[l]);
-  for (int64_t row = threadIdx.x; row < D; row += OZ_FUSED_THREADS) {
-    long long h, w;
-    oz_sum_splits(Phi, Plo, S, ss, zo + row, h, w);
-    dd t = dd_mul(tl, oz_join(h, w, em[(int64_t)q * e_gs + row], ez));
-    if (has_w) {
-      oz_sum_splits(Phi, Plo, S, ss, wo + row, h, w);
-      t = dd_add(t, dd_mul(lm, oz_join(h, w, ep[(int64_t)l * e_gs + row], ew)));
-    }
+  for (int64_t row = pt.r0 + threadIdx.x; row < pt.r1; row += blockDim.x) {
+    long long zh, zl, wh, wl;
+    oz_sum_splits2(Phi, Plo, S, ss, zo + row, wo + row, has_w, zh, zl, wh, wl);
+    dd t = dd_mul(tl, oz_join(zh, zl, em[(int64_t)q * e_gs + row], ez));
+    if (has_w) t = dd_add(t, dd_mul(lm, oz_join(wh, wl, ep[(int64_t)l * e_gs + row], ew)));
     const int64_t o = (int64_t)l * gs + col * D + row;
     const dd u = dd_sub(DD::ld(Uin, o), t);
     DD::st(Uout, o, u);
     DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
-    bh[row] = u.hi;
-    bl[row] = u.lo;
+    bh[row - pt.r0] = u.hi;
+    bl[row - pt.r0] = u.lo;
   }
-  if (q >= live_next) return;  // uniform over the CTA
+  if (q >= live_next) return;  // uniform over the cluster
   __syncthreads();
-  slice_smem_column(bh, bl, D, (int64_t)q * ncol + col, 16, KB, red, Us, eu);
+  cluster_slice_column(bh, bl, pt, D, (int64_t)q * ncol + col, 16, KB, KBC, red, &smax, Us, eu);
 }
 
 // M_q = P_l (G + lam0_l I), l = perm[q], from the exact partials of G P_l (A = the rows of G,
@@ -971,41 +1027,51 @@ int oz_pick_split_mnk(int64_t M, int64_t N, int64_t K, int groups, int NT, int c
 
 bool oz_fused_ok(int64_t D) { return (size_t)D * 8 <= 160 * 1024; }
 
+// Cluster geometry of the per-column kernels: CL <= 8 CTAs per column, KBC k-blocks of 32 rows
+// per CTA, one row per thread (up to 512 threads), the CTA's rows in shared memory.
+struct ColGeom {
+  int KB, CL, KBC, threads;
+  size_t smem;
+};
+inline ColGeom col_geom(int64_t D) {
+  ColGeom g;
+  g.KB = oz_kb(D);
+  g.CL = std::min(8, std::max(1, g.KB));
+  g.KBC = (g.KB + g.CL - 1) / g.CL;
+  g.threads = std::min(g.KBC * OZ_BK, OZ_COL_THREADS_MAX);
+  g.smem = (size_t)g.KBC * OZ_BK * 2 * sizeof(float);
+  return g;
+}
+
 cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
                             const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
                             const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
                             __nv_bfloat16* Rs, int* er, cudaStream_t st) {
   const int NTL = (int)((nnew + NT - 1) / NT);
-  const int smem = (int)(D * 8);
-  CK(same_carveout(k_make_R_oz_slice));
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_make_R_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  return launch_pdl(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT)), dim3(OZ_FUSED_THREADS), smem, st,
-                    Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau, lam0, gs, NT, NTL, oz_kb(D), Rs,
-                    er);
+  const ColGeom cg_ = col_geom(D);
+  return launch_pdl_cluster(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT * cg_.CL)), dim3(cg_.threads),
+                            cg_.smem, cg_.CL, st, Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau,
+                            lam0, gs, NT, NTL, cg_.KB, cg_.KBC, Rs, er);
 }
 
 cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
                             const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
                             CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
                             int* eu, cudaStream_t st) {
-  const int smem = (int)(D * 8);
-  CK(same_carveout(k_update_oz_slice));
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  return launch_pdl(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Zhi,
-                    Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut, perm, gs, live_next, NTn, oz_kb(D),
-                    Us, eu);
+  const ColGeom cg_ = col_geom(D);
+  return launch_pdl_cluster(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
+                            cg_.smem, cg_.CL, st, Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut,
+                            perm, gs, live_next, NTn, cg_.KB, cg_.KBC, Us, eu);
 }
 
 cudaError_t oz_update_mw_slice(const long long* Phi, const long long* Plo, int S, const int* em, const int* ep,
                                int live, int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout, CBuf Ut,
                                const int* perm, const double* tau, const double* lam0, int64_t gs, const int* eu_in,
                                int live_next, __nv_bfloat16* Us, int* eu, cudaStream_t st) {
-  const int smem = (int)(D * 8);
-  CK(same_carveout(k_update_mw_slice));
-  if (smem > 48 * 1024) CK(cudaFuncSetAttribute(k_update_mw_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  return launch_pdl(k_update_mw_slice, dim3((unsigned)((int64_t)live * ncol)), dim3(OZ_FUSED_THREADS), smem, st, Phi, Plo,
-                    S, em, ep, (int64_t)oz_rows_exps(D), live, ncol, D, K, Uin, Uout, Ut, perm, tau, lam0, gs, eu_in,
-                    live_next, oz_kb(D), Us, eu);
+  const ColGeom cg_ = col_geom(D);
+  return launch_pdl_cluster(k_update_mw_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
+                            cg_.smem, cg_.CL, st, Phi, Plo, S, em, ep, (int64_t)oz_rows_exps(D), live, ncol, D, K, Uin,
+                            Uout, Ut, perm, tau, lam0, gs, eu_in, live_next, cg_.KB, cg_.KBC, Us, eu);
 }
 
 cudaError_t oz_make_M(const long long* hi, const long long* lo, int S, int64_t D, int T, const int* eg, const int* epc,
