@@ -356,6 +356,12 @@ ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
   CallStream cs(nullptr);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
+  for (cudaStream_t* sp : {&p->side, &p->fac})
+    if (*sp) {
+      cudaStreamSynchronize(*sp);
+      cudaStreamDestroy(*sp);
+      *sp = nullptr;
+    }
   prob_free_basis(p);
   free_list(p, p->owned);
   delete p;
@@ -551,7 +557,9 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   prob_free_basis(p);
   p->plan = pl;
   if (!pl.auto_rho) finalize_plan(p, nullptr);
-  cudaEvent_t ev[5];
+  // phases: factor ev[0] -> ev[1] (factor stream); Gram + rhs ev[5] -> ev[2] (side stream,
+  // overlapping the factor); recursion ev[6] -> ev[3] (caller's stream, after both joins)
+  cudaEvent_t ev[7];
   for (auto& x : ev) cudaEventCreate(&x);
   ihsbin_status s;
   {
@@ -559,8 +567,10 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
     // persistent members (Pinv, G, Ut, W) are taken out of the scratch scope by the device code
     e = build_basis_device(p, st, ev);
     if (e != cudaSuccess) {
-      for (auto& x : ev) cudaEventDestroy(x);
       cudaStreamSynchronize(st);
+      if (p->side) cudaStreamSynchronize(p->side);
+      if (p->fac) cudaStreamSynchronize(p->fac);
+      for (auto& x : ev) cudaEventDestroy(x);
       prob_free_basis(p);
       return cuda_fail(e, "build_basis");
     }
@@ -568,8 +578,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   }
   float t01 = 0, t12 = 0, t23 = 0;
   cudaEventElapsedTime(&t01, ev[0], ev[1]);
-  cudaEventElapsedTime(&t12, ev[1], ev[2]);
-  cudaEventElapsedTime(&t23, ev[2], ev[3]);
+  cudaEventElapsedTime(&t12, ev[5], ev[2]);
+  cudaEventElapsedTime(&t23, ev[6], ev[3]);
   p->phase_ms[1] = t01;
   p->phase_ms[2] = t12;
   p->phase_ms[3] = t23;

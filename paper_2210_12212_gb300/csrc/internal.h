@@ -78,6 +78,8 @@ struct KStat {
 
 struct ihsbin_problem {
   ihsbin_ctx* ctx = nullptr;
+  cudaStream_t side = nullptr;  // build_basis: the Gram's stream, overlapping ...
+  cudaStream_t fac = nullptr;   // ... the factorization's stream
   int64_t n = 0, d = 0, K = 0;
   bool dual = false;
   ihsbin::Tall A;

@@ -1898,51 +1898,75 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaMemcpyAsync(lam0_dev, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
 
-  // a2: factor + inverse of the shifted sketched Hessians
-  CK(cudaEventRecord(ev[0], st));
-  CBuf H = cb((size_t)L * D * D);
-  CBuf Wm = cb((size_t)L * D * D);
-  const int64_t nblk = (D + NB - 1) / NB;
-  CBuf dinv = cb((size_t)L * nblk * NB * NB);
-  p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
-  CK(err);
-  CK(factor_and_invert<Mode>(p, H, Wm, dinv, lam0_dev, st));
-  if (pl.auto_rho) {
-    double* tr_dev = nullptr;
-    CK(prob_alloc(p, L * sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH));
-    k_trace<Mode><<<L, 256, 0, st>>>(p->Pinv, D, tr_dev);
-    CK(cudaGetLastError());
-    std::vector<double> trP(L);
-    CK(cudaMemcpyAsync(trP.data(), tr_dev, L * sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    finalize_plan(p, trP.data());
-    CK(cudaMemcpyAsync(tau_dev, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.k[a] > pl.k[b]; });
-    CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
-  }
-  CK(cudaEventRecord(ev[1], st));
-
-  // a3: Gram (product mode GRAM) and right-hand side
-  CBuf c = cb((size_t)D * K);
-  CK(err);
+  // a3: Gram (product mode GRAM) and right-hand side.  They do not depend on a2 (the factors of
+  // the sketched Hessian), so they run on the problem's side stream, forked here and joined
+  // before the recursion: their tensor-core work fills the SMs that the factorization's small
+  // launches leave idle.  Allocations in this section are ordered on the side stream.
+  if (!p->side) CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  cudaStream_t s2 = p->side;
+  CK(cudaEventRecord(ev[5], st));
+  CK(cudaStreamWaitEvent(s2, ev[5], 0));
   const bool csr = A.layout == IHSBIN_CSR;
-  if (pl.product == IHSBIN_PRODUCT_GRAM) {
-    p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
+  CBuf c{};
+  {
+    CallStream side_alloc(s2);
+    c = cb((size_t)D * K);
     CK(err);
-    if (csr) CK(csr_gram(p, cm, st));
-    else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, st));
-    else CK((gram_dense<Mode, ET>(p, st)));
+    if (pl.product == IHSBIN_PRODUCT_GRAM) {
+      p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
+      CK(err);
+      if (csr) CK(csr_gram(p, cm, s2));
+      else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, s2));
+      else CK((gram_dense<Mode, ET>(p, s2)));
+    }
+    if (csr && !p->dual) {
+      CK(csr_rhs(p, cm, c, s2));
+    } else if (p->dual) {
+      KTimer kt(p, K_RHS, s2, 0, (double)D * K * 16);
+      k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, s2>>>(p->B, D, K, c);
+      CK(cudaGetLastError());
+    } else {
+      CK((rhs_dense<Mode, ET>(p, c, s2)));
+    }
+    CK(cudaEventRecord(ev[2], s2));
   }
-  if (csr && !p->dual) {
-    CK(csr_rhs(p, cm, c, st));
-  } else if (p->dual) {
-    KTimer kt(p, K_RHS, st, 0, (double)D * K * 16);
-    k_copy_B_colmajor<Mode><<<nblocks(D * K, 256), 256, 0, st>>>(p->B, D, K, c);
-    CK(cudaGetLastError());
-  } else {
-    CK((rhs_dense<Mode, ET>(p, c, st)));
+
+  // a2: factor + inverse of the shifted sketched Hessians, on the problem's second internal
+  // stream (forked with the Gram's, joined before the recursion).  Allocations in this section
+  // are ordered on that stream.
+  if (!p->fac) CK(cudaStreamCreateWithFlags(&p->fac, cudaStreamNonBlocking));
+  cudaStream_t sf = p->fac;
+  CK(cudaStreamWaitEvent(sf, ev[5], 0));
+  {
+    CallStream fac_alloc(sf);
+    CK(cudaEventRecord(ev[0], sf));
+    CBuf H = cb((size_t)L * D * D);
+    CBuf Wm = cb((size_t)L * D * D);
+    const int64_t nblk = (D + NB - 1) / NB;
+    CBuf dinv = cb((size_t)L * nblk * NB * NB);
+    p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
+    CK(err);
+    CK(factor_and_invert<Mode>(p, H, Wm, dinv, lam0_dev, sf));
+    if (pl.auto_rho) {
+      double* tr_dev = nullptr;
+      CK(prob_alloc(p, L * sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH));
+      k_trace<Mode><<<L, 256, 0, sf>>>(p->Pinv, D, tr_dev);
+      CK(cudaGetLastError());
+      std::vector<double> trP(L);
+      CK(cudaMemcpyAsync(trP.data(), tr_dev, L * sizeof(double), cudaMemcpyDeviceToHost, sf));
+      CK(cudaStreamSynchronize(sf));
+      finalize_plan(p, trP.data());
+      CK(cudaMemcpyAsync(tau_dev, pl.tau.data(), L * sizeof(double), cudaMemcpyHostToDevice, sf));
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pl.k[a] > pl.k[b]; });
+      CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, sf));
+    }
+    CK(cudaEventRecord(ev[1], sf));
   }
-  CK(cudaEventRecord(ev[2], st));
+
+  // join both forks before the recursion
+  CK(cudaStreamWaitEvent(st, ev[1], 0));
+  CK(cudaStreamWaitEvent(st, ev[2], 0));
+  CK(cudaEventRecord(ev[6], st));
 
   // a4: the recursion
   const size_t per = (size_t)pl.jc * K * D;

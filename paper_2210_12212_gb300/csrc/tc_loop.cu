@@ -460,23 +460,23 @@ __global__ void __launch_bounds__(128) k_oz_slice_cols(CBuf X, int64_t D, int64_
 }
 
 // Vectors = the columns of row-major float-float matrices (group stride gs, row stride ld), K rows
-// each: CTA (32 x 8 threads) per 32 columns; a column's maximum from its 8 threads, then thread
-// (x, y) cuts rows 8c .. 8c+7 (c = y, y + 8, ...) of column x (loads coalesced across x).
+// each: CTA (32 x 32 threads) per 32 columns; a column's maximum from its 32 threads, then thread
+// (x, y) cuts rows 8c .. 8c+7 (c = y, y + 32, ...) of column x (loads coalesced across x).
 // Layout as k_oz_slice_cols with tile height TH.
-__global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int64_t gs,
+__global__ void __launch_bounds__(1024) k_oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int64_t gs,
                                                           int TH, int NTL, int KB, __nv_bfloat16* out, int* e) {
   pdl_wait();  // launched with programmatic serialization
   pdl_trigger();
-  __shared__ float red[8][33];
+  __shared__ float red[32][33];
   __shared__ int ex[32];
-  const int x = threadIdx.x, y = threadIdx.y, g = blockIdx.y;
+  const int x = threadIdx.x, y = threadIdx.y, g = blockIdx.y, ny = blockDim.y;  // 32 columns x ny row lanes
   const int64_t v = (int64_t)blockIdx.x * 32 + x;
   const bool valid = v < nvec;
   const float* xh = (const float*)X.p0 + (int64_t)g * gs;
   const float* xl = (const float*)X.p1 + (int64_t)g * gs;
   float m = 0.f;
   if (valid)
-    for (int64_t k = y; k < K; k += 8) {
+    for (int64_t k = y; k < K; k += ny) {
       const float a = fabsf(xh[k * ld + v]);
       m = (a <= 3.402823466e38f) ? fmaxf(m, a) : __int_as_float(0x7f800000);
     }
@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, in
   __syncthreads();
   if (y == 0) {
     float mm = red[0][x];
-    for (int q = 1; q < 8; ++q) mm = fmaxf(mm, red[q][x]);
+    for (int q = 1; q < ny; ++q) mm = fmaxf(mm, red[q][x]);
     ex[x] = oz_exp(mm);
     if (v < (int64_t)NTL * TH) e[(int64_t)g * NTL * TH + v] = ex[x];
   }
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(256) k_oz_slice_matcols(CBuf X, int64_t ld, in
   const bool live = valid && ev != OZ_NONFINITE;
   const int tile = (int)(v / TH), nl = (int)(v - (int64_t)tile * TH);
   const int64_t bblk = (int64_t)TH * OZ_BK;
-  for (int c = y; c < KB * 4; c += 8) {
+  for (int c = y; c < KB * 4; c += ny) {
     const int kb = c >> 2, kc = c & 3;
     float h[8], l[8];
 #pragma unroll
@@ -1100,7 +1100,7 @@ size_t oz_vec_exps(int64_t nvec, int TH) { return (size_t)((nvec + TH - 1) / TH)
 cudaError_t oz_slice_matcols(CBuf X, int64_t ld, int64_t K, int64_t nvec, int groups, int64_t gs, int TH,
                              __nv_bfloat16* out, int* e, cudaStream_t st) {
   const int NTL = (int)((nvec + TH - 1) / TH);
-  dim3 grid((unsigned)((NTL * TH + 31) / 32), (unsigned)groups), blk(32, 8);
+  dim3 grid((unsigned)((NTL * TH + 31) / 32), (unsigned)groups), blk(32, 32);
   return launch_pdl(k_oz_slice_matcols, grid, blk, 0, st, X, ld, K, nvec, gs, TH, NTL, (int)((K + OZ_BK - 1) / OZ_BK), out,
                     e);
 }
