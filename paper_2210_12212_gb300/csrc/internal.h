@@ -168,7 +168,8 @@ cudaError_t csr_gram(ihsbin_problem* p, int compute, cudaStream_t st);
 // Dense FP32/BF16 Gram on the tensor cores from exact integer slices (tc_gram.cu)
 constexpr int kGramSlices = 6;     // BF16 slices per entry
 constexpr int kGramMaxWeight = 6;  // slice pairs (s, t) kept: s + t <= kGramMaxWeight
-cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st);
+// reserve_sms > 0: the tensor-core launches leave that many SMs free (for work on other streams)
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms = 0);
 // G_S = (S A_hat)^T (S A_hat) from the FP64 sketch on the tensor cores (7 slices, FP64-class)
 cudaError_t sketch_gram_slices(ihsbin_problem* p, cudaStream_t st);
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);

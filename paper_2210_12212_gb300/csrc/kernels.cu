@@ -1898,6 +1898,8 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaMemcpyAsync(lam0_dev, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
 
+  // SMs the Gram's tensor-core launches leave to the factorization running beside them
+  constexpr int GRAM_RESERVE_SMS = 40;
   // a3: Gram (product mode GRAM) and right-hand side.  They do not depend on a2 (the factors of
   // the sketched Hessian), so they run on the problem's side stream, forked here and joined
   // before the recursion: their tensor-core work fills the SMs that the factorization's small
@@ -1916,7 +1918,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
       p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
       CK(err);
       if (csr) CK(csr_gram(p, cm, s2));
-      else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, s2));
+      else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, s2, GRAM_RESERVE_SMS));
       else CK((gram_dense<Mode, ET>(p, s2)));
     }
     if (csr && !p->dual) {

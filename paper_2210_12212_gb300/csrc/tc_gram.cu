@@ -164,7 +164,7 @@ __global__ void k_slice(const void* A, int64_t ld, int64_t N, int64_t D, const u
 }
 
 __global__ void __launch_bounds__(SL_THREADS, 1)
-    k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, SlicePlan pl, int* __restrict__ out, int* status) {
+    k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, SlicePlan pl, int* __restrict__ out, int* status, int item0) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[SL_STAGES], empty[SL_STAGES], tfull[2], tempty[2], drained;
   __shared__ uint32_t tmem_base;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // work item -> pair, tile (I, J), row range
-  const int item = blockIdx.x;
+  const int item = item0 + blockIdx.x;
   int p = 0;
   while (p + 1 < pl.np && pl.base[p + 1] <= item) ++p;
   const int s = pl.ps[p], t = pl.pt[p];
@@ -387,7 +387,7 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
 // ns slices per entry, pairs s + t <= wmax.
 template <class Mode, int ET>
 cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int64_t N, int64_t D, int ns, int wmax,
-                              CBuf G, int cat_slice, int cat_tc, int cat_combine, cudaStream_t st) {
+                              CBuf G, int cat_slice, int cat_tc, int cat_combine, cudaStream_t st, int max_ctas = 0) {
   struct {
     const void* A;
     int64_t ld;
@@ -418,11 +418,18 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
     // algorithmic BF16 work of the slice products (unpadded): 2 N per output entry and pair
     double fl = 0;
     for (int q = 0; q < pl.np; ++q) fl += 2.0 * N * (pl.ps[q] == pl.pt[q] ? D * (D + 1) / 2.0 : (double)D * D);
-    KTimer kt(p, cat_tc, st, fl, (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536);
+    const double by = (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536;
     const int smem = SL_STAGES * SL_STAGE_BYTES;
     CK(cudaFuncSetAttribute(k_gram_slices_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_gram_slices_tc<<<(unsigned)items, SL_THREADS, smem, st>>>(S, pl, out, p->status);
-    CK(cudaGetLastError());
+    // max_ctas > 0: launches of at most max_ctas CTAs (one wave each), so that the SMs beyond them
+    // stay free for work on other streams
+    const int chunk = max_ctas > 0 ? std::min(items, max_ctas) : items;
+    for (int i0 = 0; i0 < items; i0 += chunk) {
+      const int n = std::min(chunk, items - i0);
+      KTimer kt(p, cat_tc, st, fl * n / items, by * n / items);
+      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, pl, out, p->status, i0);
+      CK(cudaGetLastError());
+    }
   }
   {
     KTimer kt(p, cat_combine, st, 0, (double)items * 65536 + (double)D * D * 8);
@@ -435,17 +442,23 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
 
 }  // namespace
 
-cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st) {
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms) {
   const Tall& A = p->A;
   const int et = A.elem;
   const int cs = K_GRAM_SLICE, ct = K_GRAM_TC, cc = K_GRAM_COMBINE;
+  int mc = 0;
+  if (reserve_sms > 0) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+      mc = std::max(1, sms - reserve_sms);
+  }
   if (compute == IHSBIN_COMPUTE_F64)
     return et == ELEM_F32
-               ? gram_slices_typed<F64, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st)
-               : gram_slices_typed<F64, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st);
+               ? gram_slices_typed<F64, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc)
+               : gram_slices_typed<F64, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc);
   return et == ELEM_F32
-             ? gram_slices_typed<DD, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st)
-             : gram_slices_typed<DD, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st);
+             ? gram_slices_typed<DD, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc)
+             : gram_slices_typed<DD, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc);
 }
 
 // G_S = (S A_hat)^T (S A_hat) of the FP64 sketch: seven slices (55 bits) and pairs s + t <= 7, so
