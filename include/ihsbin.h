@@ -237,7 +237,12 @@ IHSBIN_API ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* 
  *   u_00 = P c;  for i = 1..k_l-1:  u_i = -lam0 P u_{i-1},
  *   u_j <- u_j - P(tau (A^T A u_j + lam0 u_j) + lam0 u_{j-1})  (j = i-1..1),
  *   u_0 <- u_0 - P tau (A^T A u_0 + lam0 u_0),  utilde_j += u_j.
- * The bases stay resident on the device until the problem is destroyed. */
+ * The bases stay resident on the device until the problem is destroyed.
+ * Ordered after earlier work on `stream` and synchronous: it returns when the basis
+ * is complete.  Internally the call forks two streams of the problem (created on its
+ * first build, destroyed with the problem) from `stream` -- the Gram and right-hand
+ * side on one, the factorization on the other -- and joins both back into `stream`
+ * before the recursion; nothing is left running on them when the call returns. */
 IHSBIN_API ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* desc, void* stream);
 
 /* Copy the Gram G = A_hat^T A_hat (D x D, row-major) built by the last
