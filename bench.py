@@ -108,7 +108,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -444,11 +444,12 @@ def main():
         p.set_timing(False)
         return out
 
+    # clocks sampled every 50 ms through both timed regions
     with ClockSampler(local) as clk:
         elapsed_ms, lat, stats_clean, phases = timed_steps(False)
-    # ---- the same K steps again with CUDA events around every launch, on the launching stream:
-    # the per-kernel device times of the roofline and of the kernel table
-    inst_ms, _, stats, _ = timed_steps(True)
+        # ---- the same K steps again with CUDA events around every launch, on the launching stream:
+        # the per-kernel device times of the roofline and of the kernel table
+        inst_ms, _, stats, _ = timed_steps(True)
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
