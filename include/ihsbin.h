@@ -64,7 +64,8 @@ typedef enum { IHSBIN_F64 = 0, IHSBIN_F32 = 1, IHSBIN_BF16 = 2 } ihsbin_dtype;
  *  IHSBIN_COMPUTE_F64  IEEE double throughout;
  *  IHSBIN_COMPUTE_F32X2 float-float pairs (about 44 significant bits) built from
  *                      error-free transformations on the FP32 pipe; the
- *                      sketch itself is applied in FP64 (Gaussian, SRHT) or
+ *                      sketch itself is applied in FP64 (Gaussian), in exact
+ *                      int64 fixed point (the SRHT's Hadamard transform) or
  *                      with FP64 accumulation (CountSketch). */
 typedef enum { IHSBIN_COMPUTE_F64 = 0, IHSBIN_COMPUTE_F32X2 = 1 } ihsbin_compute;
 
@@ -213,10 +214,11 @@ IHSBIN_API ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p);
 
 /* Step a1 of the hot path: S A_hat (m x D) for the sketch of Section 3 and
  * its Gram (S A_hat)^T (S A_hat), where A_hat = A (over-determined) or A^T
- * (under-determined).  S A_hat is formed in FP64 (exact for the SRHT of FP32
- * data; FP64 accumulation otherwise); its Gram is accumulated in FP64 for FP64
- * data and in float-float (about 44 significant bits) for FP32/BF16 data.
- * Re-sketching an already sketched problem discards the basis. */
+ * (under-determined).  S A_hat is returned in FP64.  The SRHT converts each column of
+ * D A_hat once to int64 fixed point at 2^-(62 - log2 N_pad) of the column's largest
+ * magnitude and then adds exactly; the other sketches accumulate in FP64.  Its Gram is
+ * formed on the tensor cores from seven exact BF16 slices of S A_hat and combined in FP64
+ * (FP64-class accuracy).  Re-sketching an already sketched problem discards the basis. */
 IHSBIN_API ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream);
 
 /* Bit-exact export of the sketch's integer draws, for tests.
