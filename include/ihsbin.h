@@ -218,7 +218,10 @@ IHSBIN_API ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p);
  * D A_hat once to int64 fixed point at 2^-(62 - log2 N_pad) of the column's largest
  * magnitude and then adds exactly; the other sketches accumulate in FP64.  Its Gram is
  * formed on the tensor cores from seven exact BF16 slices of S A_hat and combined in FP64
- * (FP64-class accuracy).  Re-sketching an already sketched problem discards the basis. */
+ * (FP64-class accuracy).  Re-sketching an already sketched problem discards the basis.
+ * Limits: the SRHT needs dense A, m <= N_pad and N_pad <= 2^24 rows (beyond that its
+ * launches exceed the grid limits and the call fails with IHSBIN_ERR_CUDA); CountSketch and
+ * Gaussian sketches take any row count. */
 IHSBIN_API ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream);
 
 /* Bit-exact export of the sketch's integer draws, for tests.
