@@ -337,6 +337,8 @@ def note(msg):
 
 def main():
     args = parse()
+    if args.impl == "reference" and int(os.environ.get("RANK", "0")) != 0:
+        return  # the reference arm runs on rank 0 alone; the other ranks exit without work
     if args.config == "c5":
         serving_arm(args)
         return
