@@ -102,6 +102,17 @@ typedef struct {
   int on_device;
 } ihsbin_matrix;
 
+/* How the Gaussian sketch S A_hat is contracted (Section 3, Gaussian sketch):
+ *  AUTO   : TENSOR for BF16 entries of dense BF16 data, FMA otherwise;
+ *  TENSOR : BF16 entries and dense BF16 data only (else IHSBIN_ERR_UNSUPPORTED).  S is drawn
+ *           once per call into the tensor cores' shared-memory image (every BF16 entry equal to
+ *           the FP64 value rounded FP64 -> FP32 -> BF16), and S A_hat runs as a BF16 tcgen05
+ *           contraction: products exact, accumulated in FP32 over at most a k-split of the rows
+ *           (a few thousand products per entry), the k-splits added in FP64;
+ *  FMA    : CUDA-core contraction, FP64 accumulation (FP64 entries) or float-float (BF16 entries
+ *           of FP32/BF16 data). */
+typedef enum { IHSBIN_APPLY_AUTO = 0, IHSBIN_APPLY_TENSOR = 1, IHSBIN_APPLY_FMA = 2 } ihsbin_sketch_apply;
+
 typedef struct {
   ihsbin_sketch_kind kind;
   int64_t m;     /* sketch rows (m % s == 0 for CountSketch/SJLT)           */
@@ -109,8 +120,8 @@ typedef struct {
   uint64_t seed; /* Philox4x32-10 key                                       */
   ihsbin_dtype entries; /* Gaussian only: IHSBIN_F64 (default) keeps the FP64 entries z/sqrt(m);
                          * IHSBIN_BF16 rounds them (FP64 -> FP32 -> BF16, to nearest even), and with
-                         * FP32/BF16 data every product of the sketch is then exact in FP32 and is
-                         * accumulated in float-float (about 8x the FP64 rate on GB300) */
+                         * FP32/BF16 data every product of the sketch is then exact in FP32 */
+  ihsbin_sketch_apply apply; /* Gaussian only: the contraction (see ihsbin_sketch_apply) */
 } ihsbin_sketch_desc;
 
 /* Interval plan and iteration parameters (Section 4.2, Theorem 4).
@@ -236,6 +247,14 @@ IHSBIN_API ihsbin_status ihsbin_sketch_export(ihsbin_problem* p, int64_t* idx, i
  * (either may be NULL), for tests. */
 IHSBIN_API ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* SA, double* GS);
 
+/* BF16 bits of the entries S[i][j], row0 <= i < row0 + nrows, col0 <= j < col0 + ncols, of a
+ * problem sketched with the Gaussian sketch with BF16 entries (Section 3), drawn by the same
+ * device code the tensor-core contraction uses; written row-major to the host array `out`
+ * (nrows * ncols values), for tests.  IHSBIN_ERR_STATE when the problem is not sketched that
+ * way, IHSBIN_ERR_INVALID_ARG for a window outside the m x N sketch. */
+IHSBIN_API ihsbin_status ihsbin_sketch_entries_export(ihsbin_problem* p, int64_t row0, int64_t nrows, int64_t col0,
+                                                      int64_t ncols, uint16_t* out);
+
 /* Steps a2-a4: per interval, the factor of (S A_hat)^T S A_hat + lam0_l I and
  * its explicit inverse P_l; the right-hand side c = A^T B (dual: c = B); then
  * Algorithm 2 / 5 (Proposition 1's recursion, re-centred at lam0_l):
@@ -337,17 +356,24 @@ IHSBIN_API ihsbin_status ihsbin_adaptive_sketch(ihsbin_problem* p, const ihsbin_
  * calls: [0] sketch, [1] factor+inverse, [2] Gram+rhs, [3] basis loop, [4] eval. */
 IHSBIN_API ihsbin_status ihsbin_phase_times(ihsbin_problem* p, float* ms5);
 
-/* Per-kernel accounting, for measurement.  Every launch is counted with its
- * algorithmic flops (2 per multiply-add of the contraction it performs, FP64
- * or float-float) and algorithmic HBM bytes; when timing is enabled each launch
- * is also bracketed by CUDA events on the stream it runs on and its device
- * time is added at the call's synchronisation point.  Categories 0 ..
- * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage). */
-#define IHSBIN_KCAT_COUNT 32
+/* Per-kernel accounting, for measurement.  Every launch is counted with the
+ * method's algorithmic work: flops = 2 per multiply-add of the contraction the
+ * paper's step performs (FP64 class), bytes = one pass over the step's operands
+ * at 8 bytes per FP64-class entry (the Gram G once per recursion step, each live
+ * P_l once, the data at its storage width).  When timing is enabled each launch
+ * is also bracketed by CUDA events on the stream it runs on and its device time
+ * is added at the call's synchronisation point.  Categories 0 ..
+ * IHSBIN_KCAT_COUNT-1 (names returned in *name, static storage; categories not
+ * in use report no launches and the name "unused"). */
+#define IHSBIN_KCAT_COUNT 40
 IHSBIN_API ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable);
 IHSBIN_API ihsbin_status ihsbin_reset_stats(ihsbin_problem* p);
 IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms,
                                              double* flops, double* bytes, const char** name);
+/* The work the same launches execute: for the exact-slice tensor-core products the
+ * BF16 flops of every kept slice pair and the bytes of the slice images they stream
+ * (12 bytes per FP64-class entry), for every other kernel the algorithmic figures. */
+IHSBIN_API ihsbin_status ihsbin_kernel_exec(ihsbin_problem* p, int32_t cat, double* xflops, double* xbytes);
 
 /* ---- Serving: a continuous-batching request loop (the library's runtime; the
  * paper solves one problem at a time).  `slots` worker threads each own a CUDA

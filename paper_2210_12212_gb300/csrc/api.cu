@@ -141,11 +141,14 @@ CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaErr
   return b;
 }
 
-KTimer::KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes) : p(pp), cat(c), st(s) {
+KTimer::KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes, double xflops, double xbytes)
+    : p(pp), cat(c), st(s) {
   KStat& k = p->kstat[c];
   k.launches += 1;
   k.flops += flops;
   k.bytes += bytes;
+  k.xflops += xflops >= 0 ? xflops : flops;
+  k.xbytes += xbytes >= 0 ? xbytes : bytes;
   if (!p->timing) return;
   while (p->ev_pool.size() < p->ev_used + 2) {
     cudaEvent_t e;
@@ -375,6 +378,8 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
   if (sk->m <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: m must be positive");
   if (sk->entries != IHSBIN_F64 && sk->entries != IHSBIN_BF16)
     return fail(IHSBIN_ERR_INVALID_ARG, "sketch: entries must be IHSBIN_F64 or IHSBIN_BF16");
+  if (sk->apply != IHSBIN_APPLY_AUTO && sk->apply != IHSBIN_APPLY_TENSOR && sk->apply != IHSBIN_APPLY_FMA)
+    return fail(IHSBIN_ERR_INVALID_ARG, "sketch: unknown apply selector");
   int64_t Np = 1;
   while (Np < N) Np <<= 1;
   if (sk->kind == IHSBIN_SK_COUNTSKETCH) {
@@ -384,6 +389,8 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
     if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: SRHT needs dense A (use CountSketch for CSR)");
   } else if (sk->kind == IHSBIN_SK_GAUSSIAN) {
     if (p->A.layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: Gaussian needs dense A");
+    if (sk->apply == IHSBIN_APPLY_TENSOR && !(p->A.elem == ELEM_BF16 && sk->entries == IHSBIN_BF16))
+      return fail(IHSBIN_ERR_UNSUPPORTED, "sketch: the tensor-core Gaussian sketch needs BF16 entries and BF16 data");
   } else {
     return fail(IHSBIN_ERR_INVALID_ARG, "sketch: unknown kind");
   }
@@ -473,6 +480,28 @@ ihsbin_status ihsbin_sketch_matrix_export(ihsbin_problem* p, double* SA, double*
   if (GS && cudaMemcpy(GS, p->GS, (size_t)D * D * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return fail(IHSBIN_ERR_CUDA, "sketch_matrix_export: copy failed");
   return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_sketch_entries_export(ihsbin_problem* p, int64_t row0, int64_t nrows, int64_t col0,
+                                           int64_t ncols, uint16_t* out) {
+  if (!p || !out) return fail(IHSBIN_ERR_INVALID_ARG, "sketch_entries_export: NULL argument");
+  if (!p->sketched || p->sk.kind != IHSBIN_SK_GAUSSIAN || p->sk.entries != IHSBIN_BF16)
+    return fail(IHSBIN_ERR_STATE, "sketch_entries_export: not sketched with BF16 Gaussian entries");
+  if (row0 < 0 || col0 < 0 || nrows <= 0 || ncols <= 0 || row0 + nrows > p->sk.m || col0 + ncols > p->A.N)
+    return fail(IHSBIN_ERR_INVALID_ARG, "sketch_entries_export: window outside the sketch");
+  cudaError_t e = cudaSetDevice(p->ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "sketch_entries_export");
+  cudaStream_t st = cudaStreamPerThread;
+  CallStream cs(st);
+  ScratchScope scratch(p);
+  uint16_t* dev = nullptr;
+  if ((e = prob_alloc(p, (size_t)nrows * ncols * 2, (void**)&dev, SCOPE_SCRATCH)) != cudaSuccess)
+    return cuda_fail(e, "sketch_entries_export");
+  if ((e = gaussian_entries_bf16(p, row0, nrows, col0, ncols, dev, st)) != cudaSuccess)
+    return cuda_fail(e, "sketch_entries_export");
+  if ((e = cudaMemcpyAsync(out, dev, (size_t)nrows * ncols * 2, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "sketch_entries_export");
+  return check_status(p, st, "sketch_entries_export");
 }
 
 ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, void* stream) {
@@ -909,7 +938,7 @@ static const char* kcat_names[K_NCAT] = {
     "trtri", "inverse_syrk", "gram", "rhs", "loop_gram_product", "loop_precond_update", "dual_map",
     "eval_coef", "eval", "sparse", "gram_slice", "gram_tc_mma", "gram_combine", "loop_slice", "loop_gram_tc",
     "loop_precond_tc", "factor_slice", "inverse_tc", "trtri_tc", "factor_syrk_tc", "loss_slice", "loss_image_tc",
-    "loss_image", "loss_resid", "adaptive_step"};
+    "loss_image", "loss_resid", "adaptive_step", "sketch_image", "sketch_tc", "sketch_reduce"};
 
 ihsbin_status ihsbin_set_timing(ihsbin_problem* p, int enable) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "set_timing: NULL");
@@ -926,13 +955,24 @@ ihsbin_status ihsbin_reset_stats(ihsbin_problem* p) {
 ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int64_t* launches, double* ms, double* flops,
                                   double* bytes, const char** name) {
   if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_stats: NULL");
-  if (cat < 0 || cat >= K_NCAT) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_stats: category out of range");
-  const KStat& k = p->kstat[cat];
+  if (cat < 0 || cat >= IHSBIN_KCAT_COUNT) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_stats: category out of range");
+  static const KStat unused{};
+  const KStat& k = cat < K_NCAT ? p->kstat[cat] : unused;  // categories not in use report no launches
   if (launches) *launches = k.launches;
   if (ms) *ms = k.ms;
   if (flops) *flops = k.flops;
   if (bytes) *bytes = k.bytes;
-  if (name) *name = kcat_names[cat];
+  if (name) *name = cat < K_NCAT ? kcat_names[cat] : "unused";
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_kernel_exec(ihsbin_problem* p, int32_t cat, double* xflops, double* xbytes) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_exec: NULL");
+  if (cat < 0 || cat >= IHSBIN_KCAT_COUNT) return fail(IHSBIN_ERR_INVALID_ARG, "kernel_exec: category out of range");
+  static const KStat unused{};
+  const KStat& k = cat < K_NCAT ? p->kstat[cat] : unused;
+  if (xflops) *xflops = k.xflops;
+  if (xbytes) *xbytes = k.xbytes;
   return IHSBIN_OK;
 }
 

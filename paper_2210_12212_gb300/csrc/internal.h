@@ -67,11 +67,13 @@ enum KCat : int {
   K_SKETCH_DRAW = 0, K_SKETCH_APPLY, K_SKETCH_GRAM, K_FACTOR_SHIFT, K_FACTOR_POTRF, K_FACTOR_TRSM,
   K_FACTOR_SYRK, K_TRTRI, K_INVERSE, K_GRAM, K_RHS, K_LOOP_Y, K_LOOP_P, K_DUAL_MAP, K_EVAL_COEF, K_EVAL,
   K_SPARSE, K_GRAM_SLICE, K_GRAM_TC, K_GRAM_COMBINE, K_LOOP_SLICE, K_LOOP_Y_TC, K_LOOP_P_TC, K_INVERSE_SLICE,
-  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_LOSS_SLICE, K_LOSS_TC, K_LOSS_IMAGE, K_LOSS_RESID, K_ADAPTIVE, K_NCAT
+  K_INVERSE_TC, K_TRTRI_TC, K_SYRK_TC, K_LOSS_SLICE, K_LOSS_TC, K_LOSS_IMAGE, K_LOSS_RESID, K_ADAPTIVE,
+  K_SKETCH_IMAGE, K_SKETCH_TC, K_SKETCH_REDUCE, K_NCAT
 };
 struct KStat {
   int64_t launches = 0;
-  double ms = 0, flops = 0, bytes = 0;
+  double ms = 0, flops = 0, bytes = 0;  // the method's (algorithmic) work
+  double xflops = 0, xbytes = 0;        // the work the implementation executes (slice products, slice images)
 };
 
 }  // namespace ihsbin
@@ -139,7 +141,9 @@ struct KTimer {
   int cat;
   cudaStream_t st;
   size_t idx = 0;
-  KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes);
+  // flops / bytes: the method's algorithmic work; xflops / xbytes (< 0: the same) what the launch executes
+  KTimer(ihsbin_problem* pp, int c, cudaStream_t s, double flops, double bytes, double xflops = -1,
+         double xbytes = -1);
   ~KTimer();
 };
 void resolve_timing(ihsbin_problem* p);
@@ -154,6 +158,12 @@ cudaError_t launch_convert_to_f64(const void* src, int elem, int64_t rows, int64
                                   double* dst, cudaStream_t st);
 
 cudaError_t sketch_gaussian(ihsbin_problem* p, cudaStream_t st);
+// Gaussian sketch with BF16 entries of dense BF16 data on the tensor cores (tc_sketch.cu)
+bool sketch_gaussian_tc_ok(const ihsbin_problem* p);
+cudaError_t sketch_gaussian_tc(ihsbin_problem* p, cudaStream_t st);
+// BF16 bits of the entries [i0, i0 + rows) x [j0, j0 + cols) of the problem's Gaussian sketch (row-major)
+cudaError_t gaussian_entries_bf16(ihsbin_problem* p, int64_t i0, int64_t rows, int64_t j0, int64_t cols,
+                                  uint16_t* out_dev, cudaStream_t st);
 cudaError_t sketch_countsketch(ihsbin_problem* p, cudaStream_t st);
 cudaError_t sketch_srht(ihsbin_problem* p, cudaStream_t st);
 cudaError_t sketch_gram(ihsbin_problem* p, cudaStream_t st);

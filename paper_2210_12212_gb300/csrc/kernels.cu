@@ -366,6 +366,7 @@ static cudaError_t gauss_apply_bf16(ihsbin_problem* p, float* Sbuf, int64_t chun
 cudaError_t sketch_gaussian(ihsbin_problem* p, cudaStream_t st) {
   const Tall& A = p->A;
   if (A.layout != IHSBIN_DENSE_ROWMAJOR) return cudaErrorNotSupported;
+  if (p->sk.apply != IHSBIN_APPLY_FMA && sketch_gaussian_tc_ok(p)) return sketch_gaussian_tc(p, st);
   if (p->sk.entries == IHSBIN_BF16 && A.elem != ELEM_F64) {
     const int64_t m = p->sk.m, N = A.N;
     int64_t chunk = std::max<int64_t>(16, std::min<int64_t>(N, (int64_t)((256ll << 20) / (4 * m))));

@@ -29,6 +29,7 @@ PRODUCT_AUTO, PRODUCT_GRAM, PRODUCT_ASPACE = 0, 1, 2
 
 SKETCH_KIND = {"gaussian": SK_GAUSSIAN, "srht": SK_SRHT, "countsketch": SK_COUNTSKETCH}
 DTYPE = {"f64": F64, "f32": F32, "bf16": BF16}
+SKETCH_APPLY = {"auto": 0, "tensor": 1, "fma": 2}
 COMPUTE = {"f64": COMPUTE_F64, "f32x2": COMPUTE_F32X2}
 PRODUCT = {"auto": PRODUCT_AUTO, "gram": PRODUCT_GRAM, "aspace": PRODUCT_ASPACE}
 GRAM_AUTO, GRAM_SLICES, GRAM_FMA = 0, 1, 2
@@ -50,7 +51,8 @@ class Matrix(C.Structure):
 
 
 class SketchDesc(C.Structure):
-    _fields_ = [("kind", C.c_int), ("m", C.c_int64), ("s", C.c_int32), ("seed", C.c_uint64), ("entries", C.c_int)]
+    _fields_ = [("kind", C.c_int), ("m", C.c_int64), ("s", C.c_int32), ("seed", C.c_uint64), ("entries", C.c_int),
+                ("apply", C.c_int)]
 
 
 class PathDesc(C.Structure):
@@ -91,9 +93,9 @@ EXPORTED = [
     "ihsbin_eval_path", "ihsbin_phase_times", "ihsbin_set_timing", "ihsbin_reset_stats",
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
-    "ihsbin_path_losses", "ihsbin_adaptive_sketch",
+    "ihsbin_path_losses", "ihsbin_adaptive_sketch", "ihsbin_sketch_entries_export", "ihsbin_kernel_exec",
 ]
-KCAT_COUNT = 32
+KCAT_COUNT = 40
 
 
 def load(path: Optional[str] = None):
@@ -116,6 +118,7 @@ def load(path: Optional[str] = None):
         "ihsbin_sketch": [vp, C.POINTER(SketchDesc), vp],
         "ihsbin_sketch_export": [vp, vp, vp, i64, C.POINTER(i64)],
         "ihsbin_sketch_matrix_export": [vp, vp, vp],
+        "ihsbin_sketch_entries_export": [vp, i64, i64, i64, i64, vp],
         "ihsbin_build_basis": [vp, C.POINTER(PathDesc), vp],
         "ihsbin_plan_export": [vp, vp, vp, vp, vp, vp, i32, C.POINTER(i32)],
         "ihsbin_basis_export": [vp, i32, vp, i64, C.POINTER(i64)],
@@ -124,6 +127,7 @@ def load(path: Optional[str] = None):
         "ihsbin_set_timing": [vp, C.c_int],
         "ihsbin_reset_stats": [vp],
         "ihsbin_kernel_stats": [vp, i32, vp, vp, vp, vp, vp],
+        "ihsbin_kernel_exec": [vp, i32, vp, vp],
         "ihsbin_sketch_gram_noalloc": [vp, i64, i64, vp, vp],
         "ihsbin_request_footprint": [C.POINTER(Request), C.POINTER(C.c_uint64)],
         "ihsbin_serve_create": [vp, C.POINTER(ServeConfig), C.POINTER(vp)],
@@ -229,8 +233,9 @@ class Problem:
         self.n, self.d, self.K = n, d, K
 
     # -- hot path -------------------------------------------------------------------------
-    def sketch(self, kind: str, m: int, s: int = 1, seed: int = 0, entries: str = "f64", stream=None):
-        sd = SketchDesc(SKETCH_KIND[kind], m, s, seed, DTYPE[entries])
+    def sketch(self, kind: str, m: int, s: int = 1, seed: int = 0, entries: str = "f64", apply: str = "auto",
+               stream=None):
+        sd = SketchDesc(SKETCH_KIND[kind], m, s, seed, DTYPE[entries], SKETCH_APPLY[apply])
         _check(_lib.ihsbin_sketch(self.h, C.byref(sd), _stream(stream)))
 
     def build_basis(self, lambda_min: float, lambda_max: float, *, L: int = 0,
@@ -262,10 +267,10 @@ class Problem:
     def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",
                         eps: float = 0.0, gamma1: float = 0.0, gamma2: float = 0.0, gamma3: float = 0.0,
                         max_iter: int = 0, m_max: int = 0, compute: str = "f32x2", trace_cap: int = 256,
-                        want_x: bool = False, stream=None):
+                        want_x: bool = False, apply: str = "auto", stream=None):
         """Algorithm 4: returns dict(m, iterations, doublings, delta0, delta, deltas, ms, steps[, x]);
         the problem is left sketched with the final m."""
-        sd = SketchDesc(SKETCH_KIND[kind], m0, s, seed, DTYPE[entries])
+        sd = SketchDesc(SKETCH_KIND[kind], m0, s, seed, DTYPE[entries], SKETCH_APPLY[apply])
         ad = AdaptiveDesc(sd, lam, eps, gamma1, gamma2, gamma3, max_iter, m_max, COMPUTE[compute])
         res = AdaptiveResult()
         dl = np.zeros(trace_cap)
@@ -337,6 +342,12 @@ class Problem:
         _check(_lib.ihsbin_sketch_export(self.h, _ptr(idx), _ptr(sign), cap, C.byref(cnt)))
         return idx, sign, cnt.value
 
+    def sketch_entries(self, row0: int, nrows: int, col0: int, ncols: int):
+        """BF16 bits (uint16, nrows x ncols) of a window of the Gaussian sketch with BF16 entries."""
+        out = np.empty((nrows, ncols), dtype=np.uint16)
+        _check(_lib.ihsbin_sketch_entries_export(self.h, row0, nrows, col0, ncols, _ptr(out)))
+        return out
+
     def sketch_matrices(self, m: int, D: int):
         SA = np.empty((m, D))
         GS = np.empty((D, D))
@@ -396,6 +407,18 @@ class Problem:
                                             C.byref(name)))
             if n.value:
                 out[name.value.decode()] = (n.value, ms.value, fl.value, by.value)
+        return out
+
+    def kernel_exec(self):
+        """{category: (executed flops, executed bytes)} for every category with launches."""
+        out = {}
+        for cat in range(KCAT_COUNT):
+            n, xf, xb = C.c_int64(), C.c_double(), C.c_double()
+            name = C.c_char_p()
+            _check(_lib.ihsbin_kernel_stats(self.h, cat, C.byref(n), None, None, None, C.byref(name)))
+            if n.value:
+                _check(_lib.ihsbin_kernel_exec(self.h, cat, C.byref(xf), C.byref(xb)))
+                out[name.value.decode()] = (xf.value, xb.value)
         return out
 
     def close(self):

@@ -246,11 +246,11 @@ def test_auto_parameters_match_oracle(ctx, compute):
 
 @pytest.mark.parametrize("compute", ["f64", "f32x2"])
 def test_bf16_gaussian_sketch_entries(ctx, compute):
-    # BF16 data with BF16 sketch entries: exact products, float-float accumulation of S A
+    # BF16 data with BF16 sketch entries on the CUDA cores: exact products, float-float accumulation of S A
     from paper_2210_12212_gb300 import ihsbin as ihs
     prob = small("c4_small")
     gp = gpu_problem(ihs, ctx, prob)
-    gp.sketch("gaussian", prob.m, 1, 21, entries="bf16")
+    gp.sketch("gaussian", prob.m, 1, 21, entries="bf16", apply="fma")
     SA, GS = gp.sketch_matrices(prob.m, prob.d)
     SAo = osk.apply_gaussian(oracle_A(prob), prob.m, 21, bf16_entries=True)
     np.testing.assert_allclose(SA, SAo, rtol=0, atol=1e-13 * np.abs(SAo).max())
