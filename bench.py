@@ -1,10 +1,11 @@
 #!/usr/bin/env python
 """Ridge-path benchmark: IHS-BIN on GB300 through the C ABI.
 
-Workload (default `c2`): dense FP32 A 65536 x 1024 with singular values 1/k and
-Haar factors, b from a planted x* plus 1% noise, SRHT sketch m = 2048, T = 200
-lambdas log-spaced in [1e-6, 1] * ||A||_2^2, L = 27 intervals, per-interval
-(rho1, rho2, k) from tests/golden/c2_params.json.
+Workload (default `c4`, the largest single-GPU configuration): dense BF16 A 262144 x 2048 with
+power-law columns (1+j)^-1, B 262144 x 64 from a planted X* plus 1% noise, Gaussian sketch
+m = 4096 with BF16 entries, T = 500 lambdas log-spaced in [1e-4, 1e-2] * ||A||_2^2, L = 9
+intervals, per-interval (rho1, rho2, k) from tests/golden/c4_params.json.  `--config c2` (dense
+FP32 65536 x 1024, SRHT) and the other workloads of synthetic/configs.py stay available.
 
 One step = one whole path: sketch (a1), factor + inverse (a2), Gram + rhs
 (a3), basis recursion (a4), evaluation of all T lambdas (a6), with A and B
@@ -51,6 +52,9 @@ WORKLOADS = {
           "(columns (1+j)^-0.8, SRHT) / 50% CSR 1% density (CountSketch s=1), m=2d, lambda in "
           "[1e-3,1e-1]*||A||_F^2/d, parameters from the sketch (Theorem 4, eps=1e-7), jmax=32",
 }
+L2_NOTE = {"c2": "inputs larger than L2 (A is 256 MiB)", "c4": "inputs larger than L2 (A is 1 GiB)",
+           "c3": "inputs larger than L2 (CSR A is 344 MB)", "c3t": "inputs larger than L2 (CSR A is 344 MB)",
+           "c1": "A is 1.5 MiB: L2-resident, latency-bound"}
 # FP32 lanes per SM and SM count of GB300; max SM clock 2070 MHz
 FP32_INSTR_PEAK = 152 * 128 * 2.07e9
 FP64_FMA_PEAK = 152 * 2 * 2.07e9
@@ -66,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ihsbin", choices=["ihsbin", "reference"])
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c4")
     ap.add_argument("--compute", default="f32x2", choices=["f32x2", "f64"])
     ap.add_argument("--jmax", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
@@ -141,55 +145,89 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------ CPU oracle
-def oracle_sample(prob, par, reps=1):
-    """The FP64 oracle, as it stands, on a bounded sample of the path: the sketch, the Gram
-    matrix and right-hand side, the factor of one interval, that interval's basis and the
-    evaluation of its lambdas.  Per-path time = fixed part + per-column time x all basis columns."""
+def _timed(fn, *a):
+    t = time.perf_counter()
+    r = fn(*a)
+    return r, time.perf_counter() - t
+
+
+def oracle_sample(prob, par, jmax=0, target_s=1.5, A=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the path (about 5 s), extrapolated to
+    one whole path:
+      * the sketch: all of it, except for the Gaussian sketch, whose rows are drawn and applied in
+        blocks (r rows of S timed, x m / r);
+      * the Gram of A_hat: all of it up to 2^34 multiply-adds, else a block of rows (x N / rows);
+      * the right-hand side A_hat^T B and one factor of G_S + lam0 I: whole (x L for the factor);
+      * the basis of the median-k interval with the same truncation jmax as the GPU run, its first
+        k_s terms (k_s doubled until a sample takes `target_s`), extrapolated by the product
+        columns of the recursion, sum over steps i of min(i, J) K, to every interval, plus its
+        evaluation.
+    A: the oracle's matrix when the caller already holds it (data preparation, not timed)."""
     from oracle import ihsbin as ob
     from oracle import sketch as osk
-    A = oracle_matrix(prob)
+    A = oracle_matrix(prob) if A is None else A
     if "tau" in par:   # the library's own plan (sketch-derived parameters)
         plan = ob.Plan(prob.lambda_min, prob.lambda_max, par["L"], np.array(par["edges"]), np.array(par["lam0"]),
                        np.array(par["tau"]), np.array(par["k"]))
     else:
         plan = ob.make_plan(prob.lambda_min, prob.lambda_max, par["rho1"], par["rho2"], par["k"], L=par["L"])
-    t0 = time.perf_counter()
-    Ahat, c, _ = ob.tall_form(A, prob.B)
-    SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
-    GS = SA.T @ SA
-    G = Ahat.T @ Ahat
-    G = np.asarray(G.todense()) if hasattr(G, "todense") else G
-    t_fixed = time.perf_counter() - t0
-    ks = np.array(par["k"])
-    l = int(np.argsort(ks)[len(ks) // 2])          # the median-k interval
-    # its basis with k_s = 8, 16, ... terms until one sample takes a few seconds (or k_s = k_l):
-    # every term of step i costs one product and one preconditioner solve per column, so the
-    # time per basis column is what extrapolates
-    t1 = time.perf_counter()
-    P = ob.precond(GS, plan.lam0[l])
-    t_factor = time.perf_counter() - t1
-    k_s = min(8, int(ks[l]))
+    (Ahat, c, _), t_rhs = _timed(ob.tall_form, A, prob.B)
+    N, D = Ahat.shape
+    bf16 = prob.storage == "bf16"
+    if prob.sketch == "gaussian" and prob.m * N * D > (1 << 32):
+        r = 8
+        while True:
+            S, t_s = _timed(lambda rr: osk._round_bf16(osk.gaussian_entries(prob.m, N, prob.sketch_seed,
+                                                                                 rows=np.arange(rr)))
+                            if bf16 else osk.gaussian_entries(prob.m, N, prob.sketch_seed, rows=np.arange(rr)), r)
+            SAr, t_a = _timed(lambda: S @ Ahat)
+            if t_s + t_a >= target_s or 2 * r > prob.m:
+                break
+            r *= 2
+        t_sketch = (t_s + t_a) * prob.m / r
+        SA = np.tile(SAr, (prob.m // r + 1, 1))[:prob.m]   # stand-in of the right shape for the timing below
+        sk_note = f"Gaussian sketch: {r} of {prob.m} rows of S drawn and applied ({t_s + t_a:.2f}s, x m/{r})"
+    else:
+        SA, t_sketch = _timed(osk.apply, prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16)
+        sk_note = f"sketch whole ({t_sketch:.2f}s)"
+    GS, t_gs = _timed(lambda: SA.T @ SA)
+    if hasattr(Ahat, "tocsr") or N * D * D <= (1 << 34):
+        G, t_gram = _timed(lambda: Ahat.T @ Ahat)
+        G = np.asarray(G.todense()) if hasattr(G, "todense") else G
+        gr_note = f"Gram whole ({t_gram:.2f}s)"
+    else:
+        nb = max(1024, min(N, (1 << 34) // (D * D)))
+        G, t_b = _timed(lambda: Ahat[:nb].T @ Ahat[:nb])
+        t_gram = t_b * N / nb
+        G = G * (N / nb)
+        gr_note = f"Gram: {nb} of {N} rows ({t_b:.2f}s, x N/{nb})"
+    t_fixed = t_sketch + t_gs + t_gram + t_rhs
+    ks = np.array(plan.k)
+    L = len(ks)
+    K = c.shape[1] if c.ndim == 2 else 1
+    l = int(np.argsort(ks)[L // 2])          # the median-k interval
+    P, t_factor = _timed(ob.precond, GS, plan.lam0[l])
+    J = lambda k: k if jmax <= 0 else min(k, jmax)
+    cols = lambda k: sum(min(i, J(k)) for i in range(1, k)) + 1    # product columns (per rhs column) of a basis
+    lams = prob.lambdas[(prob.lambdas >= plan.edges[l]) & (prob.lambdas <= plan.edges[l + 1])]
+    k_s = min(4, int(ks[l]))
     while True:
-        samples = []
-        for _ in range(reps):
-            t1 = time.perf_counter()
-            ut = ob.basis(lambda V: G @ V, P, c, plan.tau[l], k_s)
-            for lam in prob.lambdas[(prob.lambdas >= plan.edges[l]) & (prob.lambdas <= plan.edges[l + 1])]:
-                ob.evaluate(ut, plan.tau[l], plan.lam0[l], lam)
-            samples.append(time.perf_counter() - t1)
-        if k_s >= int(ks[l]) or min(samples) > 3.0:
+        t1 = time.perf_counter()
+        ut = ob.basis(lambda V: G @ V, P, c, plan.tau[l], k_s, jmax=jmax)
+        for lam in lams:
+            ob.evaluate(ut, plan.tau[l], plan.lam0[l], lam)
+        t_cols = time.perf_counter() - t1
+        if k_s >= int(ks[l]) or t_cols > target_s:
             break
         k_s = min(2 * k_s, int(ks[l]))
-    t_cols = min(samples)
-    cols = ks * (ks + 1) / 2
-    per_path = t_fixed + len(ks) * t_factor + t_cols * cols.sum() / (k_s * (k_s + 1) / 2)
-    t_int = t_factor + t_cols * cols[l] / (k_s * (k_s + 1) / 2)
+    per_path = t_fixed + L * t_factor + t_cols * sum(cols(int(k)) for k in ks) / cols(k_s)
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return dict(value=1.0 / per_path, unit="paths/s", cores=cores, kind="oracle",
-                sample=f"FP64 numpy oracle: sketch+Gram+rhs ({t_fixed:.2f}s), the factor of interval {l} "
-                       f"({t_factor:.2f}s) and its first {k_s} of k={int(ks[l])} basis terms with evaluation "
-                       f"({t_cols:.2f}s) on the {prob.name} path; per-path time = fixed + L factors + "
-                       f"time per basis column x sum_l k_l(k_l+1)/2", t_fixed=t_fixed, t_interval=t_int)
+                sample=f"FP64 numpy oracle on the {prob.name} path: {sk_note}; {gr_note}; rhs ({t_rhs:.2f}s); "
+                       f"the factor of interval {l} ({t_factor:.2f}s, x L={L}); its first {k_s} of k={int(ks[l])} "
+                       f"basis terms (jmax={jmax if jmax > 0 else 'all'}, K={K}) with evaluation ({t_cols:.2f}s), "
+                       f"extrapolated to all intervals by product columns; per-path time {per_path:.1f}s",
+                t_fixed=t_fixed)
 
 
 def oracle_matrix(prob):
@@ -200,26 +238,43 @@ def oracle_matrix(prob):
     return prob.dense_f64()
 
 
+def config_for(args, prob, par, world=1):
+    """The `config` object of both arms' JSON lines (identical keys and values)."""
+    return {"workload": WORKLOADS.get(args.config, args.config) + (
+                f"; plus {args.losses} held-out rows of the same model, a step returns the training "
+                f"and test losses of every lambda (X not formed)" if args.losses else "") + (
+                f"; the sketch dimension chosen by Algorithm 4 from m0={args.adaptive} at lambda_min "
+                f"inside each step" if args.adaptive else ""),
+            "jmax": args.jmax,
+            "storage": prob.storage,
+            "l2": L2_NOTE.get(args.config, "see workload"),
+            "params": (f"tests/golden/{args.config[:-1] if args.config == 'c3t' else args.config}_params.json"
+                       if par is not None and "tau" not in par else
+                       "from the sketch (rho from d_e, k from Theorem 4 at eps)"),
+            "parallelism": f"replicas x{world}"}
+
+
 def reference_arm(args, prob, par):
-    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only)."""
+    """--impl reference: the FP64 oracle as it stands on the host cores (rank 0 only), each step a
+    bounded sample of the same path (oracle_sample), with the GPU arm's truncation jmax."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    A = oracle_matrix(prob)            # data preparation, outside every sample
     for _ in range(args.warmup):
-        oracle_sample(prob, par)
+        oracle_sample(prob, par, jmax=args.jmax, A=A)
     times, vals = [], []
-    t0 = time.perf_counter()
     info = None
     for _ in range(args.steps):
         t1 = time.perf_counter()
-        info = oracle_sample(prob, par)
+        info = oracle_sample(prob, par, jmax=args.jmax, A=A)
         times.append(time.perf_counter() - t1)
         vals.append(info["value"])
     value = statistics.median(vals)
     line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS.get(args.config, args.config), "l2": "inputs larger than L2"},
+            "config": config_for(args, prob, par, args.gpus),
             "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "paths/s", "cores": info["cores"], "kind": "oracle",
                              "sample": info["sample"]},
@@ -452,6 +507,7 @@ def main():
         # ---- the same K steps again with CUDA events around every launch, on the launching stream:
         # the per-kernel device times of the roofline and of the kernel table
         inst_ms, _, stats, _ = timed_steps(True)
+        xstats = p.kernel_exec()
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
@@ -504,13 +560,31 @@ def main():
     traffic = read_traffic(name, launches / args.steps if args.steps else 0)
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
             "algorithmic_bytes_per_launch": byts / launches if launches else 0.0,
+            "algorithmic_flops_per_launch": flops / launches if launches else 0.0,
             "traffic": traffic, "kernel": name, "launches_per_step": launches / args.steps,
             "avg_launch_ms": ms / launches, "peak_basis": peak_note}
+    xf, xb = xstats.get(name, (flops, byts))
+    if (xf, xb) != (flops, byts):
+        # what the launches execute: the BF16 products of every kept slice pair and the slice images
+        roof["executed"] = {"flops_per_launch": xf / launches, "bytes_per_launch": xb / launches,
+                            "tflops": xf / (ms * 1e-3) / 1e12, "gbs": xb / (ms * 1e-3) / 1e9,
+                            "frac_tensor": xf / (ms * 1e-3) / 1e12 / measured_peak("bf16_tflops_sustained", 1700.0)[0],
+                            "frac_hbm": xb / (ms * 1e-3) / 1e9 / measured_peak("hbm_gbs", 6800.0)[0]}
+    # the basis build as a phase (step a4): the method's bytes of every recursion launch per path
+    # over the recursion's device time per path, against the copy bandwidth
+    loop_cats = [k for k in stats if k.startswith("loop_")]
+    bb = sum(stats[k][3] for k in loop_cats) / args.steps
+    hbm_pk = measured_peak("hbm_gbs", 6800.0)[0]
+    tb = phases["basis"]
+    basis_roof = {"bound": "hbm", "bytes_per_path": bb, "ms_per_path": tb,
+                  "achieved": bb / (tb * 1e-3) / 1e9 if tb > 0 else 0.0, "peak": hbm_pk,
+                  "unit": "GB/s", "categories": loop_cats}
+    basis_roof["frac"] = basis_roof["achieved"] / hbm_pk
 
     cpu = None
     note("parity done")
     if rank == 0 and not args.no_cpu and world == 1:
-        info = oracle_sample(prob, par if par is not None else p.plan_dict_for_oracle())
+        info = oracle_sample(prob, par if par is not None else p.plan_dict_for_oracle(), jmax=args.jmax)
         cpu = {k: info[k] for k in ("value", "unit", "cores", "kind", "sample")}
 
     gpu_launches = int(sum(v[0] for v in stats_clean.values()))
@@ -520,21 +594,12 @@ def main():
             "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.compute, "data": "synthetic",
-            "config": {"workload": WORKLOADS.get(args.config, args.config) + (
-                           f"; plus {args.losses} held-out rows of the same model, a step returns the training "
-                           f"and test losses of every lambda (X not formed)" if args.losses else "") + (
-                           f"; the sketch dimension chosen by Algorithm 4 from m0={args.adaptive} at lambda_min "
-                           f"inside each step" if args.adaptive else ""),
-                       "jmax": args.jmax,
-                       "storage": prob.storage, "l2": ("inputs larger than L2 (A is 256 MiB)" if args.config == "c2"
-                                                       else "see workload"),
-                       "params": (f"tests/golden/{args.config}_params.json" if par is not None else
-                                  "from the sketch (rho from d_e, k from Theorem 4 at eps)"),
-                       "parallelism": f"replicas x{world}"},
+            "config": config_for(args, prob, par, world),
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
             "instrumented_ms_per_step": inst_ms / args.steps,
             "phase_ms": phases,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "tuning": [" ".join(x.split()[:1] + x.split()[2:3]) for x in ihs.tuning_report().splitlines()],
+            "roofline": roof, "basis_roofline": basis_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk.summary(), "parity": check,
             "kernels": {k: {"launches": v[0], "ms": v[1], "tflops": (v[2] / (v[1] * 1e-3) / 1e12 if v[1] else 0)}
                         for k, v in stats.items()},
@@ -555,7 +620,9 @@ def parity_sample(prob, par, X, tol=1e-6, eps=1e-7):
     idx = np.unique(np.linspace(0, len(prob.lambdas) - 1, 9).round().astype(int))
     lams = prob.lambdas[idx]
     Ahat, c, dual = ob.tall_form(A, prob.B)
-    SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16")
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    SA = osk.apply(prob.sketch, Ahat, prob.m, prob.s, prob.sketch_seed, bf16_entries=prob.storage == "bf16",
+                   workers=max(1, min(16, cores - 1)))
     GS = SA.T @ SA
     if par is None:
         plan = ob.auto_plan(GS, prob.m, prob.lambda_min, prob.lambda_max, eps=eps)
@@ -620,7 +687,8 @@ def kernel_peak(name, compute):
     if name in HBM_BOUND:
         pk, how = measured_peak("hbm_gbs", 6800.0)
         return "hbm", pk, f"copy bandwidth (MEASURED_PEAKS.json hbm_gbs), {how}"
-    if name in ("gram_tc_mma", "loop_gram_tc", "loss_image_tc"):  # BF16 tensor-core slice products, inside a long step
+    if name in ("gram_tc_mma", "loop_gram_tc", "loss_image_tc", "sketch_tc", "sketch_gram", "rhs", "inverse_tc",
+                "trtri_tc", "factor_syrk_tc"):  # tensor-core products, inside a long step
         pk, how = measured_peak("bf16_tflops_sustained", 1700.0)
         return "tensor", pk, f"cuBLAS bf16 sustained (MEASURED_PEAKS.json), {how}"
     if compute == "f64":

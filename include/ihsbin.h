@@ -24,7 +24,9 @@
  *    stream has completed (the status word is read there);
  *  - device memory comes from a stream-ordered pool owned by the context
  *    (freed blocks are kept for reuse), so no call synchronises the device;
- *  - on error, outputs are unspecified and the problem keeps its previous state;
+ *  - on error, outputs are unspecified; a failed ihsbin_sketch leaves the problem unsketched
+ *    and a failed ihsbin_build_basis leaves it sketched without a basis (their previous result
+ *    is discarded when they start); every other call leaves the problem as it was;
  *  - ihsbin_last_error() returns a thread-local description of the last error.
  */
 #ifndef IHSBIN_H
@@ -198,6 +200,9 @@ typedef struct {
                      * lam0 = sqrt((hi + s)(lo + s)) - s, takes tau = 2 (lam0 + s) / ((lo + s)/rho1 + (hi + s)/rho2)
                      * and, for auto k, Theorem 4's rate with kt = rho1 (hi + s) / (rho2 (lo + s)); 0 is the
                      * default rule (lam0 = sqrt(lo hi)) */
+  const double* tau; /* NULL: tau_l from Theorem 4's rule above; else an array of L explicit steps (each finite
+                      * and > 0; needs L > 0), for callers who tuned them (Theorem 4's rho are not computable
+                      * from data in practice); rho1/rho2 still set k_l when k is NULL and k_default <= 0 */
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -209,6 +214,10 @@ typedef struct ihsbin_problem ihsbin_problem;
  * release with ihsbin_ctx_destroy after every problem of it is destroyed. */
 IHSBIN_API ihsbin_status ihsbin_ctx_create(int device, uint64_t hbm_budget_bytes, ihsbin_ctx** out);
 IHSBIN_API ihsbin_status ihsbin_ctx_destroy(ihsbin_ctx* ctx);
+/* Test hook for the error paths: after `after` more device allocations of this context succeed,
+ * every further one fails (the call returns IHSBIN_ERR_OUT_OF_MEMORY) until the hook is reset with
+ * after < 0.  The failure is made on the host, before any device memory is requested. */
+IHSBIN_API ihsbin_status ihsbin_ctx_fail_allocations(ihsbin_ctx* ctx, int64_t after);
 /* Bytes of device memory currently held by the context's problems. */
 IHSBIN_API ihsbin_status ihsbin_ctx_memory(const ihsbin_ctx* ctx, uint64_t* bytes_in_use);
 IHSBIN_API const char* ihsbin_last_error(void);
@@ -374,6 +383,17 @@ IHSBIN_API ihsbin_status ihsbin_kernel_stats(ihsbin_problem* p, int32_t cat, int
  * BF16 flops of every kept slice pair and the bytes of the slice images they stream
  * (12 bytes per FP64-class entry), for every other kernel the algorithmic figures. */
 IHSBIN_API ihsbin_status ihsbin_kernel_exec(ihsbin_problem* p, int32_t cat, double* xflops, double* xbytes);
+
+/* Launch geometry chosen by measurement (the library's own autotuner; the paper has none).
+ * Launch sites whose candidate geometries compute identical values (cluster size of the
+ * recursion's per-column kernels; the SMs the Gram of A leaves to the factorization beside
+ * it) try each candidate on their first launches of a shape class, timed with CUDA events,
+ * and settle on the fastest once every candidate has two samples.  The table is process-wide.
+ * ihsbin_tuning_report writes one text line per tuned site and shape class (the chosen value and
+ * every candidate's best time) into buf (cap bytes, NUL-terminated; *need receives the size
+ * needed); ihsbin_tuning_reset forgets every choice. */
+IHSBIN_API ihsbin_status ihsbin_tuning_report(char* buf, int64_t cap, int64_t* need);
+IHSBIN_API ihsbin_status ihsbin_tuning_reset(void);
 
 /* ---- Serving: a continuous-batching request loop (the library's runtime; the
  * paper solves one problem at a time).  `slots` worker threads each own a CUDA

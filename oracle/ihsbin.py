@@ -211,28 +211,33 @@ def precond_svd_apply(SA: np.ndarray, lam0: float, V: np.ndarray) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------- basis
-def basis(AtA: Callable, P: Precond, c: np.ndarray, tau: float, k: int) -> np.ndarray:
+def basis(AtA: Callable, P: Precond, c: np.ndarray, tau: float, k: int, jmax: int = 0) -> np.ndarray:
     """Algorithm 2 (matrix form: Algorithm 5) in the re-centred, re-scaled form.
 
-    Returns utilde with shape (k, D, K).  The in-place descending-j order of
-    Algorithm 2 is kept: u_i is formed from the old u_{i-1}, then u_j for
-    j = i-1..1 from the old u_j and old u_{j-1}, then u_0; the products
-    A^T A u_j of one outer step all use the values from before that step.
+    Returns utilde with shape (k, D, K) (jmax > 0: only the terms j < min(k, jmax), shape
+    (min(k, jmax), D, K)).  The in-place descending-j order of Algorithm 2 is kept: u_i is
+    formed from the old u_{i-1}, then u_j for j = i-1..1 from the old u_j and old u_{j-1},
+    then u_0; the products A^T A u_j of one outer step all use the values from before that
+    step.  u_j is updated from u_j and u_{j-1} only, so the terms j < jmax do not depend on
+    the higher ones and truncating at jmax leaves them unchanged.
     """
     lam0 = P.lam0
     c = np.atleast_2d(c.T).T if c.ndim == 1 else c
     D, K = c.shape
-    u: List[Optional[np.ndarray]] = [None] * k
-    ut = np.zeros((k, D, K))
+    J = k if jmax <= 0 else min(k, jmax)
+    u: List[Optional[np.ndarray]] = [None] * J
+    ut = np.zeros((J, D, K))
     u[0] = P.solve(c)                                   # u_00 = P A^T b
     ut[0] += u[0]
     for i in range(1, k):
-        Y = AtA(np.concatenate(u[:i], axis=1)).reshape(D, i, K)   # A^T A u_j, j < i (old values)
-        u[i] = -lam0 * P.solve(u[i - 1])                # u_{i,i} = -Q u_{i-1,i-1}
-        for j in range(i - 1, 0, -1):
+        n_old = min(i, J)
+        Y = AtA(np.concatenate(u[:n_old], axis=1)).reshape(D, n_old, K)   # A^T A u_j, j < i (old values)
+        if i < J:
+            u[i] = -lam0 * P.solve(u[i - 1])            # u_{i,i} = -Q u_{i-1,i-1}
+        for j in range(n_old - 1, 0, -1):
             u[j] = u[j] - P.solve(tau * (Y[:, j] + lam0 * u[j]) + lam0 * u[j - 1])
         u[0] = u[0] - P.solve(tau * (Y[:, 0] + lam0 * u[0]))
-        for j in range(i + 1):
+        for j in range(min(i + 1, J)):
             ut[j] += u[j]
     return ut
 

@@ -83,17 +83,31 @@ def fwht_rows(X: np.ndarray) -> np.ndarray:
     return X
 
 
+def _gaussian_rows(args):
+    """Rows [r0, r1) of S (BF16-rounded when asked), for a worker process."""
+    m, N, seed, r0, r1, bf16_entries = args
+    S = gaussian_entries(m, N, seed, rows=np.arange(r0, r1))
+    return _round_bf16(S).astype(np.float32) if bf16_entries else S
+
+
 def apply_gaussian(Ahat: np.ndarray, m: int, seed: int, bf16_entries: bool = False,
-                   block: int = 512) -> np.ndarray:
-    """SA for the Gaussian sketch; S is generated in row blocks (never all at once)."""
+                   block: int = 512, workers: int = 0) -> np.ndarray:
+    """SA for the Gaussian sketch; S is generated in row blocks (never all at once).
+
+    workers > 1 draws the row blocks in that many spawned processes (BF16 entries travel as
+    float32, which holds them exactly); each block's product is the same as in the serial loop."""
     N, D = Ahat.shape
     out = np.empty((m, D))
-    for r0 in range(0, m, block):
-        r1 = min(m, r0 + block)
-        S = gaussian_entries(m, N, seed, rows=np.arange(r0, r1))
-        if bf16_entries:
-            S = _round_bf16(S)
-        out[r0:r1] = S @ Ahat
+    jobs = [(m, N, seed, r0, min(m, r0 + block), bf16_entries) for r0 in range(0, m, block)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            for job, S in zip(jobs, ex.map(_gaussian_rows, jobs)):
+                out[job[3]:job[4]] = S.astype(np.float64) @ Ahat
+        return out
+    for job in jobs:
+        out[job[3]:job[4]] = _gaussian_rows(job).astype(np.float64) @ Ahat
     return out
 
 
@@ -129,10 +143,10 @@ def _round_bf16(x: np.ndarray) -> np.ndarray:
     return (r.astype(np.uint32) << np.uint32(16)).view(np.float32).astype(np.float64)
 
 
-def apply(kind: str, Ahat, m: int, s: int, seed: int, bf16_entries: bool = False) -> np.ndarray:
+def apply(kind: str, Ahat, m: int, s: int, seed: int, bf16_entries: bool = False, workers: int = 0) -> np.ndarray:
     if kind == "gaussian":
         dense = Ahat.toarray() if hasattr(Ahat, "toarray") else Ahat
-        return apply_gaussian(dense, m, seed, bf16_entries)
+        return apply_gaussian(dense, m, seed, bf16_entries, block=128 if workers > 1 else 512, workers=workers)
     if kind == "countsketch":
         return apply_countsketch(Ahat, m, s, seed)
     if kind == "srht":

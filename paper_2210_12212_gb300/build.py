@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libihsbin.so")
-SOURCES = ["api.cu", "kernels.cu", "sparse.cu", "serve.cu", "noalloc.cu", "tc_gram.cu", "tc_loop.cu", "tc_sketch.cu"]
+SOURCES = ["api.cu", "kernels.cu", "sparse.cu", "serve.cu", "noalloc.cu", "tc_gram.cu", "tc_loop.cu", "tc_sketch.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "--default-stream", "per-thread",

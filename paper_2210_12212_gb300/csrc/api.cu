@@ -54,6 +54,7 @@ ihsbin_status check_status(ihsbin_problem* p, cudaStream_t st, const char* where
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, where);
   resolve_timing(p);
+  tune_resolve();
   int s = 0;
   e = cudaMemcpy(&s, p->status, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, where);
@@ -87,7 +88,8 @@ void finalize_plan(ihsbin_problem* p, const double* trP) {
       pl.rho2[l] = (1.0 - std::sqrt(r)) * (1.0 - std::sqrt(r));
     }
     const double s2 = pl.sigma_d2;
-    pl.tau[l] = 2.0 * (pl.lam0[l] + s2) / ((lo + s2) / pl.rho1[l] + (hi + s2) / pl.rho2[l]);
+    pl.tau[l] = pl.tau_user.empty() ? 2.0 * (pl.lam0[l] + s2) / ((lo + s2) / pl.rho1[l] + (hi + s2) / pl.rho2[l])
+                                    : pl.tau_user[l];
     if (pl.auto_k) {
       const double kt = pl.rho1[l] * (hi + s2) / (pl.rho2[l] * (lo + s2));
       const double rate = (kt - 1.0) / (kt + 1.0);
@@ -107,6 +109,11 @@ cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
   if (bytes == 0) bytes = 16;
   {
     std::lock_guard<std::mutex> g(p->ctx->mu);
+    if (p->ctx->fail_after == 0) {
+      g_err = "allocation failed (the context's allocation-failure hook)";
+      return cudaErrorMemoryAllocation;
+    }
+    if (p->ctx->fail_after > 0) --p->ctx->fail_after;
     if (p->ctx->budget && p->ctx->in_use + bytes > p->ctx->budget) {
       g_err = "admission: request exceeds the context's device-memory budget";
       return cudaErrorInvalidValue;
@@ -212,6 +219,29 @@ ihsbin_status ihsbin_ctx_create(int device, uint64_t budget, ihsbin_ctx** out) {
   uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for the next request
   cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   *out = c;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_tuning_report(char* buf, int64_t cap, int64_t* need) {
+  const std::string r = tune_report();
+  if (need) *need = (int64_t)r.size() + 1;
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>(r.size(), (size_t)cap - 1);
+    std::copy(r.begin(), r.begin() + n, buf);
+    buf[n] = 0;
+  }
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_tuning_reset(void) {
+  tune_reset();
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_ctx_fail_allocations(ihsbin_ctx* ctx, int64_t after) {
+  if (!ctx) return fail(IHSBIN_ERR_INVALID_ARG, "ctx_fail_allocations: NULL");
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->fail_after = after < 0 ? -1 : after;
   return IHSBIN_OK;
 }
 
@@ -441,8 +471,10 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
   if (e == cudaSuccess) e = sketch_gram(p, st);
   cudaEventRecord(e1, st);
   if (e != cudaSuccess) {
+    cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaMemset(p->status, 0, sizeof(int));  // nothing of the failed sketch is reported later
     return cuda_fail(e, "sketch");
   }
   ihsbin_status s = check_status(p, st, "sketch");
@@ -512,6 +544,7 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   if (d->L < 0 || d->jmax < 0) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: negative L or jmax");
   if (!(d->sigma_d2 >= 0) || !std::isfinite(d->sigma_d2))
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: sigma_d2 must be finite and >= 0");
+  if (d->tau && !(d->L > 0)) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: an explicit tau array needs L > 0");
   if (d->compute != IHSBIN_COMPUTE_F64 && d->compute != IHSBIN_COMPUTE_F32X2)
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown compute mode");
   Plan pl;
@@ -534,6 +567,11 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.rho1.resize(L);
   pl.rho2.resize(L);
   pl.sigma_d2 = d->sigma_d2;
+  if (d->tau) {
+    pl.tau_user.assign(d->tau, d->tau + L);
+    for (double t : pl.tau_user)
+      if (!(t > 0) || !std::isfinite(t)) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: every tau must be finite and > 0");
+  }
   for (int l = 0; l < L; ++l) {
     const double lo = pl.edges[l], hi = pl.edges[l + 1];
     pl.lam0[l] = pl.sigma_d2 > 0 ? std::sqrt((hi + pl.sigma_d2) * (lo + pl.sigma_d2)) - pl.sigma_d2 : std::sqrt(lo * hi);
@@ -601,6 +639,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
       if (p->fac) cudaStreamSynchronize(p->fac);
       for (auto& x : ev) cudaEventDestroy(x);
       prob_free_basis(p);
+      cudaMemset(p->status, 0, sizeof(int));  // nothing of the failed build is reported later
+      tune_discard();
       return cuda_fail(e, "build_basis");
     }
     s = check_status(p, st, "build_basis");

@@ -16,6 +16,7 @@ struct ihsbin_ctx {
   uint64_t in_use = 0;
   std::mutex mu;
   cudaMemPool_t pool = nullptr;  // stream-ordered pool that keeps freed memory for reuse
+  int64_t fail_after = -1;        // test hook: allocations left before every one fails (-1: off)
 };
 
 namespace ihsbin {
@@ -55,6 +56,7 @@ struct Plan {
   double eps = 1e-7;
   double sigma_d2 = 0.0;  // known smallest eigenvalue bound (0: the default centring)
   std::vector<double> rho1, rho2;
+  std::vector<double> tau_user;  // explicit per-interval steps (empty: Theorem 4's rule)
 };
 
 struct DevBuf {
@@ -148,6 +150,25 @@ struct KTimer {
 };
 void resolve_timing(ihsbin_problem* p);
 
+// ----- online autotuner of launch geometry (tune.cu) ---------------------------
+struct TuneLaunch {
+  uint64_t key = 0;
+  int cand = 0, value = 0;
+  bool timed = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+enum TuneSite : int { TUNE_COL_R = 1, TUNE_COL_UPDATE = 2, TUNE_COL_MW = 3, TUNE_GRAM_RESERVE = 4 };
+uint64_t tune_key(int site, int64_t a, int64_t b, int64_t c);
+int shape_class(int64_t n);  // ceil(log2 n)
+// The geometry value to launch with (values[cand]); while the key is being tuned the launch is
+// bracketed by events: call tune_end after it on the same stream.
+TuneLaunch tune_begin(uint64_t key, const char* site, const int* values, int ncand, cudaStream_t st);
+void tune_end(TuneLaunch& t, cudaStream_t st);
+void tune_resolve();  // after this host thread's tuned launches have completed
+void tune_discard();
+std::string tune_report();
+void tune_reset();
+
 // ----- kernel launchers (kernels.cu); all return the first CUDA error --------
 cudaError_t launch_transpose_dense(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
                                    void* dst, cudaStream_t st);
@@ -176,10 +197,15 @@ void finalize_plan(ihsbin_problem* p, const double* trP);
 cudaError_t csr_gram(ihsbin_problem* p, int compute, cudaStream_t st);
 
 // Dense FP32/BF16 Gram on the tensor cores from exact integer slices (tc_gram.cu)
-constexpr int kGramSlices = 6;     // BF16 slices per entry
+constexpr int kGramSlices = 6;     // BF16 slices per FP32 entry
+constexpr int kGramSlicesBf16 = 4; // BF16 slices per BF16 entry (every entry within 2^-23 of its column maximum exact)
 constexpr int kGramMaxWeight = 6;  // slice pairs (s, t) kept: s + t <= kGramMaxWeight
-// reserve_sms > 0: the tensor-core launches leave that many SMs free (for work on other streams)
-cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms = 0);
+constexpr int kRhsSlices = 6;      // BF16 slices per FP64 entry of B in the right-hand side A_hat^T B
+inline int gram_slices_for(int elem) { return elem == ELEM_BF16 ? kGramSlicesBf16 : kGramSlices; }
+// reserve_sms > 0: the tensor-core launches leave that many SMs free (for work on other streams);
+// rhs != nullptr: also c = A_hat^T B (column-major D x K) from the same slices of A_hat
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms = 0,
+                              CBuf* rhs = nullptr);
 // G_S = (S A_hat)^T (S A_hat) from the FP64 sketch on the tensor cores (7 slices, FP64-class)
 cudaError_t sketch_gram_slices(ihsbin_problem* p, cudaStream_t st);
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);

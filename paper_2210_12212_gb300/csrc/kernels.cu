@@ -1153,7 +1153,8 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
       q.M = nR; q.N = B; q.K = nR; q.groups = L; q.NT = 32; q.ksplit = S;
       q.tri = OZ_TRI_LE_ROW;
       q.ohi = hi; q.olo = lo; q.status = p->status;
-      KTimer kt(p, K_TRTRI_TC, st, oz_pair_flops(1, 1, 1) * L * (nR * (nR + 1.0) / 2.0) * B,
+      KTimer kt(p, K_TRTRI_TC, st, 2.0 * L * (nR * (nR + 1.0) / 2.0) * B, (double)L * (nR * nR / 2.0 + 2.0 * nR * B) * 8,
+                oz_pair_flops(1, 1, 1) * L * (nR * (nR + 1.0) / 2.0) * B,
                 (double)L * (oz_vec_elems(nR, nR, 128) + oz_vec_elems(B, nR, 32)) * 2 + 16.0 * S * L * nR * B);
       CK(oz_gemm(q, st));
     }
@@ -1218,7 +1219,8 @@ static cudaError_t panel_update(ihsbin_problem* p, CBuf H, const PanelUpdate& u,
     q.As = u.Xs; q.ea = u.ea; q.Bs = u.Ys; q.eb = u.eb;
     q.M = M; q.N = M; q.K = w; q.groups = L; q.NT = 32; q.ksplit = 1; q.sym = 1;
     q.ohi = u.hi; q.olo = u.lo; q.status = p->status;
-    KTimer kt(p, K_SYRK_TC, st, oz_pair_flops(1, 1, 1) * L * (M * (M + 1.0) / 2.0) * w,
+    KTimer kt(p, K_SYRK_TC, st, 2.0 * L * (M * (M + 1.0) / 2.0) * w, (double)L * (M * w + M * (M + 1.0) / 2.0) * 8,
+              oz_pair_flops(1, 1, 1) * L * (M * (M + 1.0) / 2.0) * w,
               (double)L * (oz_vec_elems(M, w, 128) + oz_vec_elems(M, w, 32)) * 2 + 16.0 * L * M * M);
     CK(oz_gemm(q, st));
   }
@@ -1271,7 +1273,8 @@ static cudaError_t inverse_slices(ihsbin_problem* p, CBuf Wm, cudaStream_t st) {
     q.tri = OZ_TRI_GE_ROW | OZ_TRI_GE_COL;
     q.sym = 1;
     q.ohi = hi; q.olo = lo; q.status = p->status;
-    KTimer kt(p, K_INVERSE_TC, st, oz_pair_flops(1, 1, 1) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
+    KTimer kt(p, K_INVERSE_TC, st, (double)L * D * (D + 1.0) * (D + 2.0) / 3.0, (double)L * D * D * 8,
+              oz_pair_flops(1, 1, 1) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
               (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2 + (double)L * D * D * 16);
     CK(oz_gemm(q, st));
   }
@@ -1674,7 +1677,9 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
         q.Bs = oz.Bs;
         q.M = D; q.N = ncol; q.K = D; q.groups = 2 * live; q.NT = 16; q.ksplit = ks;
         q.ohi = oz.Zhi; q.olo = oz.Zlo; q.status = p->status;
-        KTimer kt(p, K_LOOP_P_TC, st, 2.0 * oz_pair_flops(D, ncol, D) * live,
+        // the method's step: G U (G read once) and P_l R (each live P_l once); M_l is the implementation's
+        KTimer kt(p, K_LOOP_P_TC, st, 4.0 * D * D * ncol * live, (double)(live + 1) * D * D * 8 + 16.0 * D * ncol * live,
+                  2.0 * oz_pair_flops(D, ncol, D) * live,
                   (double)2 * live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, ncol, 16) * 2) + 32.0 * ks * D * ncol * live);
         CK(oz_gemm(q, st));
       }
@@ -1698,7 +1703,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
         CK(oz_slice_cols(Uin, D, 1, ncat, NT, nold, gs, perm_dev, oz.Bs, oz.eb, st));
       }
       ny = oz_pick_split(D, ncat, 1, NT, SPLIT_MAX);
-      KTimer kt(p, K_LOOP_Y_TC, st, oz_pair_flops(D, ncat, D),
+      KTimer kt(p, K_LOOP_Y_TC, st, 2.0 * D * D * ncat, (double)D * D * 8 + 16.0 * D * ncat, oz_pair_flops(D, ncat, D),
                 (double)oz_rows_elems(D) * 2 + (double)oz_cols_elems(D, ncat, NT) * 2 + 16.0 * ny * D * ncat);
       CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, oz.Yhi, oz.Ylo, p->status, st));
     } else if (pl.product == IHSBIN_PRODUCT_GRAM) {
@@ -1760,7 +1765,8 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       }
       const int ks = oz_pick_split(D, nnew, live, NT, SPLIT_MAX);
       {
-        KTimer kt(p, K_LOOP_P_TC, st, oz_pair_flops(D, nnew, D) * live,
+        KTimer kt(p, K_LOOP_P_TC, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 16.0 * D * nnew * live,
+                  oz_pair_flops(D, nnew, D) * live,
                   (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 16.0 * ks * D * nnew * live);
         CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, erv, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
                       st));
@@ -1899,8 +1905,17 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaMemcpyAsync(lam0_dev, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
 
-  // SMs the Gram's tensor-core launches leave to the factorization running beside them
-  constexpr int GRAM_RESERVE_SMS = 40;
+  // SMs the Gram's tensor-core launches leave to the factorization running beside them: chosen by
+  // the autotuner per shape class, timing the whole fork-join region of both streams
+  const bool tune_reserve =
+      pl.product == IHSBIN_PRODUCT_GRAM && A.layout != IHSBIN_CSR && pl.gram == IHSBIN_GRAM_SLICES;
+  TuneLaunch rtune{};
+  int gram_reserve = 0;
+  if (tune_reserve) {
+    static const int cands[] = {40, 0, 24, 64};
+    rtune = tune_begin(tune_key(TUNE_GRAM_RESERVE, D, shape_class(A.N), L), "gram_reserve_sms", cands, 4, st);
+    gram_reserve = rtune.value;
+  }
   // a3: Gram (product mode GRAM) and right-hand side.  They do not depend on a2 (the factors of
   // the sketched Hessian), so they run on the problem's side stream, forked here and joined
   // before the recursion: their tensor-core work fills the SMs that the factorization's small
@@ -1915,14 +1930,20 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     CallStream side_alloc(s2);
     c = cb((size_t)D * K);
     CK(err);
+    // dense data with the sliced Gram: the right-hand side comes from the same slices of A_hat
+    // (K >= 32: the product's 128-column tiles of B are at least a quarter full)
+    const bool rhs_fused =
+        pl.product == IHSBIN_PRODUCT_GRAM && !csr && !p->dual && pl.gram == IHSBIN_GRAM_SLICES && K >= 32;
     if (pl.product == IHSBIN_PRODUCT_GRAM) {
       p->G = alloc_cbuf(p, cm, (size_t)D * D, SCOPE_BASIS, &err);
       CK(err);
       if (csr) CK(csr_gram(p, cm, s2));
-      else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, s2, GRAM_RESERVE_SMS));
+      else if (pl.gram == IHSBIN_GRAM_SLICES) CK(gram_dense_slices(p, cm, s2, gram_reserve, rhs_fused ? &c : nullptr));
       else CK((gram_dense<Mode, ET>(p, s2)));
     }
-    if (csr && !p->dual) {
+    if (rhs_fused) {
+      // c was formed with the Gram
+    } else if (csr && !p->dual) {
       CK(csr_rhs(p, cm, c, s2));
     } else if (p->dual) {
       KTimer kt(p, K_RHS, s2, 0, (double)D * K * 16);
@@ -1970,6 +1991,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaStreamWaitEvent(st, ev[1], 0));
   CK(cudaStreamWaitEvent(st, ev[2], 0));
   CK(cudaEventRecord(ev[6], st));
+  if (tune_reserve) tune_end(rtune, st);
 
   // a4: the recursion
   const size_t per = (size_t)pl.jc * K * D;
@@ -2086,7 +2108,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
         q.As = oz.Gs; q.a_shared = true; q.Bs = Pc;
         q.M = D; q.N = D; q.K = D; q.groups = Tm; q.NT = 32; q.ksplit = ks;
         q.ohi = mh; q.olo = ml; q.status = p->status;
-        KTimer kt(p, K_INVERSE_TC, st, oz_pair_flops(D, D, D) * Tm,
+        KTimer kt(p, K_INVERSE_TC, st, 2.0 * D * D * D * Tm, (double)(1 + 2 * Tm) * D * D * 8, oz_pair_flops(D, D, D) * Tm,
                   (double)oz_rows_elems(D) * 2 + (double)Tm * vcol * 2 + 16.0 * ks * Tm * D * D);
         CK(oz_gemm(q, st));
       }
@@ -2567,7 +2589,8 @@ static cudaError_t loss_term(ihsbin_problem* p, const LossSrc& s, LossCtx& c, do
         q.As = As; q.ea = ea; q.Bs = c.Bs; q.eb = c.eb;
         q.M = rows; q.N = nc; q.K = d; q.groups = 1; q.NT = 32; q.ksplit = S;
         q.ohi = hi; q.olo = lo; q.status = p->status;
-        KTimer kt(p, K_LOSS_TC, st, oz_pair_flops(rows, nc, d),
+        KTimer kt(p, K_LOSS_TC, st, 2.0 * rows * nc * d, (double)rows * d * es + 8.0 * nc * d + 8.0 * rows * nc,
+                  oz_pair_flops(rows, nc, d),
                   (double)oz_vec_elems(rows, d, 128) * 2 + (double)oz_vec_elems(nc, d, 32) * 2 + 16.0 * S * rows * nc);
         CK(oz_gemm(q, st));
       }

@@ -88,7 +88,7 @@ extern "C" IHSBIN_API ihsbin_status ihsbin_sketch_gram_noalloc(const double* SA,
   if (!SA || !GS) return noalloc_fail(IHSBIN_ERR_INVALID_ARG, "sketch_gram_noalloc: NULL pointer");
   if (m <= 0 || D <= 0) return noalloc_fail(IHSBIN_ERR_INVALID_ARG, "sketch_gram_noalloc: m and D must be positive");
   const size_t cap = kScratchBytes / sizeof(double);
-  if ((size_t)D * (size_t)D > cap)
+  if ((size_t)D > cap / (size_t)D)  // D * D > cap, without forming a product that could wrap
     return noalloc_fail(IHSBIN_ERR_INVALID_ARG,
                         "sketch_gram_noalloc: D*D partial sums exceed the 16 MiB scratch array (D <= 1448)");
   int dev = 0;

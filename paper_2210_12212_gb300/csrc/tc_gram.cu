@@ -60,8 +60,11 @@ constexpr int SL_THREADS = 192;
 
 struct SlicePlan {
   int ns, np, T, RB, KB, nsplit, kbper, D;
+  int rect;   // 1: C = X^T Y of two sliced operands (all tiles of every pair); 0: the symmetric Gram X^T X
+  int TJ;     // column tiles of the result (rect: Y's 128-column tiles; Gram: T)
+  int RBb;    // 128-column tiles of the B-side slice buffer
   int8_t ps[SL_MAX_PAIRS], pt[SL_MAX_PAIRS];
-  int base[SL_MAX_PAIRS + 1];  // first work item of each pair; base[np] = item count
+  int base[SL_MAX_PAIRS + 1];  // first tile of each pair; base[np] = tiles of all pairs (items = tiles x nsplit)
 };
 
 __host__ __device__ __forceinline__ int tile_index(bool diag_pair, int T, int I, int J) {
@@ -164,7 +167,8 @@ __global__ void k_slice(const void* A, int64_t ld, int64_t N, int64_t D, const u
 }
 
 __global__ void __launch_bounds__(SL_THREADS, 1)
-    k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, SlicePlan pl, int* __restrict__ out, int* status, int item0) {
+    k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, const __nv_bfloat16* __restrict__ SB, SlicePlan pl,
+                     int* __restrict__ out, int* status, int item0) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t full[SL_STAGES], empty[SL_STAGES], tfull[2], tempty[2], drained;
   __shared__ uint32_t tmem_base;
@@ -174,11 +178,18 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   // work item -> pair, tile (I, J), row range
   const int item = item0 + blockIdx.x;
   int p = 0;
-  while (p + 1 < pl.np && pl.base[p + 1] <= item) ++p;
+  // item = q * tiles + (tile of pair p): the row split outermost, so that the CTAs running together
+  // work on one row range and share its slice blocks in L2
+  const int tiles_all = pl.base[pl.np];
+  const int q = item / tiles_all, r_item = item - q * tiles_all;
+  while (p + 1 < pl.np && pl.base[p + 1] <= r_item) ++p;
   const int s = pl.ps[p], t = pl.pt[p];
-  const int rel = item - pl.base[p], tile = rel / pl.nsplit, q = rel - tile * pl.nsplit;
+  const int tile = r_item - pl.base[p];
   int I, J;
-  if (s == t) {
+  if (pl.rect) {
+    I = tile / pl.TJ;
+    J = tile - I * pl.TJ;
+  } else if (s == t) {
     I = 0;
     int rest = tile;
     while (rest >= pl.T - I) { rest -= pl.T - I; ++I; }
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
   const __nv_bfloat16* gA = S + (((int64_t)s * pl.RB + I) * pl.KB + kb0) * SL_BLOCK_ELEMS;
-  const __nv_bfloat16* gB = S + (((int64_t)t * pl.RB + J) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  const __nv_bfloat16* gB = SB + (((int64_t)t * pl.RBb + J) * pl.KB + kb0) * SL_BLOCK_ELEMS;
   volatile int* abort_v = &abort_flag;
 
   if (warp == 0) {
@@ -333,11 +344,11 @@ __global__ void k_gram_combine(const int* __restrict__ out, SlicePlan pl, const 
           v = 0;
           w = s + t;
         }
-        const int a = pl.base[p] + tile_index(s == t, pl.T, I, J) * pl.nsplit;
-        for (int q = 0; q < pl.nsplit; ++q) v += out[(int64_t)(a + q) * 16384 + rj * 128 + ri];
+        const int a = pl.base[p] + tile_index(s == t, pl.T, I, J);
+        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * 16384 + rj * 128 + ri];
         if (s != t) {
-          const int b = pl.base[p] + tile_index(false, pl.T, J, I) * pl.nsplit;
-          for (int q = 0; q < pl.nsplit; ++q) v += out[(int64_t)(b + q) * 16384 + ri * 128 + rj];
+          const int b = pl.base[p] + tile_index(false, pl.T, J, I);
+          for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + b) * 16384 + ri * 128 + rj];
         }
       }
       sum += ldexp((double)v, -8 * w);
@@ -354,6 +365,9 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
   pl.D = (int)D;
   pl.RB = (int)((D + 127) / 128);
   pl.T = pl.RB;
+  pl.TJ = pl.T;
+  pl.RBb = pl.RB;
+  pl.rect = 0;
   pl.KB = (int)((N + 63) / 64);
   // pairs s <= t, s + t <= wmax, ordered by weight (largest s + t first)
   pl.np = 0;
@@ -377,23 +391,92 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
   int64_t b = 0;
   for (int p = 0; p < pl.np; ++p) {
     pl.base[p] = (int)b;
-    b += (pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T) * pl.nsplit;
+    b += pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T;
   }
   pl.base[pl.np] = (int)b;
   return pl;
 }
 
+// C = X^T Y for X (N x D, nsa slices per entry) and Y (N x K, nsb slices per entry): every tile of
+// every pair (s, t), s < nsa, t < nsb, s + t <= wmax, pairs ordered by weight (largest first).
+SlicePlan make_rect_plan(int64_t N, int64_t D, int nsa, int64_t K, int nsb, int wmax) {
+  SlicePlan pl{};
+  pl.ns = nsa;
+  pl.D = (int)D;
+  pl.RB = (int)((D + 127) / 128);
+  pl.T = pl.RB;
+  pl.RBb = (int)((K + 127) / 128);
+  pl.TJ = pl.RBb;
+  pl.rect = 1;
+  pl.KB = (int)((N + 63) / 64);
+  pl.np = 0;
+  for (int w = std::min(wmax, nsa + nsb - 2); w >= 0; --w)
+    for (int a = 0; a <= w; ++a) {
+      const int b = w - a;
+      if (a >= nsa || b >= nsb) continue;
+      pl.ps[pl.np] = (int8_t)a;
+      pl.pt[pl.np] = (int8_t)b;
+      ++pl.np;
+    }
+  const int64_t tiles = (int64_t)pl.np * pl.T * pl.TJ;
+  int nsplit = (pl.KB + SL_KB_MAX - 1) / SL_KB_MAX;
+  const int64_t want = (2 * 152 + tiles - 1) / tiles;
+  nsplit = (int)std::max<int64_t>(nsplit, std::min<int64_t>(want, std::max(1, pl.KB / 16)));
+  pl.kbper = (pl.KB + nsplit - 1) / nsplit;
+  pl.nsplit = (pl.KB + pl.kbper - 1) / pl.kbper;
+  for (int q = 0; q <= pl.np; ++q) pl.base[q] = q * pl.T * pl.TJ;
+  return pl;
+}
+
+// c[r][i] (column-major, D x K) = sum over pairs of the integer tiles of X^T Y, scaled by the column
+// exponents of X (i) and Y (r); weights added from the smallest up, as in the Gram's combine.
+template <class Mode>
+__global__ void k_rect_combine(const int* __restrict__ out, SlicePlan pl, const unsigned* __restrict__ cmaxa,
+                               const unsigned* __restrict__ cmaxb, int64_t K, CBuf c) {
+  const int64_t D = pl.D;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= D) return;
+  const int I = (int)(i >> 7), ri = (int)(i & 127);
+  const int ei = col_exp(cmaxa[i]);
+  for (int64_t r = blockIdx.y; r < K; r += gridDim.y) {
+    const int J = (int)(r >> 7), rj = (int)(r & 127);
+    const int ej = col_exp(cmaxb[r]);
+    double g;
+    if (ei == SL_NONFINITE || ej == SL_NONFINITE) {
+      g = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+      double sum = 0.0;
+      int w = pl.ps[0] + pl.pt[0];
+      long long v = 0;
+      for (int p = 0; p < pl.np; ++p) {
+        if (pl.ps[p] + pl.pt[p] != w) {
+          sum += ldexp((double)v, -8 * w);
+          v = 0;
+          w = pl.ps[p] + pl.pt[p];
+        }
+        const int a = pl.base[p] + I * pl.TJ + J;
+        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * 16384 + rj * 128 + ri];
+      }
+      sum += ldexp((double)v, -8 * w);
+      g = ldexp(sum, ei + ej - 14);
+    }
+    Mode::st(c, r * D + i, Mode::from_d(g));
+  }
+}
+
 // G = X^T X for X (N x D, row-major, row stride ld, element type ET) into `G` (Mode precision):
-// ns slices per entry, pairs s + t <= wmax.
+// ns slices per entry, pairs s + t <= wmax.  With Y != nullptr (N x K FP64, row stride K) also
+// c = X^T Y (column-major D x K, Mode precision) from the same slices of X and nsy slices of Y.
 template <class Mode, int ET>
 cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int64_t N, int64_t D, int ns, int wmax,
-                              CBuf G, int cat_slice, int cat_tc, int cat_combine, cudaStream_t st, int max_ctas = 0) {
+                              CBuf G, int cat_slice, int cat_tc, int cat_combine, cudaStream_t st, int max_ctas = 0,
+                              const double* Y = nullptr, int64_t K = 0, int nsy = 0, CBuf c = CBuf{}) {
   struct {
     const void* A;
     int64_t ld;
   } A{X, ld};
   const SlicePlan pl = make_slice_plan(N, D, ns, wmax);
-  const int items = pl.base[pl.np];
+  const int items = pl.base[pl.np] * pl.nsplit;
   unsigned* cmax = nullptr;
   __nv_bfloat16* S = nullptr;
   int* out = nullptr;
@@ -415,7 +498,9 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
     CK(cudaGetLastError());
   }
   {
-    // algorithmic BF16 work of the slice products (unpadded): 2 N per output entry and pair
+    // the method's work: the symmetric Gram, N D (D + 1) flops, one read of X at its storage width;
+    // executed: the BF16 slice products (unpadded, 2 N per output entry and pair) and slice images
+    const double mfl = (double)N * D * (D + 1.0), mby = (double)N * D * es;
     double fl = 0;
     for (int q = 0; q < pl.np; ++q) fl += 2.0 * N * (pl.ps[q] == pl.pt[q] ? D * (D + 1) / 2.0 : (double)D * D);
     const double by = (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536;
@@ -426,8 +511,8 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
     const int chunk = max_ctas > 0 ? std::min(items, max_ctas) : items;
     for (int i0 = 0; i0 < items; i0 += chunk) {
       const int n = std::min(chunk, items - i0);
-      KTimer kt(p, cat_tc, st, fl * n / items, by * n / items);
-      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, pl, out, p->status, i0);
+      KTimer kt(p, cat_tc, st, mfl * n / items, mby * n / items, fl * n / items, by * n / items);
+      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, S, pl, out, p->status, i0);
       CK(cudaGetLastError());
     }
   }
@@ -437,12 +522,52 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
     k_gram_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(out, pl, cmax, G);
     CK(cudaGetLastError());
   }
+  if (!Y) return cudaSuccess;
+  // the right-hand side X^T Y from the same slices of X (step a3)
+  const SlicePlan pr = make_rect_plan(N, D, ns, K, nsy, kGramMaxWeight);
+  const int itr = pr.base[pr.np] * pr.nsplit;
+  unsigned* cmaxy = nullptr;
+  __nv_bfloat16* SY = nullptr;
+  int* outy = nullptr;
+  CK(prob_alloc(p, (size_t)K * sizeof(unsigned), (void**)&cmaxy, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)nsy * pr.RBb * pr.KB * SL_BLOCK_ELEMS * 2, (void**)&SY, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)itr * 16384 * sizeof(int), (void**)&outy, SCOPE_SCRATCH));
+  CK(cudaMemsetAsync(cmaxy, 0, (size_t)K * sizeof(unsigned), st));
+  {
+    KTimer kt(p, K_RHS, st, 0, (double)N * K * 8 * 2 + (double)nsy * pr.RBb * pr.KB * SL_BLOCK_ELEMS * 2);
+    const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, N / 64), 1024);
+    k_col_absmax<ELEM_F64><<<dim3((unsigned)pr.RBb, gy), 128, 0, st>>>(Y, K, N, K, cmaxy);
+    CK(cudaGetLastError());
+    const unsigned gy2 = (unsigned)std::min<int64_t>((int64_t)pr.KB * 8, 32768);
+    k_slice<ELEM_F64><<<dim3((unsigned)pr.RBb, gy2), 128, 0, st>>>(Y, K, N, K, cmaxy, nsy, pr.RBb, pr.KB, SY);
+    CK(cudaGetLastError());
+  }
+  {
+    double fl = 2.0 * pr.np * N * D * K;
+    const double by = ((double)pl.ns * pl.RB + (double)nsy * pr.RBb) * pr.KB * SL_BLOCK_ELEMS * 2 + (double)itr * 65536;
+    const int smem = SL_STAGES * SL_STAGE_BYTES;
+    const int chunk = max_ctas > 0 ? std::min(itr, max_ctas) : itr;
+    for (int i0 = 0; i0 < itr; i0 += chunk) {
+      const int n = std::min(chunk, itr - i0);
+      // the method's work: 2 N D K flops, one read of X and of Y
+      KTimer kt(p, K_RHS, st, 2.0 * N * D * K * n / itr, ((double)N * D * es + (double)N * K * 8) * n / itr,
+                fl * n / itr, by * n / itr);
+      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, SY, pr, outy, p->status, i0);
+      CK(cudaGetLastError());
+    }
+  }
+  {
+    KTimer kt(p, K_RHS, st, 0, (double)itr * 65536 + (double)D * K * 8);
+    const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, K), 1024);
+    k_rect_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(outy, pr, cmax, cmaxy, K, c);
+    CK(cudaGetLastError());
+  }
   return cudaSuccess;
 }
 
 }  // namespace
 
-cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms) {
+cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms, CBuf* rhs) {
   const Tall& A = p->A;
   const int et = A.elem;
   const int cs = K_GRAM_SLICE, ct = K_GRAM_TC, cc = K_GRAM_COMBINE;
@@ -452,13 +577,21 @@ cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, i
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       mc = std::max(1, sms - reserve_sms);
   }
+  const int ns = gram_slices_for(et);
+  const double* Y = rhs ? p->B : nullptr;
+  const int64_t K = rhs ? p->K : 0;
+  const CBuf c = rhs ? *rhs : CBuf{};
   if (compute == IHSBIN_COMPUTE_F64)
     return et == ELEM_F32
-               ? gram_slices_typed<F64, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc)
-               : gram_slices_typed<F64, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc);
+               ? gram_slices_typed<F64, ELEM_F32>(p, A.A, A.ld, A.N, A.D, ns, kGramMaxWeight, p->G, cs, ct, cc, st, mc,
+                                                  Y, K, kRhsSlices, c)
+               : gram_slices_typed<F64, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, ns, kGramMaxWeight, p->G, cs, ct, cc, st, mc,
+                                                   Y, K, kRhsSlices, c);
   return et == ELEM_F32
-             ? gram_slices_typed<DD, ELEM_F32>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc)
-             : gram_slices_typed<DD, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, kGramSlices, kGramMaxWeight, p->G, cs, ct, cc, st, mc);
+             ? gram_slices_typed<DD, ELEM_F32>(p, A.A, A.ld, A.N, A.D, ns, kGramMaxWeight, p->G, cs, ct, cc, st, mc, Y,
+                                               K, kRhsSlices, c)
+             : gram_slices_typed<DD, ELEM_BF16>(p, A.A, A.ld, A.N, A.D, ns, kGramMaxWeight, p->G, cs, ct, cc, st, mc, Y,
+                                                K, kRhsSlices, c);
 }
 
 // G_S = (S A_hat)^T (S A_hat) of the FP64 sketch: seven slices (55 bits) and pairs s + t <= 7, so
@@ -470,8 +603,8 @@ cudaError_t sketch_gram_slices(ihsbin_problem* p, cudaStream_t st) {
 }
 
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D) {
-  const SlicePlan pl = make_slice_plan(N, D, kGramSlices, kGramMaxWeight);
-  return (uint64_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (uint64_t)pl.base[pl.np] * 65536 + (uint64_t)D * 4;
+  const SlicePlan pl = make_slice_plan(N, D, kGramSlices, kGramMaxWeight);  // the FP32 count bounds the BF16 one
+  return (uint64_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (uint64_t)pl.base[pl.np] * pl.nsplit * 65536 + (uint64_t)D * 4;
 }
 
 }  // namespace ihsbin

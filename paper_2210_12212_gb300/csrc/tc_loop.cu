@@ -1033,14 +1033,24 @@ struct ColGeom {
   int KB, CL, KBC, threads;
   size_t smem;
 };
-inline ColGeom col_geom(int64_t D) {
+inline ColGeom col_geom(int64_t D, int CL) {
   ColGeom g;
   g.KB = oz_kb(D);
-  g.CL = std::min(8, std::max(1, g.KB));
+  g.CL = std::min(CL, std::max(1, g.KB));
   g.KBC = (g.KB + g.CL - 1) / g.CL;
   g.threads = std::min(g.KBC * OZ_BK, OZ_COL_THREADS_MAX);
   g.smem = (size_t)g.KBC * OZ_BK * 2 * sizeof(float);
   return g;
+}
+
+// Cluster sizes the autotuner tries for a per-column launch (every one gives the same values):
+// 8, 4, 2, 1 CTAs per column, as far as the column has k-blocks.
+inline int col_cands(int64_t D, int* c) {
+  const int KB = oz_kb(D);
+  int n = 0;
+  for (int cl = 8; cl >= 1; cl /= 2)
+    if (cl <= KB || cl == 1) c[n++] = cl;
+  return n;
 }
 
 cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
@@ -1048,30 +1058,57 @@ cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, 
                             const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
                             __nv_bfloat16* Rs, int* er, cudaStream_t st) {
   const int NTL = (int)((nnew + NT - 1) / NT);
-  const ColGeom cg_ = col_geom(D);
-  return launch_pdl_cluster(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT * cg_.CL)), dim3(cg_.threads),
-                            cg_.smem, cg_.CL, st, Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau,
-                            lam0, gs, NT, NTL, cg_.KB, cg_.KBC, Rs, er);
+  int cands[4];
+  const int nc = col_cands(D, cands);
+  TuneLaunch t = tune_begin(tune_key(TUNE_COL_R, D, shape_class((int64_t)live * NTL * NT), 0), "col_R_cluster",
+                            cands, nc, st);
+  const ColGeom cg_ = col_geom(D, t.value);
+  if (cg_.smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_make_R_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cg_.smem));
+  const cudaError_t e =
+      launch_pdl_cluster(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT * cg_.CL)), dim3(cg_.threads),
+                         cg_.smem, cg_.CL, st, Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau,
+                         lam0, gs, NT, NTL, cg_.KB, cg_.KBC, Rs, er);
+  tune_end(t, st);
+  return e;
 }
 
 cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
                             const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
                             CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
                             int* eu, cudaStream_t st) {
-  const ColGeom cg_ = col_geom(D);
-  return launch_pdl_cluster(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
-                            cg_.smem, cg_.CL, st, Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut,
-                            perm, gs, live_next, NTn, cg_.KB, cg_.KBC, Us, eu);
+  int cands[4];
+  const int nc = col_cands(D, cands);
+  TuneLaunch t = tune_begin(tune_key(TUNE_COL_UPDATE, D, shape_class((int64_t)live * ncol), 0), "col_update_cluster",
+                            cands, nc, st);
+  const ColGeom cg_ = col_geom(D, t.value);
+  if (cg_.smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_update_oz_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cg_.smem));
+  const cudaError_t e =
+      launch_pdl_cluster(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
+                         cg_.smem, cg_.CL, st, Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut,
+                         perm, gs, live_next, NTn, cg_.KB, cg_.KBC, Us, eu);
+  tune_end(t, st);
+  return e;
 }
 
 cudaError_t oz_update_mw_slice(const long long* Phi, const long long* Plo, int S, const int* em, const int* ep,
                                int live, int64_t ncol, int64_t D, int64_t K, CBuf Uin, CBuf Uout, CBuf Ut,
                                const int* perm, const double* tau, const double* lam0, int64_t gs, const int* eu_in,
                                int live_next, __nv_bfloat16* Us, int* eu, cudaStream_t st) {
-  const ColGeom cg_ = col_geom(D);
-  return launch_pdl_cluster(k_update_mw_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
-                            cg_.smem, cg_.CL, st, Phi, Plo, S, em, ep, (int64_t)oz_rows_exps(D), live, ncol, D, K, Uin,
-                            Uout, Ut, perm, tau, lam0, gs, eu_in, live_next, cg_.KB, cg_.KBC, Us, eu);
+  int cands[4];
+  const int nc = col_cands(D, cands);
+  TuneLaunch t = tune_begin(tune_key(TUNE_COL_MW, D, shape_class((int64_t)live * ncol), 0), "col_mw_cluster", cands,
+                            nc, st);
+  const ColGeom cg_ = col_geom(D, t.value);
+  if (cg_.smem > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_update_mw_slice, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cg_.smem));
+  const cudaError_t e =
+      launch_pdl_cluster(k_update_mw_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
+                         cg_.smem, cg_.CL, st, Phi, Plo, S, em, ep, (int64_t)oz_rows_exps(D), live, ncol, D, K, Uin,
+                         Uout, Ut, perm, tau, lam0, gs, eu_in, live_next, cg_.KB, cg_.KBC, Us, eu);
+  tune_end(t, st);
+  return e;
 }
 
 cudaError_t oz_make_M(const long long* hi, const long long* lo, int S, int64_t D, int T, const int* eg, const int* epc,

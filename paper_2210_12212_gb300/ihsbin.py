@@ -60,7 +60,8 @@ class PathDesc(C.Structure):
                 ("k", C.c_void_p), ("k_default", C.c_int32), ("rho1", C.c_void_p),
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
                 ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
-                ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int), ("sigma_d2", C.c_double)]
+                ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int), ("sigma_d2", C.c_double),
+                ("tau", C.c_void_p)]
 
 
 class AdaptiveDesc(C.Structure):
@@ -94,6 +95,7 @@ EXPORTED = [
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
     "ihsbin_path_losses", "ihsbin_adaptive_sketch", "ihsbin_sketch_entries_export", "ihsbin_kernel_exec",
+    "ihsbin_ctx_fail_allocations", "ihsbin_tuning_report", "ihsbin_tuning_reset",
 ]
 KCAT_COUNT = 40
 
@@ -128,6 +130,9 @@ def load(path: Optional[str] = None):
         "ihsbin_reset_stats": [vp],
         "ihsbin_kernel_stats": [vp, i32, vp, vp, vp, vp, vp],
         "ihsbin_kernel_exec": [vp, i32, vp, vp],
+        "ihsbin_ctx_fail_allocations": [vp, i64],
+        "ihsbin_tuning_report": [vp, i64, C.POINTER(i64)],
+        "ihsbin_tuning_reset": [],
         "ihsbin_sketch_gram_noalloc": [vp, i64, i64, vp, vp],
         "ihsbin_request_footprint": [C.POINTER(Request), C.POINTER(C.c_uint64)],
         "ihsbin_serve_create": [vp, C.POINTER(ServeConfig), C.POINTER(vp)],
@@ -184,6 +189,10 @@ class Context:
         v = C.c_uint64()
         _check(_lib.ihsbin_ctx_memory(self.h, C.byref(v)))
         return v.value
+
+    def fail_allocations(self, after: int):
+        """Test hook: after `after` more successful device allocations every one fails (< 0: off)."""
+        _check(_lib.ihsbin_ctx_fail_allocations(self.h, after))
 
     def close(self):
         if self.h:
@@ -243,7 +252,8 @@ class Problem:
                     rho1: Optional[Sequence[float]] = None, rho2: Optional[Sequence[float]] = None,
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
                     eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", loop: str = "auto",
-                    factor: str = "auto", sigma_d2: float = 0.0, stream=None):
+                    factor: str = "auto", sigma_d2: float = 0.0, tau: Optional[Sequence[float]] = None,
+                    stream=None):
         """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
         gram / loop / factor select the Gram kernel, the recursion's product kernel and the inverse's
         product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
@@ -262,6 +272,8 @@ class Problem:
         pd.loop = LOOP[loop]
         pd.factor = FACTOR[factor]
         pd.sigma_d2 = sigma_d2
+        ta = np.ascontiguousarray(tau, dtype=np.float64) if tau is not None else None
+        pd.tau = _ptr(ta)
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",
@@ -434,6 +446,19 @@ class Problem:
 
 
 # --------------------------------------------------------------------------- serving
+def tuning_report() -> str:
+    """The autotuner's table: one line per tuned launch site and shape class."""
+    need = C.c_int64()
+    _check(_lib.ihsbin_tuning_report(None, 0, C.byref(need)))
+    buf = C.create_string_buffer(max(1, need.value))
+    _check(_lib.ihsbin_tuning_report(buf, need.value, C.byref(need)))
+    return buf.value.decode()
+
+
+def tuning_reset():
+    _check(_lib.ihsbin_tuning_reset())
+
+
 def _matrix(A=None, *, dtype="f32", csr=None, shape=None, keep=None):
     m = Matrix()
     if csr is not None:

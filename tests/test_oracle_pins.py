@@ -221,6 +221,23 @@ def test_bin_equals_k_ihs_steps(m):
         assert np.allclose(ob.evaluate(ut, tau, lam0, lam), want, rtol=1e-10, atol=1e-12)
 
 
+@pytest.mark.parametrize("jmax", [1, 4, 9])
+def test_truncated_basis_keeps_its_terms(jmax):
+    # u_j is updated from u_j and u_{j-1} only, so the terms j < jmax are the full basis's terms,
+    # and the truncated expansion differs from k IHS steps only by the omitted terms.
+    A, B = rand_problem(60, 12, K=2, seed=jmax)
+    SA = sk.apply_gaussian(A, 30, 5)
+    lo, hi = 0.02, 0.06
+    lam0 = math.sqrt(lo * hi)
+    tau = ob.step_size(lo, hi, 1.8, 0.3)
+    P = ob.precond(SA.T @ SA, lam0)
+    c = A.T @ B
+    full = ob.basis(ob.aspace_operator(A), P, c, tau, 14)
+    cut = ob.basis(ob.aspace_operator(A), P, c, tau, 14, jmax=jmax)
+    assert cut.shape[0] == jmax
+    np.testing.assert_allclose(cut, full[:jmax], rtol=1e-13, atol=1e-15 * np.abs(full).max())
+
+
 def test_recentred_equals_printed_form_small_k():
     A, B = rand_problem(40, 6, seed=9)
     SA = sk.apply_srht(A, 16, 3)

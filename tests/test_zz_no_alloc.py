@@ -50,3 +50,33 @@ def test_noalloc_rejects_oversized_problem(lib):
     st = lib.ihsbin_sketch_gram_noalloc(SA.data_ptr(), 4, D, GS.data_ptr(), None)
     assert st == ihs.ERR_INVALID_ARG
     assert b"scratch" in lib.ihsbin_last_error()
+
+
+def test_noalloc_largest_size_allocates_nothing(lib):
+    """D = 1448, the largest D whose partial sums fit: the split count is cut to one, and the call
+    leaves the device's free memory unchanged (measured around a second call; the first one may
+    load the library's device code)."""
+    import torch
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    D, m = 1448, 8
+    SA = np.random.default_rng(7).standard_normal((m, D))
+    want = SA.T @ SA
+    SA_dev = torch.from_numpy(SA).cuda()
+    GS_dev = torch.full((D, D), float("nan"), dtype=torch.float64, device="cuda")
+    for call in range(2):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        st = lib.ihsbin_sketch_gram_noalloc(SA_dev.data_ptr(), m, D, GS_dev.data_ptr(), None)
+        assert st == ihs.OK, lib.ihsbin_last_error()
+        torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0
+        np.testing.assert_allclose(GS_dev.cpu().numpy(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+
+
+def test_noalloc_rejects_huge_dimension_without_wrapping(lib):
+    import torch
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    buf = torch.zeros(16, dtype=torch.float64, device="cuda")
+    st = lib.ihsbin_sketch_gram_noalloc(buf.data_ptr(), 1, 1 << 32, buf.data_ptr(), None)  # D * D wraps to 0
+    assert st == ihs.ERR_INVALID_ARG
