@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--auto", action="store_true",
                     help="parameters from the sketch (rho from d_e, k from Theorem 4 at --eps) on both sides")
     ap.add_argument("--eps", type=float, default=1e-7)
-    ap.add_argument("--requests", type=int, default=128, help="serving workload (c5): number of requests")
+    ap.add_argument("--requests", type=int, default=4096, help="serving workload (c5): number of requests")
     ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
     ap.add_argument("--adaptive", type=int, default=0, metavar="M0",
                     help="a step starts with Algorithm 4 from sketch dimension M0 at lambda_min (the path then "
@@ -231,11 +231,15 @@ def oracle_sample(prob, par, jmax=0, target_s=1.5, A=None):
 
 
 def oracle_matrix(prob):
-    """A as the oracle consumes it: FP64 dense, or scipy CSR for sparse workloads."""
+    """A as the oracle consumes it: FP64 dense, or scipy CSR for sparse workloads (TF32 storage
+    rounded by the oracle's TF32 rounding first)."""
+    from oracle.precision import round_tf32
+    tf32 = prob.storage == "tf32"
     if prob.layout == "csr":
         import scipy.sparse as sp
-        return sp.csr_matrix((prob.val.astype(np.float64), prob.col_idx, prob.row_ptr), shape=(prob.n, prob.d))
-    return prob.dense_f64()
+        val = round_tf32(prob.val) if tf32 else prob.val
+        return sp.csr_matrix((val.astype(np.float64), prob.col_idx, prob.row_ptr), shape=(prob.n, prob.d))
+    return round_tf32(prob.A).astype(np.float64) if tf32 else prob.dense_f64()
 
 
 def config_for(args, prob, par, world=1):
@@ -362,10 +366,15 @@ def serving_arm(args):
         return dict(wall=wall, lat=lat, res=res, outs=outs)
 
     served = run("f32x2", args.slots)
+    note("served run done")
     fifo = run("f64", 1)
+    note("FIFO run done")
     errs = [float(np.max(np.linalg.norm((a - b).reshape(len(a), -1), axis=1)
                          / np.maximum(np.linalg.norm(b.reshape(len(b), -1), axis=1), 1e-300)))
             for a, b in zip(served["outs"], fifo["outs"])]
+    # a sample of served results against the FP64 oracle (its own sketch-derived plan, as the library's)
+    oracle_check = serving_oracle_sample(reqs, served["outs"], big, n_each=3)
+    note("oracle sample done")
 
     def summary(r):
         lat = np.sort(r["lat"])
@@ -378,8 +387,44 @@ def serving_arm(args):
             "data": "synthetic", "config": {"workload": WORKLOADS["c5"], "requests": args.requests,
                                             "slots": args.slots, "budget_gb": 120},
             "served_f32x2": summary(served), "fifo_f64": summary(fifo),
-            "max_rel_err_served_vs_fp64": max(errs)}
+            "max_rel_err_served_vs_fp64": max(errs), "oracle_sample": oracle_check}
     print(json.dumps(line), flush=True)
+
+
+def serving_oracle_sample(reqs, outs, big, n_each=3):
+    """The n_each smallest dense and CSR requests of the trace through the FP64 oracle, with the plan
+    the oracle derives from its own sketch (rho from d_e, k from Theorem 4 at eps = 1e-7): max
+    relative error of the served x(lambda) over each request's lambdas."""
+    import scipy.sparse as sp
+    from oracle import ihsbin as ob
+    from oracle import sketch as osk
+    res = []
+    for kind in ("dense", "csr"):
+        idx = sorted((i for i, e in enumerate(reqs) if e["kind"] == kind), key=lambda i: reqs[i]["n"] * reqs[i]["d"])
+        for i in idx[:n_each]:
+            e = reqs[i]
+            n, d = e["n"], e["d"]
+            if kind == "dense":
+                A = big[:n, :d].astype(np.float64)
+                sk, s = "srht", 1
+            else:
+                rp, ci, va = e["csr"]
+                A = sp.csr_matrix((va.astype(np.float64), ci, rp), shape=(n, d))
+                sk, s = "countsketch", 1
+            m = 2 * min(n, d)
+            B = e["b"].reshape(-1, 1)
+            Ahat, c, _ = ob.tall_form(A, B)
+            SA = osk.apply(sk, Ahat, m, s, 7)
+            GS = SA.T @ SA
+            lam = e["lambdas"]
+            plan = ob.auto_plan(GS, m, lam[0], lam[-1], eps=1e-7)
+            X = ob.ihs_bin_path(A, B, sk, m, s, 7, plan, lam).X
+            got = outs[i].reshape(X.shape)
+            err = float(np.max(np.linalg.norm((got - X).reshape(len(X), -1), axis=1)
+                               / np.linalg.norm(X.reshape(len(X), -1), axis=1)))
+            res.append({"request": i, "kind": kind, "n": n, "d": d, "T": len(lam), "max_rel_err": err})
+    return {"requests": res, "max_rel_err": max(r["max_rel_err"] for r in res), "pass": all(r["max_rel_err"] <= 1e-6
+                                                                                            for r in res)}
 
 
 _T0 = time.perf_counter()
@@ -553,6 +598,18 @@ def main():
     dom = max(stats.items(), key=lambda kv: kv[1][1])
     name, (launches, ms, flops, byts) = dom
     bound, peak, peak_note = kernel_peak(name, args.compute)
+    xf0, xb0 = xstats.get(name, (flops, byts))
+    if (xf0, xb0) != (flops, byts) and ms > 0:
+        # an exact-slice product: its bound is the resource its executed work uses most (the tensor pipe
+        # for wide column panels, HBM for the slice images of thin ones)
+        ft = xf0 / (ms * 1e-3) / 1e12 / measured_peak("bf16_tflops_sustained", 1700.0)[0]
+        fh = xb0 / (ms * 1e-3) / 1e9 / measured_peak("hbm_gbs", 6800.0)[0]
+        if ft >= fh:
+            peak, how = measured_peak("bf16_tflops_sustained", 1700.0)
+            bound, peak_note = "tensor", f"cuBLAS bf16 sustained (MEASURED_PEAKS.json), {how}"
+        else:
+            peak, how = measured_peak("hbm_gbs", 6800.0)
+            bound, peak_note = "hbm", f"copy bandwidth (MEASURED_PEAKS.json hbm_gbs), {how}"
     if bound == "hbm":
         achieved, unit = (byts / (ms * 1e-3) / 1e9 if ms > 0 else 0.0), "GB/s"
     else:

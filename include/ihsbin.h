@@ -58,8 +58,10 @@ typedef enum {
   IHSBIN_ERR_NAN = 11          /* a non-finite value was produced on the device          */
 } ihsbin_status;
 
-/* Element type of caller-provided arrays. */
-typedef enum { IHSBIN_F64 = 0, IHSBIN_F32 = 1, IHSBIN_BF16 = 2 } ihsbin_dtype;
+/* Element type of caller-provided arrays.  IHSBIN_TF32 (the data matrix only): FP32 storage whose
+ * values enter the method rounded to TF32 (10 fraction bits, to nearest, ties away from zero);
+ * the library rounds a copy of A at problem creation and solves the problem of the rounded data. */
+typedef enum { IHSBIN_F64 = 0, IHSBIN_F32 = 1, IHSBIN_BF16 = 2, IHSBIN_TF32 = 3 } ihsbin_dtype;
 
 /* Arithmetic of the accuracy-critical contractions (Gram, preconditioner,
  * basis loop, right-hand side, path evaluation):
@@ -203,6 +205,10 @@ typedef struct {
   const double* tau; /* NULL: tau_l from Theorem 4's rule above; else an array of L explicit steps (each finite
                       * and > 0; needs L > 0), for callers who tuned them (Theorem 4's rho are not computable
                       * from data in practice); rho1/rho2 still set k_l when k is NULL and k_default <= 0 */
+  int32_t slice_weight; /* SLICES loop / factor kernels only: the slice pairs (s, t) with s + t <= slice_weight
+                         * are kept (0 selects 6, the float-float accuracy class; 4 or 5 drop the pairs
+                         * weighing below 2^-40 / 2^-48 of an entry's leading product, 1.8x / 1.3x fewer
+                         * tensor-core products; the Gram of A keeps every pair it needs regardless) */
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;

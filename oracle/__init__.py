@@ -16,4 +16,4 @@ Parity status: all routines are pinned by ``tests/test_oracle_pins.py``
 (closed forms, textbook routines on tiny inputs, brute force, invariants and
 the published Philox known-answer vectors); none is "parity unpinned".
 """
-from . import philox, sketch, ihsbin  # noqa: F401,E402
+from . import philox, sketch, ihsbin, precision  # noqa: F401,E402

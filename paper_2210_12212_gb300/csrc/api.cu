@@ -27,7 +27,7 @@ ihsbin_status cuda_fail(cudaError_t e, const char* where) {
 
 thread_local std::vector<DevBuf>* g_scratch = nullptr;
 
-size_t elem_size(int dt) { return dt == IHSBIN_F64 ? 8 : dt == IHSBIN_F32 ? 4 : 2; }
+size_t elem_size(int dt) { return dt == IHSBIN_F64 ? 8 : (dt == IHSBIN_F32 || dt == IHSBIN_TF32) ? 4 : 2; }
 
 void free_list(ihsbin_problem* p, std::vector<DevBuf>& v) {
   std::lock_guard<std::mutex> g(p->ctx->mu);
@@ -266,7 +266,7 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
   if (!ctx || !A || !B || !out) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: NULL argument");
   *out = nullptr;
   if (A->n <= 0 || A->d <= 0 || K <= 0 || ldb < K) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad sizes");
-  if (A->dtype < IHSBIN_F64 || A->dtype > IHSBIN_BF16) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad dtype");
+  if (A->dtype < IHSBIN_F64 || A->dtype > IHSBIN_TF32) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad dtype");
   if (b_dtype != IHSBIN_F64 && b_dtype != IHSBIN_F32) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: B must be F64 or F32");
   if (A->layout == IHSBIN_DENSE_ROWMAJOR) {
     if (!A->values || A->ld < A->d) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: dense values NULL or ld < d");
@@ -294,7 +294,8 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
   const size_t es = elem_size(A->dtype);
   Tall& T = p->A;
   T.layout = A->layout;
-  T.elem = A->dtype == IHSBIN_F64 ? ELEM_F64 : A->dtype == IHSBIN_F32 ? ELEM_F32 : ELEM_BF16;
+  T.elem = A->dtype == IHSBIN_F64 ? ELEM_F64 : (A->dtype == IHSBIN_F32 || A->dtype == IHSBIN_TF32) ? ELEM_F32 : ELEM_BF16;
+  p->tf32 = A->dtype == IHSBIN_TF32;
   if ((e = prob_alloc(p, sizeof(int), (void**)&p->status, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
   cudaMemset(p->status, 0, sizeof(int));
   if (A->layout == IHSBIN_DENSE_ROWMAJOR) {
@@ -306,6 +307,15 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
       e = cudaMemcpy2D(dptr, A->d * es, A->values, A->ld * es, A->d * es, A->n, cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return bail(e, "problem_create");
       src = dptr;
+      ld = A->d;
+    }
+    if (p->tf32) {  // the values the method takes: a rounded copy (in place when the copy is ours)
+      float* rptr = (float*)(A->on_device ? nullptr : src);
+      if (!rptr && (e = prob_alloc(p, (size_t)A->n * A->d * 4, (void**)&rptr, SCOPE_PERSIST)) != cudaSuccess)
+        return bail(e, "problem_create");
+      if ((e = launch_round_tf32((const float*)src, ld, A->n, A->d, rptr, 0)) != cudaSuccess)
+        return bail(e, "problem_create");
+      src = rptr;
       ld = A->d;
     }
     if (!p->dual) {
@@ -341,6 +351,14 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
       rp = (const int64_t*)drp;
       ci = (const int32_t*)dci;
       val = dval;
+    }
+    if (p->tf32) {  // rounded values (in place when the copy is ours)
+      float* rval = (float*)(A->on_device ? nullptr : val);
+      if (!rval && (e = prob_alloc(p, (size_t)std::max<int64_t>(1, A->nnz) * 4, (void**)&rval, SCOPE_PERSIST)) != cudaSuccess)
+        return bail(e, "problem_create");
+      if ((e = launch_round_tf32((const float*)val, A->nnz, 1, A->nnz, rval, 0)) != cudaSuccess)
+        return bail(e, "problem_create");
+      val = rval;
     }
     int64_t* trp = nullptr;
     int32_t* tci = nullptr;
@@ -545,6 +563,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   if (!(d->sigma_d2 >= 0) || !std::isfinite(d->sigma_d2))
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: sigma_d2 must be finite and >= 0");
   if (d->tau && !(d->L > 0)) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: an explicit tau array needs L > 0");
+  if (d->slice_weight != 0 && (d->slice_weight < 4 || d->slice_weight > 6))
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: slice_weight must be 0 or 4..6");
   if (d->compute != IHSBIN_COMPUTE_F64 && d->compute != IHSBIN_COMPUTE_F32X2)
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown compute mode");
   Plan pl;
@@ -567,6 +587,7 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.rho1.resize(L);
   pl.rho2.resize(L);
   pl.sigma_d2 = d->sigma_d2;
+  pl.slice_w = d->slice_weight > 0 ? d->slice_weight : 6;
   if (d->tau) {
     pl.tau_user.assign(d->tau, d->tau + L);
     for (double t : pl.tau_user)
@@ -778,7 +799,7 @@ ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64
     if (A_test->layout != IHSBIN_DENSE_ROWMAJOR) return fail(IHSBIN_ERR_UNSUPPORTED, "path_losses: A_test must be dense");
     if (A_test->d != p->d || A_test->n <= 0 || A_test->ld < A_test->d || !A_test->values)
       return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: A_test must be n_test x d with ld >= d");
-    if (A_test->dtype < IHSBIN_F64 || A_test->dtype > IHSBIN_BF16)
+    if (A_test->dtype < IHSBIN_F64 || A_test->dtype > IHSBIN_BF16)  // (TF32 test rows are not taken)
       return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: bad A_test dtype");
     if (b_test_dtype != IHSBIN_F64 && b_test_dtype != IHSBIN_F32)
       return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: B_test must be F64 or F32");

@@ -51,6 +51,7 @@ struct Plan {
   int gram = IHSBIN_GRAM_FMA;   // resolved Gram kernel (never AUTO)
   int loop = IHSBIN_LOOP_FMA;   // resolved product kernel of the basis recursion (never AUTO)
   int factor = IHSBIN_FACTOR_FMA;  // resolved kernel of the explicit inverse (never AUTO)
+  int slice_w = 6;                 // slice pairs kept by the recursion's and the inverse's products
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
@@ -87,6 +88,7 @@ struct ihsbin_problem {
   int64_t n = 0, d = 0, K = 0;
   bool dual = false;
   ihsbin::Tall A;
+  bool tf32 = false;                     // A's values were rounded to TF32 (held as FP32)
   std::vector<ihsbin::DevBuf> owned;     // every device allocation of this problem
   double* B = nullptr;                   // n x K (FP64, device)
   int* status = nullptr;                 // device status word
@@ -201,7 +203,9 @@ constexpr int kGramSlices = 6;     // BF16 slices per FP32 entry
 constexpr int kGramSlicesBf16 = 4; // BF16 slices per BF16 entry (every entry within 2^-23 of its column maximum exact)
 constexpr int kGramMaxWeight = 6;  // slice pairs (s, t) kept: s + t <= kGramMaxWeight
 constexpr int kRhsSlices = 6;      // BF16 slices per FP64 entry of B in the right-hand side A_hat^T B
-inline int gram_slices_for(int elem) { return elem == ELEM_BF16 ? kGramSlicesBf16 : kGramSlices; }
+inline int gram_slices_for(int elem, bool tf32) { return elem == ELEM_BF16 || tf32 ? kGramSlicesBf16 : kGramSlices; }
+// FP32 values rounded to TF32 (to nearest, ties away from zero): rows x cols with row stride ld -> dst (stride cols)
+cudaError_t launch_round_tf32(const float* src, int64_t ld, int64_t rows, int64_t cols, float* dst, cudaStream_t st);
 // reserve_sms > 0: the tensor-core launches leave that many SMs free (for work on other streams);
 // rhs != nullptr: also c = A_hat^T B (column-major D x K) from the same slices of A_hat
 cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms = 0,
@@ -225,8 +229,8 @@ int oz_pick_split(int64_t D, int64_t ncolg, int groups, int NT, int cap);
 // writes the exact int64 partials ohi / olo (see oz_join in common.cuh), entry ((s * groups + g) * ncolg + j) * D + i
 cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
                        const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
-                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st);
-double oz_pair_flops(int64_t M, int64_t N, int64_t K);
+                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st, int wmax = 6);
+double oz_pair_flops(int64_t M, int64_t N, int64_t K, int wmax = 6);
 
 // General form: C_g = X_g Y_g^T (M x N, contraction K) for every group g, X sliced into 128-row
 // tiles (A operand), Y into NT-row tiles (NT = 16 or 32, B operand).  Triangular operands: zero
@@ -250,6 +254,7 @@ struct OzGemm {
   long long* ohi = nullptr;  // exact partials, entry ((s * groups + g) * N + j) * M + i
   long long* olo = nullptr;
   int* status = nullptr;
+  int wmax = 6;              // slice pairs kept: s + t <= wmax (4 .. 6)
 };
 cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st);
 // the recursion's update in the two-product form (partials of M_q U and P_l U from a pair-mode product)

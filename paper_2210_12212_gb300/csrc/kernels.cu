@@ -33,6 +33,22 @@ __global__ void k_convert_f64(const void* src, int elem, int64_t rows, int64_t c
   dst[i] = load_elem_d(src, elem, r * ld + c);
 }
 
+// TF32 by the tensor cores' own conversion (cvt.rna: to nearest, ties away from zero)
+__global__ void k_round_tf32(const float* src, int64_t ld, int64_t rows, int64_t cols, float* dst) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t r = e / cols, c = e - r * cols;
+  uint32_t t;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(src[r * ld + c]));
+  dst[e] = __uint_as_float(t);
+}
+
+cudaError_t launch_round_tf32(const float* src, int64_t ld, int64_t rows, int64_t cols, float* dst, cudaStream_t st) {
+  if (rows * cols == 0) return cudaSuccess;
+  k_round_tf32<<<nblocks(rows * cols, 256), 256, 0, st>>>(src, ld, rows, cols, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_to_f64(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
                                   double* dst, cudaStream_t st) {
   if (rows * cols == 0) return cudaSuccess;
@@ -1149,12 +1165,13 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
     const int S = oz_pick_split_mnk(nR, B, nR, L, 32, 16);
     {
       OzGemm q;
+      q.wmax = p->plan.slice_w;
       q.As = Xs; q.ea = ex; q.Bs = Ys; q.eb = ey;
       q.M = nR; q.N = B; q.K = nR; q.groups = L; q.NT = 32; q.ksplit = S;
       q.tri = OZ_TRI_LE_ROW;
       q.ohi = hi; q.olo = lo; q.status = p->status;
       KTimer kt(p, K_TRTRI_TC, st, 2.0 * L * (nR * (nR + 1.0) / 2.0) * B, (double)L * (nR * nR / 2.0 + 2.0 * nR * B) * 8,
-                oz_pair_flops(1, 1, 1) * L * (nR * (nR + 1.0) / 2.0) * B,
+                oz_pair_flops(1, 1, 1, p->plan.slice_w) * L * (nR * (nR + 1.0) / 2.0) * B,
                 (double)L * (oz_vec_elems(nR, nR, 128) + oz_vec_elems(B, nR, 32)) * 2 + 16.0 * S * L * nR * B);
       CK(oz_gemm(q, st));
     }
@@ -1216,11 +1233,12 @@ static cudaError_t panel_update(ihsbin_problem* p, CBuf H, const PanelUpdate& u,
   }
   {
     OzGemm q;
+    q.wmax = p->plan.slice_w;
     q.As = u.Xs; q.ea = u.ea; q.Bs = u.Ys; q.eb = u.eb;
     q.M = M; q.N = M; q.K = w; q.groups = L; q.NT = 32; q.ksplit = 1; q.sym = 1;
     q.ohi = u.hi; q.olo = u.lo; q.status = p->status;
     KTimer kt(p, K_SYRK_TC, st, 2.0 * L * (M * (M + 1.0) / 2.0) * w, (double)L * (M * w + M * (M + 1.0) / 2.0) * 8,
-              oz_pair_flops(1, 1, 1) * L * (M * (M + 1.0) / 2.0) * w,
+              oz_pair_flops(1, 1, 1, p->plan.slice_w) * L * (M * (M + 1.0) / 2.0) * w,
               (double)L * (oz_vec_elems(M, w, 128) + oz_vec_elems(M, w, 32)) * 2 + 16.0 * L * M * M);
     CK(oz_gemm(q, st));
   }
@@ -1268,13 +1286,14 @@ static cudaError_t inverse_slices(ihsbin_problem* p, CBuf Wm, cudaStream_t st) {
   }
   {
     OzGemm q;
+    q.wmax = p->plan.slice_w;
     q.As = As; q.ea = ea; q.Bs = Bs; q.eb = eb;
     q.M = D; q.N = D; q.K = D; q.groups = L; q.NT = 32; q.ksplit = 1;
     q.tri = OZ_TRI_GE_ROW | OZ_TRI_GE_COL;
     q.sym = 1;
     q.ohi = hi; q.olo = lo; q.status = p->status;
     KTimer kt(p, K_INVERSE_TC, st, (double)L * D * (D + 1.0) * (D + 2.0) / 3.0, (double)L * D * D * 8,
-              oz_pair_flops(1, 1, 1) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
+              oz_pair_flops(1, 1, 1, p->plan.slice_w) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
               (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2 + (double)L * D * D * 16);
     CK(oz_gemm(q, st));
   }
@@ -1673,13 +1692,14 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       int* eu_out = parity ? oz.eb : oz.eb2;
       {
         OzGemm q;
+        q.wmax = p->plan.slice_w;
         q.As = oz.Ms; q.As2 = oz.Ps; q.a_perm2 = perm_dev; q.pair = 1;
         q.Bs = oz.Bs;
         q.M = D; q.N = ncol; q.K = D; q.groups = 2 * live; q.NT = 16; q.ksplit = ks;
         q.ohi = oz.Zhi; q.olo = oz.Zlo; q.status = p->status;
         // the method's step: G U (G read once) and P_l R (each live P_l once); M_l is the implementation's
         KTimer kt(p, K_LOOP_P_TC, st, 4.0 * D * D * ncol * live, (double)(live + 1) * D * D * 8 + 16.0 * D * ncol * live,
-                  2.0 * oz_pair_flops(D, ncol, D) * live,
+                  2.0 * oz_pair_flops(D, ncol, D, pl.slice_w) * live,
                   (double)2 * live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, ncol, 16) * 2) + 32.0 * ks * D * ncol * live);
         CK(oz_gemm(q, st));
       }
@@ -1703,9 +1723,10 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
         CK(oz_slice_cols(Uin, D, 1, ncat, NT, nold, gs, perm_dev, oz.Bs, oz.eb, st));
       }
       ny = oz_pick_split(D, ncat, 1, NT, SPLIT_MAX);
-      KTimer kt(p, K_LOOP_Y_TC, st, 2.0 * D * D * ncat, (double)D * D * 8 + 16.0 * D * ncat, oz_pair_flops(D, ncat, D),
+      KTimer kt(p, K_LOOP_Y_TC, st, 2.0 * D * D * ncat, (double)D * D * 8 + 16.0 * D * ncat, oz_pair_flops(D, ncat, D, pl.slice_w),
                 (double)oz_rows_elems(D) * 2 + (double)oz_cols_elems(D, ncat, NT) * 2 + 16.0 * ny * D * ncat);
-      CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, oz.Yhi, oz.Ylo, p->status, st));
+      CK(oz_product(oz.Gs, oz.eg, nullptr, true, oz.Bs, oz.eb, D, ncat, 1, NT, ny, oz.Yhi, oz.Ylo, p->status, st,
+                    pl.slice_w));
     } else if (pl.product == IHSBIN_PRODUCT_GRAM) {
       // every live interval multiplies the same G: one contraction over their concatenated columns
       const int64_t ncat = nold * live;
@@ -1766,10 +1787,10 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       const int ks = oz_pick_split(D, nnew, live, NT, SPLIT_MAX);
       {
         KTimer kt(p, K_LOOP_P_TC, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 16.0 * D * nnew * live,
-                  oz_pair_flops(D, nnew, D) * live,
+                  oz_pair_flops(D, nnew, D, pl.slice_w) * live,
                   (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 16.0 * ks * D * nnew * live);
         CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, erv, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
-                      st));
+                      st, pl.slice_w));
       }
       if (fused) {
         // the intervals still running at the next step take their new columns' slices now
@@ -2105,10 +2126,11 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
       }
       {
         OzGemm q;
+        q.wmax = p->plan.slice_w;
         q.As = oz.Gs; q.a_shared = true; q.Bs = Pc;
         q.M = D; q.N = D; q.K = D; q.groups = Tm; q.NT = 32; q.ksplit = ks;
         q.ohi = mh; q.olo = ml; q.status = p->status;
-        KTimer kt(p, K_INVERSE_TC, st, 2.0 * D * D * D * Tm, (double)(1 + 2 * Tm) * D * D * 8, oz_pair_flops(D, D, D) * Tm,
+        KTimer kt(p, K_INVERSE_TC, st, 2.0 * D * D * D * Tm, (double)(1 + 2 * Tm) * D * D * 8, oz_pair_flops(D, D, D, pl.slice_w) * Tm,
                   (double)oz_rows_elems(D) * 2 + (double)Tm * vcol * 2 + 16.0 * ks * Tm * D * D);
         CK(oz_gemm(q, st));
       }

@@ -49,26 +49,31 @@ namespace {
     if (e__ != cudaSuccess) return e__;    \
   } while (0)
 
-constexpr int SL_STAGES = 6;
-constexpr int SL_STAGE_BYTES = 32768;    // A block + B block
 constexpr int SL_BLOCK_ELEMS = 8192;     // 128 rows x 64 k (BF16)
 constexpr int SL_CHUNK = 8;              // K-blocks per exact Tensor Memory chunk (512 k)
 constexpr int SL_KB_MAX = 1024;          // K-blocks per work item (65536 k)
 constexpr int SL_MAX_PAIRS = 36;
 constexpr int SL_NONFINITE = 1 << 20;    // column exponent marking a column holding Inf/NaN
-constexpr int SL_THREADS = 192;
 
 struct SlicePlan {
-  int ns, np, T, RB, KB, nsplit, kbper, D;
+  int ns, np, T, RB, KB, nsplit, kbper, D;  // RB: 128-column blocks per slice of the A-side buffer (its stride)
   int rect;   // 1: C = X^T Y of two sliced operands (all tiles of every pair); 0: the symmetric Gram X^T X
-  int TJ;     // column tiles of the result (rect: Y's 128-column tiles; Gram: T)
-  int RBb;    // 128-column tiles of the B-side slice buffer
+  int nw;     // 128-column blocks per result tile (1 or 2)
+  int TJ;     // result column tiles (each nw blocks wide)
+  int RBb;    // 128-column blocks per slice of the B-side buffer (TJ nw: padded with zero blocks)
   int8_t ps[SL_MAX_PAIRS], pt[SL_MAX_PAIRS];
   int base[SL_MAX_PAIRS + 1];  // first tile of each pair; base[np] = tiles of all pairs (items = tiles x nsplit)
 };
 
-__host__ __device__ __forceinline__ int tile_index(bool diag_pair, int T, int I, int J) {
-  return diag_pair ? I * T - I * (I - 1) / 2 + (J - I) : I * T + J;
+// sum over I' < I of floor(I' / nw): the tiles a symmetric pair skips before row tile I
+__host__ __device__ __forceinline__ int diag_skip(int I, int nw) {
+  if (nw == 1) return I * (I - 1) / 2;
+  const int a = I / 2;
+  return a * (a - 1) + (I & 1) * a;
+}
+// index of result tile (I, Jw) (Jw in nw-wide column tiles) within its pair
+__host__ __device__ __forceinline__ int tile_index(bool diag_pair, int TJ, int nw, int I, int Jw) {
+  return diag_pair ? I * TJ - diag_skip(I, nw) + (Jw - I / nw) : I * TJ + Jw;
 }
 
 __device__ __forceinline__ int col_exp(unsigned mbits) {
@@ -166,50 +171,74 @@ __global__ void k_slice(const void* A, int64_t ld, int64_t N, int64_t D, const u
   }
 }
 
-__global__ void __launch_bounds__(SL_THREADS, 1)
+// Work item of the slice products: pair p = (s, t), tile (I, J) with J counted in NW-block-wide
+// column tiles, row split q.  item = q * tiles + (tile of pair p): the row split outermost, so that
+// the CTAs running together work on one row range and share its slice blocks in L2.
+struct SlItem {
+  int s, t, I, J, q;
+};
+__device__ __forceinline__ SlItem sl_decode(const SlicePlan& pl, int item) {
+  SlItem w;
+  const int tiles_all = pl.base[pl.np];
+  w.q = item / tiles_all;
+  const int r = item - w.q * tiles_all;
+  int p = 0;
+  while (p + 1 < pl.np && pl.base[p + 1] <= r) ++p;
+  w.s = pl.ps[p];
+  w.t = pl.pt[p];
+  const int tile = r - pl.base[p];
+  if (!pl.rect && w.s == w.t) {  // symmetric pair: only tiles reaching the upper triangle
+    int I = 0, rest = tile;
+    while (rest >= pl.TJ - I / pl.nw) {
+      rest -= pl.TJ - I / pl.nw;
+      ++I;
+    }
+    w.I = I;
+    w.J = I / pl.nw + rest;
+  } else {
+    w.I = tile / pl.TJ;
+    w.J = tile - w.I * pl.TJ;
+  }
+  return w;
+}
+
+// One CTA per work item: a 128 x (128 NW) tile of one slice pair over one row range.  NW = 2 halves
+// the shared-memory traffic per MMA flop (the A block serves a 256-wide B operand).
+template <int NW>
+struct SlCfg {
+  static constexpr int STAGES = NW == 1 ? 6 : 4;
+  static constexpr int STAGE = (1 + NW) * SL_BLOCK_ELEMS * 2;  // A block + NW B blocks
+  static constexpr int SMEM = STAGES * STAGE;                   // 192 KiB
+  static constexpr int EPI = 4 * NW;                            // epilogue warps (128 columns each)
+  static constexpr int THREADS = 64 + 32 * EPI;
+  static constexpr int COLS = 256 * NW;                         // two 128 x 128 NW accumulators
+};
+
+template <int NW>
+__global__ void __launch_bounds__(SlCfg<NW>::THREADS, 1)
     k_gram_slices_tc(const __nv_bfloat16* __restrict__ S, const __nv_bfloat16* __restrict__ SB, SlicePlan pl,
                      int* __restrict__ out, int* status, int item0) {
+  using C = SlCfg<NW>;
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t full[SL_STAGES], empty[SL_STAGES], tfull[2], tempty[2], drained;
+  __shared__ __align__(8) uint64_t full[C::STAGES], empty[C::STAGES], tfull[2], tempty[2], drained;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-  // work item -> pair, tile (I, J), row range
   const int item = item0 + blockIdx.x;
-  int p = 0;
-  // item = q * tiles + (tile of pair p): the row split outermost, so that the CTAs running together
-  // work on one row range and share its slice blocks in L2
-  const int tiles_all = pl.base[pl.np];
-  const int q = item / tiles_all, r_item = item - q * tiles_all;
-  while (p + 1 < pl.np && pl.base[p + 1] <= r_item) ++p;
-  const int s = pl.ps[p], t = pl.pt[p];
-  const int tile = r_item - pl.base[p];
-  int I, J;
-  if (pl.rect) {
-    I = tile / pl.TJ;
-    J = tile - I * pl.TJ;
-  } else if (s == t) {
-    I = 0;
-    int rest = tile;
-    while (rest >= pl.T - I) { rest -= pl.T - I; ++I; }
-    J = I + rest;
-  } else {
-    I = tile / pl.T;
-    J = tile - I * pl.T;
-  }
-  const int kb0 = q * pl.kbper, kb1 = min(pl.KB, kb0 + pl.kbper);
+  const SlItem w = sl_decode(pl, item);
+  const int kb0 = w.q * pl.kbper, kb1 = min(pl.KB, kb0 + pl.kbper);
   const int nkb = kb1 - kb0, nch = (nkb + SL_CHUNK - 1) / SL_CHUNK;
 
-  if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_base), 256);
+  if (warp == 1) tc::tmem_alloc(tc::smem_addr(&tmem_base), C::COLS);
   if (tid == 0) {
-    for (int i = 0; i < SL_STAGES; ++i) {
+    for (int i = 0; i < C::STAGES; ++i) {
       tc::bar_init(tc::smem_addr(&full[i]), 1);
       tc::bar_init(tc::smem_addr(&empty[i]), 1);
     }
     for (int i = 0; i < 2; ++i) {
       tc::bar_init(tc::smem_addr(&tfull[i]), 1);
-      tc::bar_init(tc::smem_addr(&tempty[i]), 4);
+      tc::bar_init(tc::smem_addr(&tempty[i]), C::EPI);
     }
     tc::bar_init(tc::smem_addr(&drained), 1);
     abort_flag = 0;
@@ -219,34 +248,38 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const __nv_bfloat16* gA = S + (((int64_t)s * pl.RB + I) * pl.KB + kb0) * SL_BLOCK_ELEMS;
-  const __nv_bfloat16* gB = SB + (((int64_t)t * pl.RBb + J) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  const __nv_bfloat16* gA = S + (((int64_t)w.s * pl.RB + w.I) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  const __nv_bfloat16* gB = SB + (((int64_t)w.t * pl.RBb + (int64_t)w.J * NW) * pl.KB + kb0) * SL_BLOCK_ELEMS;
+  const int64_t bstep = (int64_t)pl.KB * SL_BLOCK_ELEMS;  // next 128-column block of B
   volatile int* abort_v = &abort_flag;
 
   if (warp == 0) {
     if (lane == 0) {  // producer: bulk copies into the stage ring
       int issued = 0;
       for (int it = 0; it < nkb; ++it) {
-        const int st = it % SL_STAGES, rnd = it / SL_STAGES;
+        const int st = it % C::STAGES, rnd = it / C::STAGES;
         if (rnd > 0 && !tc::bar_wait(tc::smem_addr(&empty[st]), (rnd - 1) & 1)) {
           dev_fail(status, DEV_TIMEOUT);
           *abort_v = 1;
           break;
         }
         if (*abort_v) break;
-        const uint32_t sa = tc::smem_addr(smem + st * SL_STAGE_BYTES), fb = tc::smem_addr(&full[st]);
-        tc::bar_arrive_tx(fb, SL_STAGE_BYTES);
-        tc::bulk_load(sa, gA + (int64_t)it * SL_BLOCK_ELEMS, SL_STAGE_BYTES / 2, fb);
-        tc::bulk_load(sa + SL_STAGE_BYTES / 2, gB + (int64_t)it * SL_BLOCK_ELEMS, SL_STAGE_BYTES / 2, fb);
+        const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), fb = tc::smem_addr(&full[st]);
+        tc::bar_arrive_tx(fb, C::STAGE);
+        tc::bulk_load(sa, gA + (int64_t)it * SL_BLOCK_ELEMS, SL_BLOCK_ELEMS * 2, fb);
+#pragma unroll
+        for (int b = 0; b < NW; ++b)  // the B blocks land adjacent: one 128 NW-row operand
+          tc::bulk_load(sa + (1 + b) * SL_BLOCK_ELEMS * 2, gB + b * bstep + (int64_t)it * SL_BLOCK_ELEMS,
+                        SL_BLOCK_ELEMS * 2, fb);
         issued = it + 1;
       }
       // the copies of the last stages land before the CTA may leave
-      for (int it = issued > SL_STAGES ? issued - SL_STAGES : 0; it < issued; ++it)
-        tc::bar_wait(tc::smem_addr(&full[it % SL_STAGES]), (it / SL_STAGES) & 1);
+      for (int it = issued > C::STAGES ? issued - C::STAGES : 0; it < issued; ++it)
+        tc::bar_wait(tc::smem_addr(&full[it % C::STAGES]), (it / C::STAGES) & 1);
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+      constexpr uint32_t idesc = tc::idesc_bf16(128, 128 * NW);
       bool ok = true;
       for (int c = 0; c < nch && ok; ++c) {
         const int h = c & 1;
@@ -256,10 +289,10 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
           break;
         }
         tc::fence_after_sync();
-        const uint32_t d = tmem + (uint32_t)(h * 128);
+        const uint32_t d = tmem + (uint32_t)(h * 128 * NW);
         const int i0 = c * SL_CHUNK, i1 = min(nkb, i0 + SL_CHUNK);
         for (int it = i0; it < i1; ++it) {
-          const int st = it % SL_STAGES, rnd = it / SL_STAGES;
+          const int st = it % C::STAGES, rnd = it / C::STAGES;
           if (!tc::bar_wait(tc::smem_addr(&full[st]), rnd & 1) || *abort_v) {
             dev_fail(status, DEV_TIMEOUT);
             *abort_v = 1;
@@ -267,11 +300,11 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
             break;
           }
           tc::fence_after_sync();
-          const uint32_t sa = tc::smem_addr(smem + st * SL_STAGE_BYTES);
+          const uint32_t sa = tc::smem_addr(smem + st * C::STAGE);
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)  // K = 16 per MMA: two core matrices (256 bytes) along K
             tc::mma_bf16(d, tc::smem_desc(sa + ks * 256, 128, 1024),
-                         tc::smem_desc(sa + SL_STAGE_BYTES / 2 + ks * 256, 128, 1024), idesc,
+                         tc::smem_desc(sa + SL_BLOCK_ELEMS * 2 + ks * 256, 128, 1024), idesc,
                          (it > i0 || ks > 0) ? 1u : 0u);
           tc::commit(tc::smem_addr(&empty[st]));
         }
@@ -280,8 +313,8 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
       tc::commit(tc::smem_addr(&drained));  // every MMA of this CTA has completed
       tc::bar_wait(tc::smem_addr(&drained), 0);
     }
-  } else {  // warps 2..5: Tensor Memory lanes 32 (warp % 4) .. +31 are this thread's rows
-    const int qd = warp & 3;
+  } else {  // epilogue: lanes 32 (warp % 4) .. +31 are this thread's rows; warp group cg its 128 columns
+    const int qd = warp & 3, cg = (warp - 2) >> 2;
     int acc[128];
 #pragma unroll
     for (int c = 0; c < 128; ++c) acc[c] = 0;
@@ -298,7 +331,7 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
 #pragma unroll
       for (int cc = 0; cc < 128; cc += 32) {
         uint32_t r[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * 128 + cc), r);
+        tc::tmem_ld32(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * 128 * NW + cg * 128 + cc), r);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int x = 0; x < 32; ++x) acc[cc + x] += __float2int_rn(__uint_as_float(r[x]));  // integer-valued
@@ -307,15 +340,15 @@ __global__ void __launch_bounds__(SL_THREADS, 1)
       __syncwarp();
       if (lane == 0) tc::bar_arrive(tc::smem_addr(&tempty[h]));
     }
-    if (ok) {  // tile stored column-major: out[item][col][row]
-      int* o = out + (int64_t)item * 16384 + qd * 32 + lane;
+    if (ok) {  // tile stored column-major: out[item][col][row], 128 NW columns
+      int* o = out + (int64_t)item * (16384 * NW) + (int64_t)cg * 16384 + qd * 32 + lane;
 #pragma unroll
       for (int c = 0; c < 128; ++c) o[c * 128] = acc[c];
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 1) tc::tmem_dealloc(tmem, 256);
+  if (warp == 1) tc::tmem_dealloc(tmem, C::COLS);
 }
 
 // G[i][j] = G[j][i] for i <= j from the integer tiles (pairs ordered by weight, largest first)
@@ -344,11 +377,15 @@ __global__ void k_gram_combine(const int* __restrict__ out, SlicePlan pl, const 
           v = 0;
           w = s + t;
         }
-        const int a = pl.base[p] + tile_index(s == t, pl.T, I, J);
-        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * 16384 + rj * 128 + ri];
+        // tile (I, J / nw), column (J % nw) 128 + rj; tiles hold 16384 nw integers
+        const int64_t ts = (int64_t)16384 * pl.nw;
+        const int a = pl.base[p] + tile_index(s == t, pl.TJ, pl.nw, I, J / pl.nw);
+        const int ca = (J % pl.nw) * 128 + rj;
+        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * ts + ca * 128 + ri];
         if (s != t) {
-          const int b = pl.base[p] + tile_index(false, pl.T, J, I);
-          for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + b) * 16384 + ri * 128 + rj];
+          const int b = pl.base[p] + tile_index(false, pl.TJ, pl.nw, J, I / pl.nw);
+          const int cb = (I % pl.nw) * 128 + ri;
+          for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + b) * ts + cb * 128 + rj];
         }
       }
       sum += ldexp((double)v, -8 * w);
@@ -363,10 +400,10 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
   SlicePlan pl{};
   pl.ns = ns;
   pl.D = (int)D;
-  pl.RB = (int)((D + 127) / 128);
-  pl.T = pl.RB;
-  pl.TJ = pl.T;
-  pl.RBb = pl.RB;
+  pl.T = (int)((D + 127) / 128);
+  pl.nw = pl.T >= 2 ? 2 : 1;                 // 256-wide tiles once there are two column blocks
+  pl.TJ = (pl.T + pl.nw - 1) / pl.nw;
+  pl.RB = pl.RBb = pl.TJ * pl.nw;           // one buffer for both sides, padded with zero blocks
   pl.rect = 0;
   pl.KB = (int)((N + 63) / 64);
   // pairs s <= t, s + t <= wmax, ordered by weight (largest s + t first)
@@ -379,9 +416,11 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
       pl.pt[pl.np] = (int8_t)t;
       ++pl.np;
     }
+  auto pair_tiles = [&](int p) {
+    return pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * pl.TJ - diag_skip(pl.T, pl.nw) : (int64_t)pl.T * pl.TJ;
+  };
   int64_t tiles = 0;
-  for (int p = 0; p < pl.np; ++p)
-    tiles += pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T;
+  for (int p = 0; p < pl.np; ++p) tiles += pair_tiles(p);
   // split the rows so that every item stays within SL_KB_MAX K-blocks and the GPU gets >= 2 waves
   int nsplit = (pl.KB + SL_KB_MAX - 1) / SL_KB_MAX;
   const int64_t want = (2 * 152 + tiles - 1) / tiles;
@@ -391,22 +430,37 @@ SlicePlan make_slice_plan(int64_t N, int64_t D, int ns, int wmax) {
   int64_t b = 0;
   for (int p = 0; p < pl.np; ++p) {
     pl.base[p] = (int)b;
-    b += pl.ps[p] == pl.pt[p] ? (int64_t)pl.T * (pl.T + 1) / 2 : (int64_t)pl.T * pl.T;
+    b += pair_tiles(p);
   }
   pl.base[pl.np] = (int)b;
   return pl;
 }
 
+// Launch items [i0, i0 + n) of a slice-product plan (tile width pl.nw blocks).
+cudaError_t launch_slices(const SlicePlan& pl, const __nv_bfloat16* S, const __nv_bfloat16* SB, int* out, int* status,
+                          int i0, int n, cudaStream_t st) {
+  if (pl.nw == 2) {
+    CK(cudaFuncSetAttribute(k_gram_slices_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SlCfg<2>::SMEM));
+    k_gram_slices_tc<2><<<(unsigned)n, SlCfg<2>::THREADS, SlCfg<2>::SMEM, st>>>(S, SB, pl, out, status, i0);
+  } else {
+    CK(cudaFuncSetAttribute(k_gram_slices_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SlCfg<1>::SMEM));
+    k_gram_slices_tc<1><<<(unsigned)n, SlCfg<1>::THREADS, SlCfg<1>::SMEM, st>>>(S, SB, pl, out, status, i0);
+  }
+  return cudaGetLastError();
+}
+
 // C = X^T Y for X (N x D, nsa slices per entry) and Y (N x K, nsb slices per entry): every tile of
 // every pair (s, t), s < nsa, t < nsb, s + t <= wmax, pairs ordered by weight (largest first).
-SlicePlan make_rect_plan(int64_t N, int64_t D, int nsa, int64_t K, int nsb, int wmax) {
+SlicePlan make_rect_plan(int64_t N, int64_t D, int nsa, int a_stride, int64_t K, int nsb, int wmax) {
   SlicePlan pl{};
   pl.ns = nsa;
   pl.D = (int)D;
-  pl.RB = (int)((D + 127) / 128);
-  pl.T = pl.RB;
-  pl.RBb = (int)((K + 127) / 128);
-  pl.TJ = pl.RBb;
+  pl.RB = a_stride;                          // the A side is the Gram's slice buffer
+  pl.T = (int)((D + 127) / 128);
+  const int kb = (int)((K + 127) / 128);
+  pl.nw = kb >= 2 ? 2 : 1;
+  pl.TJ = (kb + pl.nw - 1) / pl.nw;
+  pl.RBb = pl.TJ * pl.nw;
   pl.rect = 1;
   pl.KB = (int)((N + 63) / 64);
   pl.np = 0;
@@ -454,8 +508,10 @@ __global__ void k_rect_combine(const int* __restrict__ out, SlicePlan pl, const 
           v = 0;
           w = pl.ps[p] + pl.pt[p];
         }
-        const int a = pl.base[p] + I * pl.TJ + J;
-        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * 16384 + rj * 128 + ri];
+        const int a = pl.base[p] + I * pl.TJ + J / pl.nw;
+        const int ca = (J % pl.nw) * 128 + rj;
+        const int64_t ts = (int64_t)16384 * pl.nw;
+        for (int q = 0; q < pl.nsplit; ++q) v += out[((int64_t)q * pl.base[pl.np] + a) * ts + ca * 128 + ri];
       }
       sum += ldexp((double)v, -8 * w);
       g = ldexp(sum, ei + ej - 14);
@@ -482,7 +538,7 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
   int* out = nullptr;
   CK(prob_alloc(p, (size_t)D * sizeof(unsigned), (void**)&cmax, SCOPE_SCRATCH));
   CK(prob_alloc(p, (size_t)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2, (void**)&S, SCOPE_SCRATCH));
-  CK(prob_alloc(p, (size_t)items * 16384 * sizeof(int), (void**)&out, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)items * 16384 * pl.nw * sizeof(int), (void**)&out, SCOPE_SCRATCH));
   CK(cudaMemsetAsync(cmax, 0, (size_t)D * sizeof(unsigned), st));
   const size_t es = ET == ELEM_F64 ? 8 : ET == ELEM_F32 ? 4 : 2;
   {
@@ -503,35 +559,32 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
     const double mfl = (double)N * D * (D + 1.0), mby = (double)N * D * es;
     double fl = 0;
     for (int q = 0; q < pl.np; ++q) fl += 2.0 * N * (pl.ps[q] == pl.pt[q] ? D * (D + 1) / 2.0 : (double)D * D);
-    const double by = (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536;
-    const int smem = SL_STAGES * SL_STAGE_BYTES;
-    CK(cudaFuncSetAttribute(k_gram_slices_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const double by = (double)pl.ns * pl.RB * pl.KB * SL_BLOCK_ELEMS * 2 + (double)items * 65536 * pl.nw;
     // max_ctas > 0: launches of at most max_ctas CTAs (one wave each), so that the SMs beyond them
     // stay free for work on other streams
     const int chunk = max_ctas > 0 ? std::min(items, max_ctas) : items;
     for (int i0 = 0; i0 < items; i0 += chunk) {
       const int n = std::min(chunk, items - i0);
       KTimer kt(p, cat_tc, st, mfl * n / items, mby * n / items, fl * n / items, by * n / items);
-      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, S, pl, out, p->status, i0);
-      CK(cudaGetLastError());
+      CK(launch_slices(pl, S, S, out, p->status, i0, n, st));
     }
   }
   {
-    KTimer kt(p, cat_combine, st, 0, (double)items * 65536 + (double)D * D * 8);
+    KTimer kt(p, cat_combine, st, 0, (double)items * 65536 * pl.nw + (double)D * D * 8);
     const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, D), 1024);
     k_gram_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(out, pl, cmax, G);
     CK(cudaGetLastError());
   }
   if (!Y) return cudaSuccess;
   // the right-hand side X^T Y from the same slices of X (step a3)
-  const SlicePlan pr = make_rect_plan(N, D, ns, K, nsy, kGramMaxWeight);
+  const SlicePlan pr = make_rect_plan(N, D, ns, pl.RB, K, nsy, kGramMaxWeight);
   const int itr = pr.base[pr.np] * pr.nsplit;
   unsigned* cmaxy = nullptr;
   __nv_bfloat16* SY = nullptr;
   int* outy = nullptr;
   CK(prob_alloc(p, (size_t)K * sizeof(unsigned), (void**)&cmaxy, SCOPE_SCRATCH));
   CK(prob_alloc(p, (size_t)nsy * pr.RBb * pr.KB * SL_BLOCK_ELEMS * 2, (void**)&SY, SCOPE_SCRATCH));
-  CK(prob_alloc(p, (size_t)itr * 16384 * sizeof(int), (void**)&outy, SCOPE_SCRATCH));
+  CK(prob_alloc(p, (size_t)itr * 16384 * pr.nw * sizeof(int), (void**)&outy, SCOPE_SCRATCH));
   CK(cudaMemsetAsync(cmaxy, 0, (size_t)K * sizeof(unsigned), st));
   {
     KTimer kt(p, K_RHS, st, 0, (double)N * K * 8 * 2 + (double)nsy * pr.RBb * pr.KB * SL_BLOCK_ELEMS * 2);
@@ -544,20 +597,19 @@ cudaError_t gram_slices_typed(ihsbin_problem* p, const void* X, int64_t ld, int6
   }
   {
     double fl = 2.0 * pr.np * N * D * K;
-    const double by = ((double)pl.ns * pl.RB + (double)nsy * pr.RBb) * pr.KB * SL_BLOCK_ELEMS * 2 + (double)itr * 65536;
-    const int smem = SL_STAGES * SL_STAGE_BYTES;
+    const double by = ((double)pl.ns * pl.RB + (double)nsy * pr.RBb) * pr.KB * SL_BLOCK_ELEMS * 2 +
+                      (double)itr * 65536 * pr.nw;
     const int chunk = max_ctas > 0 ? std::min(itr, max_ctas) : itr;
     for (int i0 = 0; i0 < itr; i0 += chunk) {
       const int n = std::min(chunk, itr - i0);
       // the method's work: 2 N D K flops, one read of X and of Y
       KTimer kt(p, K_RHS, st, 2.0 * N * D * K * n / itr, ((double)N * D * es + (double)N * K * 8) * n / itr,
                 fl * n / itr, by * n / itr);
-      k_gram_slices_tc<<<(unsigned)n, SL_THREADS, smem, st>>>(S, SY, pr, outy, p->status, i0);
-      CK(cudaGetLastError());
+      CK(launch_slices(pr, S, SY, outy, p->status, i0, n, st));
     }
   }
   {
-    KTimer kt(p, K_RHS, st, 0, (double)itr * 65536 + (double)D * K * 8);
+    KTimer kt(p, K_RHS, st, 0, (double)itr * 65536 * pr.nw + (double)D * K * 8);
     const unsigned gy = (unsigned)std::min<int64_t>(std::max<int64_t>(1, K), 1024);
     k_rect_combine<Mode><<<dim3((unsigned)((D + 127) / 128), gy), 128, 0, st>>>(outy, pr, cmax, cmaxy, K, c);
     CK(cudaGetLastError());
@@ -577,7 +629,7 @@ cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, i
     if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
       mc = std::max(1, sms - reserve_sms);
   }
-  const int ns = gram_slices_for(et);
+  const int ns = gram_slices_for(et, p->tf32);
   const double* Y = rhs ? p->B : nullptr;
   const int64_t K = rhs ? p->K : 0;
   const CBuf c = rhs ? *rhs : CBuf{};

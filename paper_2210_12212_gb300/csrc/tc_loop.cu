@@ -97,6 +97,7 @@ struct OzArgs {
   long long* ohi;        // exact partials (weights 0..3 / 4..6), entry ((s * groups + g) * N + j) * M + i
   long long* olo;
   int* status;
+  int wmax;              // slice pairs kept: s + t <= wmax (<= OZ_W); the others weigh below 2^(-8 (wmax + 1))
 };
 
 // Persistent: CTA b takes work items b, b + gridDim.x, ...; item = ((g * ksplit + sp) * MT + mt) * NTL + nt
@@ -233,10 +234,11 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
             for (int ks = 0; ks < OZ_BK / 16; ++ks)
 #pragma unroll
               for (int s = 0; s < OZ_S; ++s) {
+                if (s > a.wmax) break;  // uniform
                 const bool first = it == i0 && ks == 0 && s == 0;
                 // descriptor start-address field: byte offset / 16 (no carry: shared addresses < 2^18)
                 tc::mma_bf16(dbase + (uint32_t)(s * NT), da0 + (uint64_t)((s * (OZ_ABLK * 2) + ks * 256) >> 4),
-                             db0 + (uint64_t)((ks * 256) >> 4), tc::idesc_bf16(128, (OZ_W + 1 - s) * NT),
+                             db0 + (uint64_t)((ks * 256) >> 4), tc::idesc_bf16(128, (a.wmax + 1 - s) * NT),
                              first ? 0u : 1u);
               }
             tc::commit(tc::smem_addr(&empty[st]));
@@ -268,7 +270,7 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
         tc::fence_after_sync();
 #pragma unroll
         for (int wi = 0; wi < C::WPG; ++wi) {
-          if (w0 + wi >= OZ_NW) continue;  // warp-uniform
+          if (w0 + wi > a.wmax) continue;  // warp-uniform; weights above wmax stay zero
           const uint32_t ta =
               tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT);
           if constexpr (NT == 16) {
@@ -988,13 +990,16 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   a.ohi = q.ohi;
   a.olo = q.olo;
   a.status = q.status;
+  if (q.wmax < 1 || q.wmax > OZ_W) return cudaErrorInvalidValue;
+  a.wmax = q.wmax;
   return q.NT == 16 ? launch_oz<16>(a, st) : launch_oz<32>(a, st);
 }
 
 cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
                        const __nv_bfloat16* Bs, const int* eb, int64_t D, int64_t ncolg, int groups, int NT,
-                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st) {
+                       int ksplit, long long* ohi, long long* olo, int* status, cudaStream_t st, int wmax) {
   OzGemm q;
+  q.wmax = wmax;
   q.As = As; q.ea = ea; q.a_perm = a_perm; q.a_shared = a_shared;
   q.Bs = Bs; q.eb = eb;
   q.M = D; q.N = ncolg; q.K = D; q.groups = groups; q.NT = NT; q.ksplit = ksplit;
@@ -1148,10 +1153,10 @@ uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max) {
          bcols * (uint64_t)oz_kb(D) * OZ_S * OZ_BK * 2 + bcols * 4;
 }
 
-double oz_pair_flops(int64_t M, int64_t N, int64_t K) {
+double oz_pair_flops(int64_t M, int64_t N, int64_t K, int wmax) {
   int pairs = 0;
   for (int s = 0; s < OZ_S; ++s)
-    for (int t = 0; t < OZ_S; ++t) pairs += s + t <= OZ_W;
+    for (int t = 0; t < OZ_S; ++t) pairs += s + t <= wmax;
   return 2.0 * pairs * (double)M * (double)N * (double)K;
 }
 

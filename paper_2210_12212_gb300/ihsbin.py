@@ -21,14 +21,14 @@ LIB_PATH = os.path.join(_HERE, "libihsbin.so")
 OK, ERR_INVALID_ARG, ERR_OUT_OF_MEMORY, ERR_CUDA, ERR_NOT_SPD, ERR_LAMBDA_RANGE, ERR_STATE, \
     ERR_TIMEOUT, ERR_ADMISSION, ERR_UNSUPPORTED = range(10)
 ERR_NAN = 11
-F64, F32, BF16 = 0, 1, 2
+F64, F32, BF16, TF32 = 0, 1, 2, 3
 COMPUTE_F64, COMPUTE_F32X2 = 0, 1
 DENSE, CSR = 0, 1
 SK_GAUSSIAN, SK_SRHT, SK_COUNTSKETCH = 0, 1, 2
 PRODUCT_AUTO, PRODUCT_GRAM, PRODUCT_ASPACE = 0, 1, 2
 
 SKETCH_KIND = {"gaussian": SK_GAUSSIAN, "srht": SK_SRHT, "countsketch": SK_COUNTSKETCH}
-DTYPE = {"f64": F64, "f32": F32, "bf16": BF16}
+DTYPE = {"f64": F64, "f32": F32, "bf16": BF16, "tf32": TF32}
 SKETCH_APPLY = {"auto": 0, "tensor": 1, "fma": 2}
 COMPUTE = {"f64": COMPUTE_F64, "f32x2": COMPUTE_F32X2}
 PRODUCT = {"auto": PRODUCT_AUTO, "gram": PRODUCT_GRAM, "aspace": PRODUCT_ASPACE}
@@ -61,7 +61,7 @@ class PathDesc(C.Structure):
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
                 ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
                 ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int), ("sigma_d2", C.c_double),
-                ("tau", C.c_void_p)]
+                ("tau", C.c_void_p), ("slice_weight", C.c_int32)]
 
 
 class AdaptiveDesc(C.Structure):
@@ -253,7 +253,7 @@ class Problem:
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
                     eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", loop: str = "auto",
                     factor: str = "auto", sigma_d2: float = 0.0, tau: Optional[Sequence[float]] = None,
-                    stream=None):
+                    slice_weight: int = 0, stream=None):
         """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
         gram / loop / factor select the Gram kernel, the recursion's product kernel and the inverse's
         product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
@@ -274,6 +274,7 @@ class Problem:
         pd.sigma_d2 = sigma_d2
         ta = np.ascontiguousarray(tau, dtype=np.float64) if tau is not None else None
         pd.tau = _ptr(ta)
+        pd.slice_weight = slice_weight
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
 
     def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",

@@ -51,7 +51,8 @@ class Problem:
     d: int
     K: int
     layout: str                 # "dense" | "csr"
-    storage: str                # "f64" | "f32" | "bf16"  (element type of A as stored)
+    storage: str                # "f64" | "f32" | "tf32" | "bf16"  (element type of A as stored; "tf32"
+                                #  data is held as FP32 and the library rounds it, as the oracle does)
     A: Optional[np.ndarray]     # dense n x d (float64/float32, or uint16 bf16 bit patterns)
     row_ptr: Optional[np.ndarray]  # CSR int64 (n+1)
     col_idx: Optional[np.ndarray]  # CSR int32 (nnz), sorted within a row, no duplicates
@@ -320,7 +321,7 @@ def make_problem(name: str, seed: int = 0, **overrides) -> Problem:
                                  else np.float32)
             Af = A
     elif cfg["kind"] == "haar":
-        A = _haar_lowrank(rng, n, d).astype(np.float32 if cfg["storage"] == "f32" else np.float64)
+        A = _haar_lowrank(rng, n, d).astype(np.float32 if cfg["storage"] in ("f32", "tf32") else np.float64)
         Af = A
     elif cfg["kind"] == "csr":
         layout = "csr"

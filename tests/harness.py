@@ -20,12 +20,15 @@ def rel_err_max(X, Xref):
 
 
 def oracle_A(prob):
-    """A as the oracle consumes it: FP64 dense array or scipy CSR (values widened exactly)."""
+    """A as the oracle consumes it: FP64 dense array or scipy CSR (values widened exactly; TF32
+    storage rounded by the oracle's own TF32 rounding first)."""
+    from oracle.precision import round_tf32
+    tf32 = prob.storage == "tf32"
     if prob.layout == "csr":
         import scipy.sparse as sp
-        return sp.csr_matrix((prob.val.astype(np.float64), prob.col_idx, prob.row_ptr),
-                             shape=(prob.n, prob.d))
-    return prob.dense_f64()
+        val = round_tf32(prob.val) if tf32 else prob.val
+        return sp.csr_matrix((val.astype(np.float64), prob.col_idx, prob.row_ptr), shape=(prob.n, prob.d))
+    return round_tf32(prob.A).astype(np.float64) if tf32 else prob.dense_f64()
 
 
 def gpu_problem(ihs, ctx, prob, device_inputs=False):

@@ -467,3 +467,31 @@ def test_split_keeps_the_model():
     assert np.array_equal(train.A, full.A[:3000]) and np.array_equal(At, full.A[3000:])
     tr, A2, B2 = make_split("c3_small", 50, seed=0)
     assert tr.row_ptr.shape == (tr.n + 1,) and A2.shape == (50, tr.d)
+
+
+def test_tf32_rounding_known_values():
+    # TF32 keeps 10 fraction bits: 1 + k 2^-10 are representable; halfway points go away from zero
+    from oracle.precision import round_tf32
+    u = 2.0 ** -10
+    x = np.array([1.0, 1.0 + u, 1.0 + u / 2, 1.0 + u / 2 - 2.0 ** -23, 1.0 + 3 * u / 2, -(1.0 + u / 2),
+                  2.0 ** -126, 3.0e38, 0.0, -0.0, np.inf], dtype=np.float32)
+    want = np.array([1.0, 1.0 + u, 1.0 + u, 1.0, 1.0 + 2 * u, -(1.0 + u), 2.0 ** -126, np.float32(3.0e38),
+                     0.0, -0.0, np.inf], dtype=np.float32)
+    got = round_tf32(x)
+    # 3e38 = 0x7F61B1E6: its 13 low bits 0x11E6 >= 0x1000 round the magnitude up
+    want[7] = np.uint32(0x7F61C000).view(np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert np.isnan(round_tf32(np.array([np.nan], dtype=np.float32)))[0]
+
+
+def test_tf32_rounding_is_nearest():
+    # against the definition on a grid: the result is one of the two neighbours at 2^-10 relative
+    # spacing, the nearer one, and the error is at most half the spacing
+    from oracle.precision import round_tf32
+    rng = np.random.default_rng(4)
+    x = (rng.standard_normal(100000) * 10.0 ** rng.integers(-8, 8, 100000)).astype(np.float32)
+    r = round_tf32(x).astype(np.float64)
+    e = np.floor(np.log2(np.abs(x.astype(np.float64))))
+    ulp = 2.0 ** (e - 10)
+    assert np.all(np.abs(r - x) <= ulp / 2 * (1 + 1e-12))
+    assert np.all(np.abs(r / ulp - np.round(r / ulp)) == 0)   # on the TF32 grid of x's binade (or the next)
