@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--config", default="c4")
     ap.add_argument("--compute", default="f32x2", choices=["f32x2", "f64"])
     ap.add_argument("--jmax", type=int, default=16)
+    ap.add_argument("--slice-weight", type=int, default=0,
+                    help="slice pairs kept by the recursion's tensor-core products (0 = 6: float-float class)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -250,6 +252,7 @@ def config_for(args, prob, par, world=1):
                 f"; the sketch dimension chosen by Algorithm 4 from m0={args.adaptive} at lambda_min "
                 f"inside each step" if args.adaptive else ""),
             "jmax": args.jmax,
+            "slice_weight": args.slice_weight or 6,
             "storage": prob.storage,
             "l2": L2_NOTE.get(args.config, "see workload"),
             "params": (f"tests/golden/{args.config[:-1] if args.config == 'c3t' else args.config}_params.json"
@@ -473,10 +476,11 @@ def main():
     X_dev = torch.empty((T, prob.d, prob.K), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     if par is None:
-        bkw = dict(k=None, k_default=0, eps=args.eps, auto_rho=True, jmax=args.jmax, compute=args.compute)
+        bkw = dict(k=None, k_default=0, eps=args.eps, auto_rho=True, jmax=args.jmax, compute=args.compute,
+                   slice_weight=args.slice_weight)
     else:
         bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
-                   compute=args.compute)
+                   compute=args.compute, slice_weight=args.slice_weight)
     entries = "bf16" if prob.storage == "bf16" else "f64"
     if prob.layout == "csr":
         csr_dev = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda()

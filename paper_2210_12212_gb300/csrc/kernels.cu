@@ -1985,11 +1985,12 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   {
     CallStream fac_alloc(sf);
     CK(cudaEventRecord(ev[0], sf));
+    p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
+    CK(err);
     CBuf H = cb((size_t)L * D * D);
     CBuf Wm = cb((size_t)L * D * D);
     const int64_t nblk = (D + NB - 1) / NB;
     CBuf dinv = cb((size_t)L * nblk * NB * NB);
-    p->Pinv = alloc_cbuf(p, cm, (size_t)L * D * D, SCOPE_BASIS, &err);
     CK(err);
     CK(factor_and_invert<Mode>(p, H, Wm, dinv, lam0_dev, sf));
     if (pl.auto_rho) {

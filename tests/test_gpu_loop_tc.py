@@ -105,3 +105,21 @@ def test_inverse_slices_match_fma(ctx, name, k):
     plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L)
     assert rel_err_max(out["slices"], _oracle(prob, plan).X) <= 1e-10
     assert rel_err_max(out["slices"], out["fma"]) <= 1e-10
+
+
+@pytest.mark.parametrize("name,k", [("c2_small", 40), ("c4_small", 30)])
+@pytest.mark.parametrize("w", [4, 5])
+def test_slice_weight_keeps_float32_class_accuracy(ctx, name, k, w):
+    """Dropping the slice pairs with s + t > w (each weighs below 2^(-8(w+1)) of an entry's leading
+    product) in the recursion and inverse products: the path stays within the FP32/TF32 tolerance."""
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small(name)
+    L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
+    r1, r2, kk = default_params(prob, L, k)
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute="f32x2", slice_weight=w)
+    Xw = gp.eval_path(prob.lambdas)
+    gp.close()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L)
+    assert rel_err_max(Xw, _oracle(prob, plan).X) <= (1e-6 if w == 4 else 1e-8)
