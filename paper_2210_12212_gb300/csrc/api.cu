@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace ihsbin;
 
@@ -191,6 +192,16 @@ void prob_free_basis(ihsbin_problem* p) {
 
 }  // namespace ihsbin
 
+
+namespace {
+// A named range on the profiler's timeline for each hot-path call (NVTX, header-only; no cost
+// when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+}  // namespace
+
 extern "C" {
 
 const char* ihsbin_last_error(void) { return g_err.c_str(); }
@@ -263,6 +274,7 @@ ihsbin_status ihsbin_ctx_memory(const ihsbin_ctx* c, uint64_t* bytes) {
 
 ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, const void* B, int64_t K, int64_t ldb,
                                     ihsbin_dtype b_dtype, int b_on_device, ihsbin_problem** out) {
+  Range range_("ihsbin_problem_create");
   if (!ctx || !A || !B || !out) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: NULL argument");
   *out = nullptr;
   if (A->n <= 0 || A->d <= 0 || K <= 0 || ldb < K) return fail(IHSBIN_ERR_INVALID_ARG, "problem_create: bad sizes");
@@ -420,6 +432,7 @@ ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
 }
 
 ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream) {
+  Range range_("ihsbin_sketch");
   if (!p || !sk) return fail(IHSBIN_ERR_INVALID_ARG, "sketch: NULL argument");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   const int64_t N = p->A.N, D = p->A.D;
@@ -555,6 +568,7 @@ ihsbin_status ihsbin_sketch_entries_export(ihsbin_problem* p, int64_t row0, int6
 }
 
 ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, void* stream) {
+  Range range_("ihsbin_build_basis");
   if (!p || !d) return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: NULL argument");
   if (!p->sketched) return fail(IHSBIN_ERR_STATE, "build_basis: call ihsbin_sketch first");
   if (!(d->lambda_min > 0) || !(d->lambda_max >= d->lambda_min) || !std::isfinite(d->lambda_max))
@@ -746,6 +760,7 @@ ihsbin_status ihsbin_gram_export(ihsbin_problem* p, double* G) {
 
 ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t T, void* X, ihsbin_dtype x_dtype,
                                int x_on_device, void* stream) {
+  Range range_("ihsbin_eval_path");
   if (!p || !lambdas || !X) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: NULL argument");
   if (!p->built) return fail(IHSBIN_ERR_STATE, "eval_path: call ihsbin_build_basis first");
   if (T <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "eval_path: T must be positive");
@@ -791,6 +806,7 @@ ihsbin_status ihsbin_eval_path(ihsbin_problem* p, const double* lambdas, int64_t
 ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64_t T, const ihsbin_matrix* A_test,
                                  const void* B_test, int64_t ldb_test, ihsbin_dtype b_test_dtype, int b_test_on_device,
                                  double* train_loss, double* test_loss, void* stream) {
+  Range range_("ihsbin_path_losses");
   if (!p || !lambdas) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: NULL argument");
   if (!p->built) return fail(IHSBIN_ERR_STATE, "path_losses: call ihsbin_build_basis first");
   if (T <= 0) return fail(IHSBIN_ERR_INVALID_ARG, "path_losses: T must be positive");
@@ -867,6 +883,7 @@ ihsbin_status ihsbin_path_losses(ihsbin_problem* p, const double* lambdas, int64
 ihsbin_status ihsbin_adaptive_sketch(ihsbin_problem* p, const ihsbin_adaptive_desc* desc, ihsbin_adaptive_result* res,
                                      double* delta_trace, int64_t* m_trace, double* step_trace, int32_t trace_cap,
                                      double* x_out, void* stream) {
+  Range range_("ihsbin_adaptive_sketch");
   if (!p || !desc || !res) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: NULL argument");
   const double lam = desc->lambda;
   if (!(lam > 0) || !std::isfinite(lam)) return fail(IHSBIN_ERR_INVALID_ARG, "adaptive_sketch: lambda must be positive");

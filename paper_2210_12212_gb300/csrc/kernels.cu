@@ -829,10 +829,16 @@ __global__ void k_shift_copy(const double* GS, int64_t D, const double* lam0, CB
 
 constexpr int NB = 32;
 
-// Factor the diagonal block kb of every interval in place (unblocked, column by
-// column) and store the inverse of the resulting lower-triangular block.
+// Factor the diagonal block kb of every interval in place (unblocked, column by column) and store
+// the inverse of the resulting lower-triangular block (NB x NB, one CTA per interval).
+// The block is held in registers: warp w owns rows w, w + 8, w + 16,
+// w + 24 and lane c column c.  Column j of a step is published through shared memory (double
+// buffered, so one barrier per step), and every thread forms the pivot's square root and
+// reciprocal itself, so no thread waits on another's scalar work.  The inverse X = L^-1 is a
+// column sweep in the same layout: row k of X divided by L_kk, then subtracted from the rows
+// below with L's column k.
 template <class Mode>
-__global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, CBuf dinv, int* status) {
+__global__ void __launch_bounds__(256) k_potrf_diag_reg(CBuf H, int64_t D, int kb, CBuf dinv, int* status) {
   pdl_wait();  // launched with programmatic serialization
   pdl_trigger();
   using V = typename Mode::V;
@@ -840,67 +846,76 @@ __global__ void __launch_bounds__(256) k_potrf_diag(CBuf H, int64_t D, int kb, C
   const int64_t off = (int64_t)l * D * D;
   const int64_t r0 = (int64_t)kb * NB;
   const int nb = (D - r0 < NB) ? (int)(D - r0) : NB;
-  __shared__ V a[NB][NB + 1];
-  __shared__ V inv[NB][NB + 1];
-  __shared__ V red[8][NB];
+  const int w = threadIdx.x >> 5, c = threadIdx.x & 31;
+  __shared__ V col[2][NB];   // column j of L (step j)
+  __shared__ V xrow[2][NB];  // row k of X (inverse step k)
+  __shared__ V rdiag[NB];    // 1 / L_kk
   __shared__ int bad;
-  const int tid = threadIdx.x;
-  if (tid == 0) bad = 0;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int i = e / NB, j = e % NB;
-    a[i][j] = (i < nb && j < nb) ? Mode::ld(H, off + (r0 + i) * D + r0 + j) : Mode::zero();
+  if (threadIdx.x == 0) bad = 0;
+  V a[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = w + 8 * q;
+    a[q] = (i < nb && c < nb) ? Mode::ld(H, off + (r0 + i) * D + r0 + c) : (i == c ? Mode::from_d(1.0) : Mode::zero());
   }
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      V s = a[j][j];
-      double sd = Mode::to_d(s);
-      if (!(sd > 0.0)) {
-        bad = (sd != sd) ? DEV_NAN : DEV_NOT_SPD;
-        s = Mode::from_d(1.0);
+  // Cholesky: column j
+  for (int j = 0; j < NB; ++j) {
+    V* cj = col[j & 1];
+    if (c == j) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cj[w + 8 * q] = a[q];
+    }
+    __syncthreads();
+    V piv = cj[j];
+    if (!(Mode::to_d(piv) > 0.0)) {
+      if (threadIdx.x == 0 && j < nb) bad = (Mode::to_d(piv) != Mode::to_d(piv)) ? DEV_NAN : DEV_NOT_SPD;
+      piv = Mode::from_d(1.0);
+    }
+    const V d = Mode::sqrt_(piv);
+    const V rinv = Mode::div(Mode::from_d(1.0), d);
+    if (threadIdx.x == 0) rdiag[j] = rinv;
+    const V lc = Mode::mul(cj[c], rinv);  // L[c][j] for c > j
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = w + 8 * q;
+      if (c == j) {
+        a[q] = i > j ? Mode::mul(a[q], rinv) : (i == j ? d : a[q]);
+      } else if (c > j && i >= c) {
+        a[q] = Mode::sub(a[q], Mode::mul(Mode::mul(cj[i], rinv), lc));
       }
-      a[j][j] = Mode::sqrt_(s);
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) a[i][j] = Mode::div(a[i][j], a[j][j]);
-    __syncthreads();
-    // rank-1 update of the trailing lower triangle
-    for (int e = tid; e < (nb - j - 1) * (nb - j - 1); e += blockDim.x) {
-      int i = j + 1 + e / (nb - j - 1), c = j + 1 + e % (nb - j - 1);
-      if (c <= i) a[i][c] = Mode::sub(a[i][c], Mode::mul(a[i][j], a[c][j]));
-    }
-    __syncthreads();
-  }
-  // inverse of the lower-triangular block, row by row (forward substitution):
-  //   inv[i][c] = (delta_ic - sum_{c <= k < i} a[i][k] inv[k][c]) / a[i][i];
-  // thread (ks, c) = (tid / 32, tid % 32) forms the partial sum over k = c + ks, c + ks + 8, ...
-  {
-    const int c = tid & (NB - 1), ks = tid >> 5;  // blockDim.x = 256 = 8 x NB
-    for (int i = 0; i < NB; ++i) {
-      V s = Mode::zero();
-      if (i < nb && c < i)
-        for (int k = c + ks; k < i; k += 8) s = Mode::add(s, Mode::mul(a[i][k], inv[k][c]));
-      red[ks][c] = s;
-      __syncthreads();
-      if (ks == 0) {
-        if (i < nb && c <= i) {
-          V t = Mode::zero();
-          for (int q = 0; q < 8; ++q) t = Mode::add(t, red[q][c]);
-          t = Mode::sub(c == i ? Mode::from_d(1.0) : Mode::zero(), t);
-          inv[i][c] = Mode::div(t, a[i][i]);
-        } else {
-          inv[i][c] = Mode::zero();
-        }
-      }
-      __syncthreads();
     }
   }
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int i = e / NB, j = e % NB;
-    if (i < nb && j < nb) Mode::st(H, off + (r0 + i) * D + r0 + j, j <= i ? a[i][j] : Mode::zero());
-    Mode::st(dinv, ((int64_t)l * ((D + NB - 1) / NB) + kb) * NB * NB + e, inv[i][j]);
+  // X = L^-1 (column sweep), X lower triangular; x starts as the identity
+  V x[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) x[q] = (w + 8 * q == c) ? Mode::from_d(1.0) : Mode::zero();
+  __syncthreads();  // rdiag complete
+  for (int k = 0; k < NB; ++k) {
+    V* xr = xrow[k & 1];
+    V* lk = col[k & 1];
+    if (w == (k & 7)) xr[c] = Mode::mul(x[k >> 3], rdiag[k]);  // row k of X, final
+    if (c == k) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lk[w + 8 * q] = a[q];           // column k of L
+    }
+    __syncthreads();
+    const V xk = xr[c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = w + 8 * q;
+      if (i == k) x[q] = xk;
+      else if (i > k) x[q] = Mode::sub(x[q], Mode::mul(lk[i], xk));
+    }
   }
-  if (tid == 0 && bad) dev_fail(status, bad);
+  const int64_t dbase = ((int64_t)l * ((D + NB - 1) / NB) + kb) * NB * NB;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = w + 8 * q;
+    const bool in = i < nb && c < nb;
+    if (in) Mode::st(H, off + (r0 + i) * D + r0 + c, c <= i ? a[q] : Mode::zero());
+    Mode::st(dinv, dbase + i * NB + c, (in && c <= i) ? x[q] : Mode::zero());
+  }
+  if (threadIdx.x == 0 && bad) dev_fail(status, bad);
 }
 
 // panel rows below the diagonal block: L[i, kb] = H[i, kb] * Linv_kk^T  (in place)
@@ -1320,7 +1335,7 @@ static cudaError_t factor_and_invert(ihsbin_problem* p, CBuf H, CBuf Wm, CBuf di
   for (int kb = 0; kb < nblk; ++kb) {
     {
       KTimer kt(p, K_FACTOR_POTRF, st, (double)L * NB * NB * NB * 2.0 / 3.0, (double)L * NB * NB * cs * 3);
-      CK(launch_pdl(k_potrf_diag<Mode>, dim3(L), dim3(256), 0, st, H, D, kb, dinv, p->status));
+      CK(launch_pdl(k_potrf_diag_reg<Mode>, dim3(L), dim3(256), 0, st, H, D, kb, dinv, p->status));
     }
     CK(cudaGetLastError());
     const int64_t r0 = (int64_t)(kb + 1) * NB;
@@ -1875,7 +1890,10 @@ __global__ void k_eval_chunks(CBuf Bm, int64_t rows, int64_t K, int jc, int64_t 
   const int c = blockIdx.y;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= rows * K) return;
-  const int64_t r = e / rows, i = e % rows;
+  // X[t][i][r] is row-major with r fastest: for several right-hand sides consecutive threads take
+  // consecutive r, so that the writes (the dominant traffic) coalesce; for K < 4, consecutive i
+  const bool rfast = K >= 4;
+  const int64_t r = rfast ? e % K : e / rows, i = rfast ? e / K : e % rows;
   const int l = chunk_l[c], nq = chunk_n[c], t0 = chunk_t0[c];
   const int jn = jcount[l];
   int tq[EVAL_TB];
