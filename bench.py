@@ -82,6 +82,9 @@ def parse():
                     help="parameters from the sketch (rho from d_e, k from Theorem 4 at --eps) on both sides")
     ap.add_argument("--eps", type=float, default=1e-7)
     ap.add_argument("--requests", type=int, default=4096, help="serving workload (c5): number of requests")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="the workload's structure at this many rows (for profiling captures on a few GB; "
+                         "0 = the workload's own size)")
     ap.add_argument("--slots", type=int, default=6, help="serving workload (c5): concurrent slots")
     ap.add_argument("--adaptive", type=int, default=0, metavar="M0",
                     help="a step starts with Algorithm 4 from sketch dimension M0 at lambda_min (the path then "
@@ -258,7 +261,7 @@ def config_for(args, prob, par, world=1):
             "params": (f"tests/golden/{args.config[:-1] if args.config == 'c3t' else args.config}_params.json"
                        if par is not None and "tau" not in par else
                        "from the sketch (rho from d_e, k from Theorem 4 at eps)"),
-            "parallelism": f"replicas x{world}"}
+            "parallelism": f"replicas x{world}", **({"rows": args.rows} if args.rows else {})}
 
 
 def reference_arm(args, prob, par):
@@ -450,7 +453,7 @@ def main():
     if args.losses > 0:
         prob, A_test, B_test = make_split(args.config, args.losses, seed=0)
     else:
-        prob = make_problem(args.config, seed=0)
+        prob = make_problem(args.config, seed=0, **({"n": args.rows} if args.rows else {}))
     note(f"workload {args.config} generated")
     if args.adaptive:
         args.auto = True

@@ -746,7 +746,7 @@ __device__ void cluster_slice_column(const float* hi, const float* lo, const Col
 
 // The recursion's right-hand sides R (as k_make_R_oz) with their slicing fused: one cluster per
 // column of R, padded to NTL x NT per live interval.
-__global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo,
+__global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo,
                                                             int ny, int64_t ny_stride, const int* eg, const int* eu,
                                                             CBuf U, int64_t nold, int64_t nnew, int64_t D, int64_t K,
                                                             int inew, const int* perm, const double* tau,
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_make_R_oz_slice(const lo
 // The update of the recursion (as k_update_oz) with the next step's slicing of the new columns
 // fused: one cluster per new column (g, col); for an interval still live at the next step, the
 // new u is cut into the next step's concatenated-column layout (column g * ncol + col, tile NTn).
-__global__ void __launch_bounds__(OZ_COL_THREADS_MAX) k_update_oz_slice(const long long* Zhi, const long long* Zlo,
+__global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_update_oz_slice(const long long* Zhi, const long long* Zlo,
                                                             int S, const int* ep, int64_t ep_gs, const int* er,
                                                             int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K,
                                                             int i, CBuf Uin, CBuf Uout, CBuf Ut, const int* perm,
