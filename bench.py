@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--jmax", type=int, default=16)
     ap.add_argument("--slice-weight", type=int, default=0,
                     help="slice pairs kept by the recursion's tensor-core products (0 = 6: float-float class)")
+    ap.add_argument("--form", default="auto", choices=["auto", "residual", "increment"],
+                    help="how the tensor-core recursion carries the basis (auto = residual where it runs)")
+    ap.add_argument("--precond-weight", type=int, default=0,
+                    help="residual form: slice pairs kept by P_l r (0 = from the conditioning bound)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-check", action="store_true")
@@ -256,6 +260,7 @@ def config_for(args, prob, par, world=1):
                 f"inside each step" if args.adaptive else ""),
             "jmax": args.jmax,
             "slice_weight": args.slice_weight or 6,
+            "form": args.form, "precond_weight": args.precond_weight or "auto",
             "storage": prob.storage,
             "l2": L2_NOTE.get(args.config, "see workload"),
             "params": (f"tests/golden/{args.config[:-1] if args.config == 'c3t' else args.config}_params.json"
@@ -484,6 +489,7 @@ def main():
     else:
         bkw = dict(L=par["L"], k=par["k"], rho1=par["rho1"], rho2=par["rho2"], jmax=args.jmax,
                    compute=args.compute, slice_weight=args.slice_weight)
+    bkw.update(form=args.form, precond_weight=args.precond_weight)
     entries = "bf16" if prob.storage == "bf16" else "f64"
     if prob.layout == "csr":
         csr_dev = tuple(torch.from_numpy(np.ascontiguousarray(a)).cuda()
@@ -528,6 +534,10 @@ def main():
         step(p, X_dev)
     torch.cuda.synchronize()
     note("warm-up done")
+    recursion = None
+    if args.warmup > 0 and not args.adaptive:
+        f, w = p.recursion_form()
+        recursion = {"form": f, "precond_weight": w}
 
     # ---- timed region: K steps as a user runs them (no per-kernel events)
     def timed_steps(instrumented):
@@ -661,7 +671,7 @@ def main():
             "config": config_for(args, prob, par, world),
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
             "instrumented_ms_per_step": inst_ms / args.steps,
-            "phase_ms": phases,
+            "phase_ms": phases, "recursion": recursion,
             "tuning": [" ".join(x.split()[:1] + x.split()[2:3]) for x in ihs.tuning_report().splitlines()],
             "roofline": roof, "basis_roofline": basis_roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clk.summary(), "parity": check,

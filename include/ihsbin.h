@@ -181,6 +181,22 @@ typedef enum { IHSBIN_LOOP_AUTO = 0, IHSBIN_LOOP_SLICES = 1, IHSBIN_LOOP_FMA = 2
  *  FMA    : CUDA-core contraction in the compute mode's arithmetic. */
 typedef enum { IHSBIN_FACTOR_AUTO = 0, IHSBIN_FACTOR_SLICES = 1, IHSBIN_FACTOR_FMA = 2 } ihsbin_factor;
 
+/* Form in which the SLICES recursion carries the basis (the FMA kernels always run INCREMENT).
+ *  AUTO      : RESIDUAL where available (Gram product mode, D <= 20480) and the automatic
+ *              precond_weight below is at most 4, else INCREMENT.
+ *  INCREMENT : Algorithm 2 as printed: the per-step terms u_{i,j} are carried and added into
+ *              utilde_j; every product keeps slice_weight's pairs; the longest intervals switch to
+ *              the two-product steps with M_l = P_l (G + lam0_l I) once at most six are running.
+ *  RESIDUAL  : the same polynomial carried as its partial sums v_{i,j} = sum_{i' <= i} u_{i',j},
+ *              which are utilde_j after the last step.  Summing the recursion of Proposition 1 over
+ *              the steps gives v_j <- v_j + P_l r_j with the residual
+ *              r_j = [j = 0] c - tau (G + lam0 I) v_j - lam0 v_{j-1}  (re-centred, re-scaled form),
+ *              equal to the INCREMENT result in exact arithmetic.  An error made in applying P_l
+ *              reappears in the next residual and is removed by the following steps (the residual
+ *              correction of IHS), so only G v needs the float-float class: P_l r keeps the pairs
+ *              s + t <= precond_weight. */
+typedef enum { IHSBIN_FORM_AUTO = 0, IHSBIN_FORM_RESIDUAL = 1, IHSBIN_FORM_INCREMENT = 2 } ihsbin_form;
+
 typedef struct {
   double lambda_min, lambda_max;
   int32_t L;
@@ -209,6 +225,16 @@ typedef struct {
                          * are kept (0 selects 6, the float-float accuracy class; 4 or 5 drop the pairs
                          * weighing below 2^-40 / 2^-48 of an entry's leading product, 1.8x / 1.3x fewer
                          * tensor-core products; the Gram of A keeps every pair it needs regardless) */
+  int32_t form;          /* ihsbin_form (0 = AUTO) */
+  int32_t precond_weight; /* RESIDUAL form: the slice pairs kept by the P_l r products (1..6; each step
+                           * of 1 divides the weight of the dropped pairs by 2^8; up to 3 the
+                           * products run on 64-column tiles).  0 = the smallest w in 2..5 with
+                           * (1) 2^(-8(w+1)) sqrt(D) kappa <= 2^-5, kappa = 1 + tr(G_S) / min_l lam0_l
+                           * (the iteration map keeps its contraction), and
+                           * (2) 2^(-8(w+1)) max_l k_l rate_l^(k_l - 1) <= max_l k_l 2^-47, rate_l
+                           * Theorem 4's contraction bound of interval l (the error the steps carry
+                           * to the end is no larger than the increment form's); 6 when none is.
+                           * A nonzero value selects the RESIDUAL form under AUTO. */
 } ihsbin_path_desc;
 
 typedef struct ihsbin_ctx ihsbin_ctx;
@@ -290,6 +316,10 @@ IHSBIN_API ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path
  * A-space (no Gram is formed). */
 IHSBIN_API ihsbin_status ihsbin_gram_export(ihsbin_problem* p, double* G);
 
+/* The form and the preconditioner pair weight the last ihsbin_build_basis ran with (ihsbin_form
+ * RESIDUAL or INCREMENT; in the INCREMENT form the weight is slice_weight's).  Either pointer may be NULL.
+ * Fails with STATE before the first build. */
+IHSBIN_API ihsbin_status ihsbin_recursion_form(const ihsbin_problem* p, int32_t* form, int32_t* precond_weight);
 /* The plan the library derived from the descriptor: arrays of L (edges: L+1),
  * any may be NULL; *L_out receives L.  Fails with INVALID_ARG if cap_L < L. */
 IHSBIN_API ihsbin_status ihsbin_plan_export(ihsbin_problem* p, double* edges, double* lam0, double* tau,

@@ -242,6 +242,39 @@ def basis(AtA: Callable, P: Precond, c: np.ndarray, tau: float, k: int, jmax: in
     return ut
 
 
+def basis_partial_sums(AtA: Callable, P: Precond, c: np.ndarray, tau: float, k: int, jmax: int = 0,
+                       solve: Optional[Callable] = None) -> np.ndarray:
+    """The recursion of `basis` carried as its partial sums v_{i,j} = sum_{i' <= i} u_{i',j}.
+
+    Summing the re-centred recursion u_{i+1,j} = B0 u_{i,j} - Q u_{i,j-1} (B0 = I - tau P H0,
+    H0 = A^T A + lam0 I, Q = lam0 P) over the steps 0..i gives, with u_00 = P c,
+        v_{i+1,j} = v_{i,j} + P r_{i,j},
+        r_{i,j} = [j = 0] c - tau H0 v_{i,j} - lam0 v_{i,j-1},
+    i.e. the fixed-preconditioner IHS update (Section 3, eq. equ:ihs) x <- x + tau P (A^T b -
+    (A^T A + lam I) x) taken coefficient by coefficient in theta.  v_{k-1,j} = utilde_j, so the
+    result equals `basis` in exact arithmetic (same shape, same truncation at jmax: r_j reads
+    v_j and v_{j-1} only).  `solve` replaces P.solve (tests apply a perturbed preconditioner).
+    """
+    lam0 = P.lam0
+    solve = solve or P.solve
+    c = np.atleast_2d(c.T).T if c.ndim == 1 else c
+    D, K = c.shape
+    J = k if jmax <= 0 else min(k, jmax)
+    v = np.zeros((J, D, K))
+    v[0] = solve(c)                                     # v_00 = u_00 = P A^T b
+    for i in range(1, k):
+        live = min(i, J)                                # v_j != 0 for j < i before the step
+        Y = AtA(np.concatenate(list(v[:live]), axis=1)).reshape(D, live, K)
+        new = v.copy()
+        for j in range(min(i + 1, J)):
+            r = -lam0 * v[j - 1] if j > 0 else c.astype(float).copy()
+            if j < live:
+                r = r - tau * (Y[:, j] + lam0 * v[j])
+            new[j] = v[j] + solve(r)
+        v = new
+    return v
+
+
 def evaluate(ut: np.ndarray, tau: float, lam0: float, lam: float) -> np.ndarray:
     """x_k(lam) = tau * sum_j theta^j utilde_j, theta = tau (lam - lam0) / lam0."""
     theta = tau * (lam - lam0) / lam0

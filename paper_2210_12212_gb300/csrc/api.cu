@@ -581,6 +581,10 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: slice_weight must be 0 or 4..6");
   if (d->compute != IHSBIN_COMPUTE_F64 && d->compute != IHSBIN_COMPUTE_F32X2)
     return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown compute mode");
+  if (d->form != IHSBIN_FORM_AUTO && d->form != IHSBIN_FORM_RESIDUAL && d->form != IHSBIN_FORM_INCREMENT)
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: unknown recursion form");
+  if (d->precond_weight < 0 || d->precond_weight > 6)
+    return fail(IHSBIN_ERR_INVALID_ARG, "build_basis: precond_weight must be 0..6");
   Plan pl;
   const double beta = d->lambda_max / d->lambda_min;
   pl.L = d->L > 0 ? d->L : std::max(1, (int)std::floor(2.0 * std::log(beta)));
@@ -602,6 +606,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   pl.rho2.resize(L);
   pl.sigma_d2 = d->sigma_d2;
   pl.slice_w = d->slice_weight > 0 ? d->slice_weight : 6;
+  pl.form = d->form;
+  pl.precond_req = d->precond_weight;
   if (d->tau) {
     pl.tau_user.assign(d->tau, d->tau + L);
     for (double t : pl.tau_user)
@@ -693,6 +699,14 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
     return s;
   }
   p->built = true;
+  return IHSBIN_OK;
+}
+
+ihsbin_status ihsbin_recursion_form(const ihsbin_problem* p, int32_t* form, int32_t* precond_weight) {
+  if (!p) return fail(IHSBIN_ERR_INVALID_ARG, "recursion_form: NULL");
+  if (!p->built || p->plan.form_run == 0) return fail(IHSBIN_ERR_STATE, "recursion_form: no basis built");
+  if (form) *form = p->plan.form_run;
+  if (precond_weight) *precond_weight = p->plan.precond_w;
   return IHSBIN_OK;
 }
 

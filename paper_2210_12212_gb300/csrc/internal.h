@@ -52,6 +52,9 @@ struct Plan {
   int loop = IHSBIN_LOOP_FMA;   // resolved product kernel of the basis recursion (never AUTO)
   int factor = IHSBIN_FACTOR_FMA;  // resolved kernel of the explicit inverse (never AUTO)
   int slice_w = 6;                 // slice pairs kept by the recursion's and the inverse's products
+  int form = IHSBIN_FORM_AUTO;     // requested; resolved by the build into form_run
+  int precond_req = 0;             // requested pair weight of the residual form's P_l r (0: from the bound)
+  int form_run = 0, precond_w = 6; // what the last build ran (0: no build yet)
   // parameters completed after the factor phase (rho from the sketch, k from Theorem 4)
   bool auto_rho = false, auto_k = false;
   double eps = 1e-7;
@@ -216,7 +219,7 @@ uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);
 
 // Exact-slice tensor-core products of the basis recursion (tc_loop.cu).  A operands
 // (D x D, rows sliced, once per build) and B operands (column panels, every step).
-int oz_tile_n(int64_t ncolg);
+int oz_tile_n(int64_t ncolg, int wmax = 6);  // 64-column tiles for products keeping s + t <= 3
 size_t oz_rows_elems(int64_t D);
 size_t oz_rows_exps(int64_t D);
 size_t oz_cols_elems(int64_t D, int64_t ncolg, int NT);
@@ -283,11 +286,11 @@ bool oz_fused_ok(int64_t D);
 cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
                             const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
                             const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
-                            __nv_bfloat16* Rs, int* er, cudaStream_t st);
+                            __nv_bfloat16* Rs, int* er, CBuf c, cudaStream_t st);
 cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
                             const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
                             CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
-                            int* eu, cudaStream_t st);
+                            int* eu, int resid, cudaStream_t st);
 // device bytes of the recursion's slices (G, every P_l, one step's B operand)
 uint64_t loop_slices_bytes(int64_t D, int L, int64_t ncol_max);
 cudaError_t csr_rhs(ihsbin_problem* p, int compute, CBuf c, cudaStream_t st);

@@ -1664,7 +1664,56 @@ struct OzLoop {
   const __nv_bfloat16* Ms = nullptr;
   const int* em = nullptr;
   int* eb2 = nullptr;
+  // residual form (fused path only): U aliases Ut, which holds the partial sums v; c enters the
+  // j = 0 residual; P_l R keeps the slice pairs s + t <= pw
+  bool resid = false;
+  int pw = 6;
 };
+
+// tr(G_S) in FP64 (one CTA of 256 threads), for the residual form's pair-weight rule
+__global__ void k_diag_sum(const double* M, int64_t D, double* out) {
+  __shared__ double part[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < D; i += blockDim.x) s += M[i * D + i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = part[0];
+}
+
+// The residual form's default pair weight for P_l r.  Dropping the pairs s + t > w makes each
+// application of P_l wrong by about eps_w = 2^(-8(w+1)) of |P_l| |r| (relative to the row and
+// column maxima), i.e. by up to kappa eps_w relative, kappa <= 1 + tr(G_S) / lam0 bounding the
+// conditioning of the shifted sketched Hessian.  Two conditions on w:
+//  (1) the iteration map I - tau P_l (G + lam0 I) changes by at most sqrt(D) kappa eps_w <= 2^-5,
+//      so it keeps its contraction;
+//  (2) the error carried to the end is no larger than the increment form's own: there step i's
+//      error is damped by the later steps to about rate^(k-1-i) of it while |r_i| falls like
+//      rate^i, so the k steps leave about g kappa eps_w of x, g = max_l k_l rate_l^(k_l - 1), with
+//      rate Theorem 4's bound max(|1 - tau e_min|, |1 - tau e_max|) over the interval's spectrum
+//      bounds e = rho2 (lo + s) / (lam0 + s) .. rho1 (hi + s) / (lam0 + s); the increment form keeps
+//      every step's rounding of 2^-47 kappa (the slices hold each entry to 2^-47 of its row's
+//      maximum), about k_max kappa 2^-47 in all.  So g eps_w <= k_max 2^-47.
+// Returns the smallest such w in 2..5, or 6 when none qualifies.
+static int precond_weight_rule(int64_t D, double trGS, const Plan& pl) {
+  double lmin = pl.lam0[0], g = 0.0;
+  for (int l = 0; l < pl.L; ++l) {
+    lmin = std::min(lmin, pl.lam0[l]);
+    const double s2 = pl.sigma_d2, lo = pl.edges[l], hi = pl.edges[l + 1];
+    const double emin = pl.rho2[l] * (lo + s2) / (pl.lam0[l] + s2), emax = pl.rho1[l] * (hi + s2) / (pl.lam0[l] + s2);
+    const double rate = std::max(std::fabs(1.0 - pl.tau[l] * emin), std::fabs(1.0 - pl.tau[l] * emax));
+    g = std::max(g, pl.k[l] * std::pow(rate, pl.k[l] - 1));
+  }
+  const double kappa = 1.0 + trGS / lmin;
+  for (int w = 2; w < 6; ++w) {
+    const double ew = std::ldexp(1.0, -8 * (w + 1));
+    if (std::sqrt((double)D) * kappa * ew <= std::ldexp(1.0, -5) && g * ew <= pl.kmax * std::ldexp(1.0, -47)) return w;
+  }
+  return 6;
+}
 
 template <class Mode, int ET>
 static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf Y, CBuf Z, CBuf R, CBuf Wtmp,
@@ -1686,6 +1735,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
   }
   CBuf Uin = U0, Uout = U1;
   const int J = pl.jmax > 0 ? pl.jmax : (1 << 30);
+  const int pw = oz.resid ? oz.pw : pl.slice_w;  // pair weight of the P_l R products
   for (int i = 1; i < pl.kmax; ++i) {
     int live = 0;
     while (live < L && pl.k[order[live]] > i) ++live;
@@ -1778,7 +1828,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     if (fused) {
       KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ny + 24 + 12));
       CK(oz_make_R_slice(oz.Yhi, oz.Ylo, ny, (int64_t)live * ys, oz.eg, oz.eb, Uin, live, nold, nnew, D, K, inew,
-                         perm_dev, tau_dev, lam0_dev, gs, oz_tile_n(nnew), oz.Bs, oz.er, st));
+                         perm_dev, tau_dev, lam0_dev, gs, oz_tile_n(nnew, pw), oz.Bs, oz.er, oz.resid ? c : CBuf{}, st));
     } else if (oz.on && pl.product == IHSBIN_PRODUCT_GRAM) {
       KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ny + 24));
       k_make_R_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
@@ -1793,7 +1843,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
     }
     if (oz.on) {
       // P_l R_l of every live interval, on the tensor cores
-      const int NT = oz_tile_n(nnew);
+      const int NT = oz_tile_n(nnew, pw);
       int* erv = fused ? oz.er : oz.eb;  // column exponents of R
       if (!fused) {
         KTimer kt(p, K_LOOP_SLICE, st, 0, 20.0 * D * nnew * live);
@@ -1801,11 +1851,13 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       }
       const int ks = oz_pick_split(D, nnew, live, NT, SPLIT_MAX);
       {
+        // the residual form's P_l R keeps the pairs s + t <= pw and reads only the slices 0 .. pw
+        const double fsl = (std::min(pw, 5) + 1) / 6.0;
         KTimer kt(p, K_LOOP_P_TC, st, 2.0 * D * D * nnew * live, (double)live * D * D * 8 + 16.0 * D * nnew * live,
-                  oz_pair_flops(D, nnew, D, pl.slice_w) * live,
-                  (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) + 16.0 * ks * D * nnew * live);
+                  oz_pair_flops(D, nnew, D, pw) * live,
+                  (double)live * (oz_rows_elems(D) * 2 + oz_cols_elems(D, nnew, NT) * 2) * fsl + 16.0 * ks * D * nnew * live);
         CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, erv, D, nnew, live, NT, ks, oz.Zhi, oz.Zlo, p->status,
-                      st, pl.slice_w));
+                      st, pw));
       }
       if (fused) {
         // the intervals still running at the next step take their new columns' slices now
@@ -1814,7 +1866,8 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
                                                                                        : 16;
         KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24 + 12));
         CK(oz_update_slice(oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er, (int64_t)oz_cols_exps(nnew, NT),
-                           live, nnew, D, K, i, Uin, Uout, p->Ut, perm_dev, gs, live_next, NTn, oz.Bs, oz.eb, st));
+                           live, nnew, D, K, i, Uin, Uout, p->Ut, perm_dev, gs, live_next, NTn, oz.Bs, oz.eb,
+                           oz.resid ? 1 : 0, st));
       } else {
         KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24));
         k_update_oz<<<nblocks((int64_t)live * nnew * D, 256), 256, 0, st>>>(
@@ -1944,6 +1997,22 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaMemcpyAsync(lam0_dev, pl.lam0.data(), L * sizeof(double), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(perm_dev, order.data(), L * sizeof(int), cudaMemcpyHostToDevice, st));
 
+  // the recursion's form (resolved after the factorization, when the plan is final): the residual
+  // form is possible where the fused tensor-core recursion runs; every other configuration carries
+  // the increments of Algorithm 2 as printed.  tr(G_S) for the default pair weight is read here,
+  // where the stream is idle (the sketch call ended with a synchronisation).
+  const bool oz_on = Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES;
+  const bool resid_ok = oz_on && pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D) && pl.form != IHSBIN_FORM_INCREMENT;
+  double trGS = 0.0;
+  if (resid_ok && pl.precond_req == 0) {
+    double* tr_dev = nullptr;
+    CK(prob_alloc(p, sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH));
+    k_diag_sum<<<1, 256, 0, st>>>(p->GS, D, tr_dev);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&trGS, tr_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+  }
+
   // SMs the Gram's tensor-core launches leave to the factorization running beside them: chosen by
   // the autotuner per shape class, timing the whole fork-join region of both streams
   const bool tune_reserve =
@@ -2033,13 +2102,24 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CK(cudaEventRecord(ev[6], st));
   if (tune_reserve) tune_end(rtune, st);
 
-  // a4: the recursion
+  // a4: the recursion, in the residual form when it is possible and asked for (RESIDUAL, or an
+  // explicit precond_weight) or when AUTO's pair weight is at most 4
+  int pw = pl.slice_w;
+  bool resid = false;
+  if (resid_ok) {
+    pw = pl.precond_req > 0 ? pl.precond_req : precond_weight_rule(D, trGS, pl);
+    // AUTO: from weight 5 on the products save little (21 of 26 pairs) and the increment form's
+    // two-product steps at the end of the longest intervals are faster
+    resid = pl.form == IHSBIN_FORM_RESIDUAL || pl.precond_req > 0 || pw <= 4;
+  }
+  pl.form_run = resid ? IHSBIN_FORM_RESIDUAL : IHSBIN_FORM_INCREMENT;
+  pl.precond_w = resid ? pw : pl.slice_w;
   const size_t per = (size_t)pl.jc * K * D;
-  CBuf U0 = cb(per * L), U1 = cb(per * L);
   p->Ut = alloc_cbuf(p, cm, per * L, SCOPE_BASIS, &err);
   CK(err);
+  // the residual form keeps only the partial sums (in Ut); the increment form ping-pongs U0 / U1
+  CBuf U0 = resid ? p->Ut : cb(per * L), U1 = resid ? p->Ut : cb(per * L);
   const int64_t ncol_max = (int64_t)pl.jc * K;
-  const bool oz_on = Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES;
   // the tensor-core products leave exact int64 partials instead of float-float ones
   CBuf Y = cb((oz_on && pl.product == IHSBIN_PRODUCT_GRAM) ? 1 : (size_t)SPLIT_MAX * ncol_max * D * L);
   CBuf Z = cb(oz_on ? 1 : (size_t)SPLIT_MAX * ncol_max * D * L);
@@ -2047,14 +2127,16 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   CBuf Wtmp{};
   if (pl.product == IHSBIN_PRODUCT_ASPACE) Wtmp = cb((size_t)ncol_max * A.N * L);
   CK(err);
-  CK(cudaMemsetAsync(U0.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
-  if (U0.p1) CK(cudaMemsetAsync(U0.p1, 0, per * L * 4, st));
+  if (!resid) {
+    CK(cudaMemsetAsync(U0.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
+    if (U0.p1) CK(cudaMemsetAsync(U0.p1, 0, per * L * 4, st));
+  }
   CK(cudaMemsetAsync(p->Ut.p0, 0, per * L * (cm == IHSBIN_COMPUTE_F64 ? 8 : 4), st));
   if (p->Ut.p1) CK(cudaMemsetAsync(p->Ut.p1, 0, per * L * 4, st));
   OzLoop oz;
   if (oz_on) {
     oz.on = true;
-    const int64_t bcols = (int64_t)L * (ncol_max + 32);
+    const int64_t bcols = (int64_t)L * (ncol_max + 64);  // columns padded to the tile width (<= 64)
     __nv_bfloat16 *Ps = nullptr, *Bs = nullptr;
     int *ep = nullptr, *eb = nullptr;
     CK(prob_alloc(p, oz_rows_elems(D) * 2 * L, (void**)&Ps, SCOPE_SCRATCH));
@@ -2067,9 +2149,12 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     // tile height 16) at which at most MFORM_LIVE intervals are still running.  It spends one D^3
     // product per interval on M_q = P_l (G + lam0_l I) and saves two of the four launches of every
     // later step.
+    // (Not in the residual form: there M_l v would carry the residual, so both of its products
+    // would need every pair, while the residual form's P_l r needs few.)
     constexpr int MFORM_LIVE = 6;
     int mform_from = 0, Tm = 0;
-    if (pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D) && pl.jmax > 0 && ((int64_t)pl.jmax * K) % 16 == 0) {
+    if (!resid && pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D) && pl.jmax > 0 &&
+        ((int64_t)pl.jmax * K) % 16 == 0) {
       for (int i = std::max(pl.jmax, 2); i < pl.kmax; ++i) {
         int live = 0;
         while (live < L && pl.k[order[live]] > i) ++live;
@@ -2097,7 +2182,8 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
         const int64_t ncat = nold * live;
         if (pl.product == IHSBIN_PRODUCT_GRAM)
           ymax = std::max(ymax, (size_t)oz_pick_split(D, ncat, 1, oz_tile_n(ncat), SPLIT_MAX) * ncat * D);
-        zmax = std::max(zmax, (size_t)oz_pick_split(D, nnew, live, oz_tile_n(nnew), SPLIT_MAX) * live * nnew * D);
+        zmax = std::max(zmax, (size_t)oz_pick_split(D, nnew, live, oz_tile_n(nnew, resid ? pw : pl.slice_w), SPLIT_MAX) *
+                                  live * nnew * D);
       }
     }
     CK(prob_alloc(p, ymax * 8, (void**)&oz.Yhi, SCOPE_SCRATCH));
@@ -2122,6 +2208,8 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     oz.ep = ep;
     oz.Bs = Bs;
     oz.eb = eb;
+    oz.resid = resid;
+    oz.pw = pl.precond_w;
     if (mform_from > 0) {
       // M_q = P_l G + lam0_l P_l for l = order[q], q < Tm: the exact-slice product G P_l (A = the
       // rows of G, shared; B = the columns of P_l), joined with lam0_l P_l, then cut by rows

@@ -58,19 +58,28 @@ constexpr int OZ_CHUNK = 4;          // k-blocks between drains (6 x 128 x 2^14 
 constexpr int OZ_KB_MAX = 512;       // k-blocks per CTA (int32 sums: 6 x 16384 x 2^14 < 2^31)
 constexpr int OZ_NONFINITE = OZ_EXP_NONFINITE;
 
+// NT = 16 / 32: every weight 0..6 (seven accumulators per buffer).  NT = 64 ("wide"): products
+// that keep only the pairs s + t <= 3 (the residual form's P_l r), four accumulators of 64
+// columns per buffer, and a stage holding the four slices those pairs read.
 template <int NT>
 struct OzCfg {
+  static constexpr bool WIDE = NT == 64;
+  static constexpr int WMAX = WIDE ? 3 : OZ_W;          // largest pair weight the layout holds
   static constexpr int BBLK = NT * OZ_BK;               // B block: NT rows x 32 k
-  static constexpr int A_BYTES = OZ_S * OZ_ABLK * 2;    // 48 KiB
-  static constexpr int B_BYTES = OZ_S * BBLK * 2;       // 6 / 12 KiB copied per stage
-  static constexpr int B_SLOT = (OZ_S + 1) * BBLK * 2;  // plus one all-zero slice (see the MMA issue)
+  static constexpr int A_BYTES = (WMAX + 1 < OZ_S ? WMAX + 1 : OZ_S) * OZ_ABLK * 2;  // 48 / 32 KiB
+  static constexpr int B_BYTES = (WMAX + 1 < OZ_S ? WMAX + 1 : OZ_S) * BBLK * 2;     // 6 / 12 / 16 KiB
+  // plus one all-zero slice where the s = 0 MMA reaches weight 6 (see the MMA issue)
+  static constexpr int B_SLOT = B_BYTES + (WIDE ? 0 : BBLK * 2);
   static constexpr int STAGE = A_BYTES + B_SLOT;
-  static constexpr int STAGES = NT == 16 ? 4 : 3;
-  static constexpr int SMEM = STAGES * STAGE;              // 220 / 186 KiB
+  static constexpr int STAGES = NT == 32 ? 3 : 4;
+  static constexpr int SMEM = STAGES * STAGE;              // 220 / 186 / 192 KiB
   static constexpr int EPI_WARPS = NT == 16 ? 4 : 8;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
-  static constexpr int COLS = NT == 16 ? 256 : 512;     // two buffers of 7 accumulators
-  static constexpr int WPG = NT == 16 ? OZ_NW : 4;      // weights per epilogue warpgroup
+  static constexpr int COLS = NT == 16 ? 256 : 512;     // two buffers of (WMAX + 1) NT accumulator columns
+  // an epilogue warpgroup drains WPG weights of EC columns: NT = 32 splits the weights between
+  // the two warpgroups, NT = 64 the columns
+  static constexpr int WPG = NT == 16 ? OZ_NW : 4;
+  static constexpr int EC = WIDE ? 32 : NT;
 };
 
 struct OzArgs {
@@ -154,9 +163,10 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
     tc::bar_init_fence();
   }
   // the seventh B slice of every stage stays zero (the copies fill slices 0..5 only)
-  for (int st = 0; st < C::STAGES; ++st)
-    for (int x = tid; x < C::BBLK * 2 / 16; x += C::THREADS)
-      reinterpret_cast<uint4*>(smem + st * C::STAGE + C::A_BYTES + C::B_BYTES)[x] = make_uint4(0, 0, 0, 0);
+  if constexpr (!C::WIDE)
+    for (int st = 0; st < C::STAGES; ++st)
+      for (int x = tid; x < C::BBLK * 2 / 16; x += C::THREADS)
+        reinterpret_cast<uint4*>(smem + st * C::STAGE + C::A_BYTES + C::B_BYTES)[x] = make_uint4(0, 0, 0, 0);
   tc::fence_proxy_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -169,6 +179,9 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
 
   if (warp == 0) {
     if (lane == 0) {  // producer
+      // only the slices 0 .. wmax of either operand meet a kept pair: a prefix of each block
+      const int nsl = min(a.wmax, OZ_S - 1) + 1;
+      const uint32_t a_bytes = (uint32_t)nsl * OZ_ABLK * 2, b_bytes = (uint32_t)nsl * C::BBLK * 2;
       uint32_t q = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
@@ -188,9 +201,9 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
             break;
           }
           const uint32_t sa = tc::smem_addr(smem + st * C::STAGE), fb = tc::smem_addr(&full[st]);
-          tc::bar_arrive_tx(fb, C::A_BYTES + C::B_BYTES);
-          tc::bulk_load(sa, gA + (int64_t)it * (OZ_S * OZ_ABLK), C::A_BYTES, fb);
-          tc::bulk_load(sa + C::A_BYTES, gB + (int64_t)it * (OZ_S * C::BBLK), C::B_BYTES, fb);
+          tc::bar_arrive_tx(fb, a_bytes + b_bytes);
+          tc::bulk_load(sa, gA + (int64_t)it * (OZ_S * OZ_ABLK), a_bytes, fb);
+          tc::bulk_load(sa + C::A_BYTES, gB + (int64_t)it * (OZ_S * C::BBLK), b_bytes, fb);
         }
       }
       // the copies of the last stages land before the CTA may leave
@@ -249,17 +262,18 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
       tc::commit(tc::smem_addr(&done));
       tc::bar_wait(tc::smem_addr(&done), 0);
     }
-  } else {  // epilogue warps: warpgroup qg drains weights [qg * WPG, qg * WPG + WPG)
+  } else {  // epilogue warps: warpgroup qg drains weights [w0, w0 + WPG) of columns [c0, c0 + EC)
     const int qg = (warp - 2) >> 2, lq = warp & 3;
-    const int w0 = qg * C::WPG;
+    const int w0 = C::WIDE ? 0 : qg * C::WPG;
+    const int c0 = C::WIDE ? qg * C::EC : 0;
     const int r = lq * 32 + lane;  // Tensor Memory lane = row of the tile
     uint32_t cc = 0;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
       const Item w = decode(item);
       const int nch = (w.nkb + OZ_CHUNK - 1) / OZ_CHUNK;
-      int acc[C::WPG * NT];
+      int acc[C::WPG * C::EC];
 #pragma unroll
-      for (int x = 0; x < C::WPG * NT; ++x) acc[x] = 0;
+      for (int x = 0; x < C::WPG * C::EC; ++x) acc[x] = 0;
       for (int c = 0; c < nch; ++c, ++cc) {
         const int h = cc & 1;
         if (!tc::bar_wait(tc::smem_addr(&tfull[h]), (cc >> 1) & 1) || *abort_v) {
@@ -272,19 +286,19 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
         for (int wi = 0; wi < C::WPG; ++wi) {
           if (w0 + wi > a.wmax) continue;  // warp-uniform; weights above wmax stay zero
           const uint32_t ta =
-              tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT);
-          if constexpr (NT == 16) {
+              tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(h * (C::COLS / 2) + (w0 + wi) * NT + c0);
+          if constexpr (C::EC == 16) {
             uint32_t v[16];
             tc::tmem_ld16(ta, v);
             tc::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+            for (int j = 0; j < 16; ++j) acc[wi * C::EC + j] += __float2int_rn(__uint_as_float(v[j]));
           } else {
             uint32_t v[32];
             tc::tmem_ld32(ta, v);
             tc::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) acc[wi * NT + j] += __float2int_rn(__uint_as_float(v[j]));
+            for (int j = 0; j < 32; ++j) acc[wi * C::EC + j] += __float2int_rn(__uint_as_float(v[j]));
           }
         }
         tc::fence_before_sync();
@@ -298,18 +312,24 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
       // converts (with the row / column exponents) at full occupancy:
       //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6.
       const int64_t i = (int64_t)w.mt * 128 + r;
+      constexpr int E = C::EC;
       if (i < a.M && !w.skip) {
 #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          const int64_t jj = (int64_t)w.nt * NT + j;
+        for (int j = 0; j < E; ++j) {
+          const int64_t jj = (int64_t)w.nt * NT + c0 + j;
           if (jj >= a.N) break;
           const int64_t o = (((int64_t)w.sp * a.groups + w.g) * a.N + jj) * a.M + i;
-          if (qg == 0)
-            a.ohi[o] = (((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j]) * 256 + acc[3 * NT + j];
-          if constexpr (C::EPI_WARPS == 8) {
-            if (qg == 1) a.olo[o] = ((long long)acc[j] * 256 + acc[NT + j]) * 256 + acc[2 * NT + j];  // weights 4..6
+          if constexpr (C::WIDE) {  // weights 0..3 only
+            a.ohi[o] = (((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j]) * 256 + acc[3 * E + j];
+            a.olo[o] = 0;
           } else {
-            a.olo[o] = ((long long)acc[4 * NT + j] * 256 + acc[5 * NT + j]) * 256 + acc[6 * NT + j];
+            if (qg == 0)
+              a.ohi[o] = (((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j]) * 256 + acc[3 * E + j];
+            if constexpr (C::EPI_WARPS == 8) {
+              if (qg == 1) a.olo[o] = ((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j];  // weights 4..6
+            } else {
+              a.olo[o] = ((long long)acc[4 * E + j] * 256 + acc[5 * E + j]) * 256 + acc[6 * E + j];
+            }
           }
         }
       }
@@ -745,13 +765,15 @@ __device__ void cluster_slice_column(const float* hi, const float* lo, const Col
 }
 
 // The recursion's right-hand sides R (as k_make_R_oz) with their slicing fused: one cluster per
-// column of R, padded to NTL x NT per live interval.
+// column of R, padded to NTL x NT per live interval.  In the residual form U holds the partial
+// sums v_j and Cr the right-hand side c: R is then minus the residual,
+//   R_j = tau (G v_j + lam0 v_j) + lam0 v_{j-1} - [j = 0] c.
 __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_make_R_oz_slice(const long long* Yhi, const long long* Ylo,
                                                             int ny, int64_t ny_stride, const int* eg, const int* eu,
                                                             CBuf U, int64_t nold, int64_t nnew, int64_t D, int64_t K,
                                                             int inew, const int* perm, const double* tau,
                                                             const double* lam0, int64_t gs, int NT, int NTL, int KB,
-                                                            int KBC, __nv_bfloat16* Rs, int* er) {
+                                                            int KBC, __nv_bfloat16* Rs, int* er, CBuf Cr) {
   extern __shared__ float colbuf[];  // hi[KBC 32], lo[KBC 32]
   __shared__ float red[OZ_COL_THREADS_MAX / 32];
   __shared__ float smax;
@@ -779,6 +801,7 @@ __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_make_R_oz_slice(const
         oz_sum_splits2(Yhi, Ylo, ny, ny_stride, yo, yo, false, h, w, h2, w2);
         r = dd_mul(tl, dd_add(oz_join(h, w, eg[k], eu[cc]), dd_mul(lm, DD::ld(U, o))));
         if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
+        else if (Cr.p0) r = dd_sub(r, DD::ld(Cr, col * D + k));  // residual form: minus c in the j = 0 term
       }
       bh[k - pt.r0] = r.hi;
       bl[k - pt.r0] = r.lo;
@@ -794,12 +817,13 @@ __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_make_R_oz_slice(const
 // The update of the recursion (as k_update_oz) with the next step's slicing of the new columns
 // fused: one cluster per new column (g, col); for an interval still live at the next step, the
 // new u is cut into the next step's concatenated-column layout (column g * ncol + col, tile NTn).
+// Residual form (resid != 0): Ut holds the partial sums v, updated in place, and v is cut.
 __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_update_oz_slice(const long long* Zhi, const long long* Zlo,
                                                             int S, const int* ep, int64_t ep_gs, const int* er,
                                                             int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K,
                                                             int i, CBuf Uin, CBuf Uout, CBuf Ut, const int* perm,
                                                             int64_t gs, int live_next, int NTn, int KB, int KBC,
-                                                            __nv_bfloat16* Us, int* eu) {
+                                                            __nv_bfloat16* Us, int* eu, int resid) {
   extern __shared__ float colbuf[];
   __shared__ float red[OZ_COL_THREADS_MAX / 32];
   __shared__ float smax;
@@ -819,10 +843,15 @@ __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_update_oz_slice(const
     oz_sum_splits2(Zhi, Zlo, S, ss, zo, zo, false, h, w, h2, w2);
     const dd z = oz_join(h, w, ep[(int64_t)l * ep_gs + row], ec);
     const int64_t o = (int64_t)l * gs + col * D + row;
-    dd u = (j < i) ? DD::ld(Uin, o) : DD::zero();
-    u = dd_sub(u, z);
-    DD::st(Uout, o, u);
-    DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
+    dd u;
+    if (resid) {  // v_j <- v_j - P_l R_j, in place (a new term's v is still zero)
+      u = dd_sub(DD::ld(Ut, o), z);
+      DD::st(Ut, o, u);
+    } else {
+      u = dd_sub((j < i) ? DD::ld(Uin, o) : DD::zero(), z);
+      DD::st(Uout, o, u);
+      DD::st(Ut, o, dd_add(DD::ld(Ut, o), u));
+    }
     bh[row - pt.r0] = u.hi;
     bl[row - pt.r0] = u.lo;
   }
@@ -925,7 +954,7 @@ cudaError_t launch_oz(const OzArgs& a, cudaStream_t st) {
 }  // namespace
 
 // ---------------------------------------------------------------- host interface
-int oz_tile_n(int64_t ncolg) { return ncolg <= 16 ? 16 : 32; }
+int oz_tile_n(int64_t ncolg, int wmax) { return ncolg <= 16 ? 16 : (ncolg <= 32 || wmax > OzCfg<64>::WMAX) ? 32 : 64; }
 
 size_t oz_rows_elems(int64_t D) { return (size_t)oz_mt(D) * oz_kb(D) * OZ_S * OZ_ABLK; }
 size_t oz_rows_exps(int64_t D) { return (size_t)oz_mt(D) * 128; }
@@ -962,7 +991,7 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   OzArgs a{};
   const int KB = (int)((q.K + OZ_BK - 1) / OZ_BK), MT = (int)((q.M + 127) / 128);
   const int NTL = (int)((q.N + q.NT - 1) / q.NT);
-  if (q.NT != 16 && q.NT != 32) return cudaErrorInvalidValue;
+  if (q.NT != 16 && q.NT != 32 && !(q.NT == 64 && q.wmax <= OzCfg<64>::WMAX)) return cudaErrorInvalidValue;
   a.As = q.As;
   a.a_gstride = q.a_shared ? 0 : (int64_t)oz_vec_elems(q.M, q.K, 128);
   a.a_perm = q.a_perm;
@@ -992,7 +1021,7 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   a.status = q.status;
   if (q.wmax < 1 || q.wmax > OZ_W) return cudaErrorInvalidValue;
   a.wmax = q.wmax;
-  return q.NT == 16 ? launch_oz<16>(a, st) : launch_oz<32>(a, st);
+  return q.NT == 16 ? launch_oz<16>(a, st) : q.NT == 32 ? launch_oz<32>(a, st) : launch_oz<64>(a, st);
 }
 
 cudaError_t oz_product(const __nv_bfloat16* As, const int* ea, const int* a_perm, bool a_shared,
@@ -1061,7 +1090,7 @@ inline int col_cands(int64_t D, int* c) {
 cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, int64_t ny_stride, const int* eg,
                             const int* eu, CBuf U, int live, int64_t nold, int64_t nnew, int64_t D, int64_t K, int inew,
                             const int* perm, const double* tau, const double* lam0, int64_t gs, int NT,
-                            __nv_bfloat16* Rs, int* er, cudaStream_t st) {
+                            __nv_bfloat16* Rs, int* er, CBuf c, cudaStream_t st) {
   const int NTL = (int)((nnew + NT - 1) / NT);
   int cands[4];
   const int nc = col_cands(D, cands);
@@ -1073,7 +1102,7 @@ cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, 
   const cudaError_t e =
       launch_pdl_cluster(k_make_R_oz_slice, dim3((unsigned)((int64_t)live * NTL * NT * cg_.CL)), dim3(cg_.threads),
                          cg_.smem, cg_.CL, st, Yhi, Ylo, ny, ny_stride, eg, eu, U, nold, nnew, D, K, inew, perm, tau,
-                         lam0, gs, NT, NTL, cg_.KB, cg_.KBC, Rs, er);
+                         lam0, gs, NT, NTL, cg_.KB, cg_.KBC, Rs, er, c);
   tune_end(t, st);
   return e;
 }
@@ -1081,7 +1110,7 @@ cudaError_t oz_make_R_slice(const long long* Yhi, const long long* Ylo, int ny, 
 cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, const int* ep, int64_t ep_gs,
                             const int* er, int64_t er_gs, int live, int64_t ncol, int64_t D, int64_t K, int i, CBuf Uin,
                             CBuf Uout, CBuf Ut, const int* perm, int64_t gs, int live_next, int NTn, __nv_bfloat16* Us,
-                            int* eu, cudaStream_t st) {
+                            int* eu, int resid, cudaStream_t st) {
   int cands[4];
   const int nc = col_cands(D, cands);
   TuneLaunch t = tune_begin(tune_key(TUNE_COL_UPDATE, D, shape_class((int64_t)live * ncol), 0), "col_update_cluster",
@@ -1092,7 +1121,7 @@ cudaError_t oz_update_slice(const long long* Zhi, const long long* Zlo, int S, c
   const cudaError_t e =
       launch_pdl_cluster(k_update_oz_slice, dim3((unsigned)((int64_t)live * ncol * cg_.CL)), dim3(cg_.threads),
                          cg_.smem, cg_.CL, st, Zhi, Zlo, S, ep, ep_gs, er, er_gs, live, ncol, D, K, i, Uin, Uout, Ut,
-                         perm, gs, live_next, NTn, cg_.KB, cg_.KBC, Us, eu);
+                         perm, gs, live_next, NTn, cg_.KB, cg_.KBC, Us, eu, resid);
   tune_end(t, st);
   return e;
 }

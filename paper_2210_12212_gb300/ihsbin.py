@@ -36,6 +36,7 @@ GRAM_AUTO, GRAM_SLICES, GRAM_FMA = 0, 1, 2
 GRAM = {"auto": GRAM_AUTO, "slices": GRAM_SLICES, "fma": GRAM_FMA}
 LOOP = {"auto": 0, "slices": 1, "fma": 2}
 FACTOR = {"auto": 0, "slices": 1, "fma": 2}
+FORM = {"auto": 0, "residual": 1, "increment": 2}
 
 
 class IhsbinError(RuntimeError):
@@ -61,7 +62,8 @@ class PathDesc(C.Structure):
                 ("rho2", C.c_void_p), ("rho", C.c_double), ("jmax", C.c_int32),
                 ("compute", C.c_int), ("product", C.c_int), ("eps", C.c_double), ("auto_rho", C.c_int32),
                 ("gram", C.c_int), ("loop", C.c_int), ("factor", C.c_int), ("sigma_d2", C.c_double),
-                ("tau", C.c_void_p), ("slice_weight", C.c_int32)]
+                ("tau", C.c_void_p), ("slice_weight", C.c_int32), ("form", C.c_int32),
+                ("precond_weight", C.c_int32)]
 
 
 class AdaptiveDesc(C.Structure):
@@ -95,7 +97,7 @@ EXPORTED = [
     "ihsbin_kernel_stats", "ihsbin_sketch_gram_noalloc", "ihsbin_request_footprint", "ihsbin_serve_create",
     "ihsbin_serve_submit", "ihsbin_serve_wait", "ihsbin_serve_destroy", "ihsbin_serve", "ihsbin_gram_export",
     "ihsbin_path_losses", "ihsbin_adaptive_sketch", "ihsbin_sketch_entries_export", "ihsbin_kernel_exec",
-    "ihsbin_ctx_fail_allocations", "ihsbin_tuning_report", "ihsbin_tuning_reset",
+    "ihsbin_ctx_fail_allocations", "ihsbin_tuning_report", "ihsbin_tuning_reset", "ihsbin_recursion_form",
 ]
 KCAT_COUNT = 40
 
@@ -133,6 +135,7 @@ def load(path: Optional[str] = None):
         "ihsbin_ctx_fail_allocations": [vp, i64],
         "ihsbin_tuning_report": [vp, i64, C.POINTER(i64)],
         "ihsbin_tuning_reset": [],
+        "ihsbin_recursion_form": [vp, C.POINTER(i32), C.POINTER(i32)],
         "ihsbin_sketch_gram_noalloc": [vp, i64, i64, vp, vp],
         "ihsbin_request_footprint": [C.POINTER(Request), C.POINTER(C.c_uint64)],
         "ihsbin_serve_create": [vp, C.POINTER(ServeConfig), C.POINTER(vp)],
@@ -253,10 +256,12 @@ class Problem:
                     rho: float = 0.0, jmax: int = 0, compute: str = "f64", product: str = "auto",
                     eps: float = 0.0, auto_rho: bool = False, gram: str = "auto", loop: str = "auto",
                     factor: str = "auto", sigma_d2: float = 0.0, tau: Optional[Sequence[float]] = None,
-                    slice_weight: int = 0, stream=None):
+                    slice_weight: int = 0, form: str = "auto", precond_weight: int = 0, stream=None):
         """k=None with k_default <= 0 selects Theorem 4's k for `eps`; auto_rho takes rho from the sketch;
         gram / loop / factor select the Gram kernel, the recursion's product kernel and the inverse's
-        product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores)."""
+        product kernel ("auto", "slices" = tensor-core exact slices, "fma" = CUDA cores); form selects
+        how the tensor-core recursion carries the basis ("auto", "residual", "increment") and
+        precond_weight the slice pairs of the residual form's P_l r (0 = from the conditioning bound)."""
         pd = PathDesc()
         pd.lambda_min, pd.lambda_max, pd.L = lambda_min, lambda_max, L
         ka = np.ascontiguousarray(k, dtype=np.int32) if k is not None else None
@@ -275,7 +280,15 @@ class Problem:
         ta = np.ascontiguousarray(tau, dtype=np.float64) if tau is not None else None
         pd.tau = _ptr(ta)
         pd.slice_weight = slice_weight
+        pd.form = FORM[form]
+        pd.precond_weight = precond_weight
         _check(_lib.ihsbin_build_basis(self.h, C.byref(pd), _stream(stream)))
+
+    def recursion_form(self):
+        """(form, precond_weight) the last build ran with: form "residual" or "increment"."""
+        f, w = C.c_int32(), C.c_int32()
+        _check(_lib.ihsbin_recursion_form(self.h, C.byref(f), C.byref(w)))
+        return {v: k for k, v in FORM.items() if k != "auto"}[f.value], w.value
 
     def adaptive_sketch(self, kind: str, m0: int, lam: float, *, s: int = 1, seed: int = 0, entries: str = "f64",
                         eps: float = 0.0, gamma1: float = 0.0, gamma2: float = 0.0, gamma3: float = 0.0,

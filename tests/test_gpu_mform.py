@@ -1,4 +1,4 @@
-"""The recursion's two-product form (GPU).
+"""The recursion's two-product form (GPU), part of the increment form (form="increment").
 
 Once the basis is truncated to jmax columns (jmax K a multiple of 16) and at most six
 intervals are still running, every step forms [M_q U, P_l U] with M_q = P_l (G + lam0_l I) in
@@ -39,7 +39,7 @@ def _run(ctx, prob, loop, kk, r1, r2, L, basis=False):
     gp = gpu_problem(ihs, ctx, prob)
     gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
     gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, jmax=JMAX, compute="f32x2",
-                   loop=loop)
+                   loop=loop, form="increment")
     X = gp.eval_path(prob.lambdas)
     terms = [gp.basis(l, min(prob.n, prob.d)) for l in range(L)] if basis else None
     gp.close()
