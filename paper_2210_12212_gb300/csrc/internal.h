@@ -258,7 +258,15 @@ struct OzGemm {
   long long* olo = nullptr;
   int* status = nullptr;
   int wmax = 6;              // slice pairs kept: s + t <= wmax (4 .. 6)
+  // float-float epilogue instead of the partials (ksplit = 1 only): C_ij joined with the row and
+  // column exponents and written into out (group g at g * out_gs, row stride out_ld):
+  //   OZ_EPI_STORE_NEG : out[(r0 + i) ld + c0 + j]  = -C_ij
+  //   OZ_EPI_STORE_SYM : out[j ld + i] = out[i ld + j] = C_ij for i <= j
+  int epi = 0;
+  CBuf out{};
+  int64_t out_ld = 0, out_gs = 0, out_r0 = 0, out_c0 = 0;
 };
+enum OzEpi : int { OZ_EPI_PARTIALS = 0, OZ_EPI_STORE_NEG = 2, OZ_EPI_STORE_SYM = 3 };
 cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st);
 // the recursion's update in the two-product form (partials of M_q U and P_l U from a pair-mode product)
 cudaError_t oz_update_mw_slice(const long long* Phi, const long long* Plo, int S, const int* em, const int* ep,

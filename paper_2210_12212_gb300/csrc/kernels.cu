@@ -1185,12 +1185,15 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
       q.M = nR; q.N = B; q.K = nR; q.groups = L; q.NT = 32; q.ksplit = S;
       q.tri = OZ_TRI_LE_ROW;
       q.ohi = hi; q.olo = lo; q.status = p->status;
+      if (S == 1) {  // W[R0 + i][J0 + j] = -(W_RR T)_ij written by the kernel's epilogue
+        q.epi = OZ_EPI_STORE_NEG; q.out = Wm; q.out_ld = D; q.out_gs = D * D; q.out_r0 = R0; q.out_c0 = J0;
+      }
       KTimer kt(p, K_TRTRI_TC, st, 2.0 * L * (nR * (nR + 1.0) / 2.0) * B, (double)L * (nR * nR / 2.0 + 2.0 * nR * B) * 8,
                 oz_pair_flops(1, 1, 1, p->plan.slice_w) * L * (nR * (nR + 1.0) / 2.0) * B,
                 (double)L * (oz_vec_elems(nR, nR, 128) + oz_vec_elems(B, nR, 32)) * 2 + 16.0 * S * L * nR * B);
       CK(oz_gemm(q, st));
     }
-    {
+    if (S > 1) {
       KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * nR * B * (16.0 * S + 8));
       CK(launch_pdl(k_oz_store_wblock, dim3(nblocks((int64_t)L * nR * B, 256)), dim3(256), 0, st, hi, lo, S, nR, B, L,
                     ex, (int64_t)oz_vec_exps(nR, 128), ey, (int64_t)oz_vec_exps(B, 32), D, R0, J0, Wm));
@@ -1202,7 +1205,9 @@ static cudaError_t trtri_sweep_slices(ihsbin_problem* p, CBuf H, CBuf Wm, cudaSt
 // ---- Two-level Cholesky: within a 128-wide panel the 32-wide steps update only the panel's
 // columns; at the panel's end the trailing matrix takes the delayed rank-128 update
 //   H[c1:, c1:] -= L_p L_p^T,  L_p = L[c1:, c0:c1],
-// as an exact-slice product on the tensor cores (symmetric: tiles touching i <= j).
+// as an exact-slice product on the tensor cores (symmetric: tiles touching i <= j).  Its exact
+// partials are subtracted by a separate pass at full occupancy: a read-modify-write of H in the
+// product's epilogue (8 warps per SM) took longer than the product itself.
 __global__ void k_oz_sub_sym(const long long* hi, const long long* lo, int S, int64_t M, int L, const int* ea,
                              int64_t eag, const int* eb, int64_t ebg, int64_t D, int64_t c1, CBuf H) {
   pdl_wait();  // launched with programmatic serialization
@@ -1262,59 +1267,34 @@ static cudaError_t panel_update(ihsbin_problem* p, CBuf H, const PanelUpdate& u,
                     (int64_t)oz_vec_exps(M, 128), u.eb, (int64_t)oz_vec_exps(M, 32), D, c1, H);
 }
 
-// P_l[i][j] = P_l[j][i] (i <= j) from the exact partials of W_l^T W_l on the tensor cores
-__global__ void k_oz_store_sym(const long long* hi, const long long* lo, int S, int64_t D, int L, const int* ea,
-                               int64_t ea_gs, const int* eb, int64_t eb_gs, CBuf P) {
-  pdl_wait();  // launched with programmatic serialization
-  pdl_trigger();
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)L * D * D) return;
-  const int64_t l = e / (D * D), rr = e - l * D * D, j = rr / D, i = rr - j * D;
-  if (i > j) return;
-  long long h = 0, w = 0;
-  for (int s = 0; s < S; ++s) {
-    h += hi[(int64_t)s * L * D * D + e];
-    w += lo[(int64_t)s * L * D * D + e];
-  }
-  const dd v = oz_join(h, w, ea[l * ea_gs + i], eb[l * eb_gs + j]);
-  DD::st(P, l * D * D + j * D + i, v);
-  DD::st(P, l * D * D + i * D + j, v);
-}
-
 // P_l = W_l^T W_l on the tensor cores: X = Y = W_l^T (vectors = the columns of W_l), k >= max(i, j)
 static cudaError_t inverse_slices(ihsbin_problem* p, CBuf Wm, cudaStream_t st) {
   const int64_t D = p->A.D;
   const int L = p->plan.L;
   __nv_bfloat16 *As = nullptr, *Bs = nullptr;
   int *ea = nullptr, *eb = nullptr;
-  long long *hi = nullptr, *lo = nullptr;
   CK(prob_alloc(p, oz_vec_elems(D, D, 128) * 2 * L, (void**)&As, SCOPE_SCRATCH));
   CK(prob_alloc(p, oz_vec_exps(D, 128) * 4 * L, (void**)&ea, SCOPE_SCRATCH));
   CK(prob_alloc(p, oz_vec_elems(D, D, 32) * 2 * L, (void**)&Bs, SCOPE_SCRATCH));
   CK(prob_alloc(p, oz_vec_exps(D, 32) * 4 * L, (void**)&eb, SCOPE_SCRATCH));
-  CK(prob_alloc(p, (size_t)L * D * D * 8, (void**)&hi, SCOPE_SCRATCH));
-  CK(prob_alloc(p, (size_t)L * D * D * 8, (void**)&lo, SCOPE_SCRATCH));
   {
     KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * D * D * 8 * 2 + (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2);
     CK(oz_slice_matcols(Wm, D, D, D, L, D * D, 128, As, ea, st));
     CK(oz_slice_matcols(Wm, D, D, D, L, D * D, 32, Bs, eb, st));
   }
-  {
-    OzGemm q;
-    q.wmax = p->plan.slice_w;
-    q.As = As; q.ea = ea; q.Bs = Bs; q.eb = eb;
-    q.M = D; q.N = D; q.K = D; q.groups = L; q.NT = 32; q.ksplit = 1;
-    q.tri = OZ_TRI_GE_ROW | OZ_TRI_GE_COL;
-    q.sym = 1;
-    q.ohi = hi; q.olo = lo; q.status = p->status;
-    KTimer kt(p, K_INVERSE_TC, st, (double)L * D * (D + 1.0) * (D + 2.0) / 3.0, (double)L * D * D * 8,
-              oz_pair_flops(1, 1, 1, p->plan.slice_w) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
-              (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2 + (double)L * D * D * 16);
-    CK(oz_gemm(q, st));
-  }
-  KTimer kt(p, K_INVERSE_SLICE, st, 0, (double)L * D * D * (16 + 16));
-  return launch_pdl(k_oz_store_sym, dim3(nblocks((int64_t)L * D * D, 256)), dim3(256), 0, st, hi, lo, 1, D, L, ea,
-                    (int64_t)oz_vec_exps(D, 128), eb, (int64_t)oz_vec_exps(D, 32), p->Pinv);
+  OzGemm q;
+  q.wmax = p->plan.slice_w;
+  q.As = As; q.ea = ea; q.Bs = Bs; q.eb = eb;
+  q.M = D; q.N = D; q.K = D; q.groups = L; q.NT = 32; q.ksplit = 1;
+  q.tri = OZ_TRI_GE_ROW | OZ_TRI_GE_COL;
+  q.sym = 1;
+  q.status = p->status;
+  // P_l[i][j] = P_l[j][i] written by the kernel's epilogue
+  q.epi = OZ_EPI_STORE_SYM; q.out = p->Pinv; q.out_ld = D; q.out_gs = D * D;
+  KTimer kt(p, K_INVERSE_TC, st, (double)L * D * (D + 1.0) * (D + 2.0) / 3.0, (double)L * D * D * 8,
+            oz_pair_flops(1, 1, 1, p->plan.slice_w) / 2.0 * L * D * (D + 1.0) * (D + 2.0) / 3.0,
+            (double)L * (oz_vec_elems(D, D, 128) + oz_vec_elems(D, D, 32)) * 2 + (double)L * D * D * 16);
+  return oz_gemm(q, st);
 }
 
 template <class Mode>
@@ -1725,8 +1705,37 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
   const Plan& pl = p->plan;
   const int64_t gs = (int64_t)pl.jc * K * D;  // per-interval stride of U / Ut
   const int L = pl.L;
-  // u_00 = P_l c for every interval
-  {
+  const int pw = oz.resid ? oz.pw : pl.slice_w;  // pair weight of the P_l R products
+  if (oz.resid) {
+    // v_0 = P_l c as a step of the residual form from v = 0 (R = -c, no product with G): the
+    // tensor-core P_l r with pw's pairs, whose error the later steps remove like any other's;
+    // the update cuts v_0 for the first G v
+    int live0 = 0;
+    while (live0 < L && pl.k[order[live0]] > 0) ++live0;
+    const int live1 = pl.kmax > 1 ? [&] { int n = 0; while (n < L && pl.k[order[n]] > 1) ++n; return n; }() : 0;
+    const int NT = oz_tile_n(K, pw);
+    {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live0 * K * D * (16.0 + 12));
+      CK(oz_make_R_slice(oz.Yhi, oz.Ylo, 0, 0, oz.eg, oz.eb, p->Ut, live0, 0, K, D, K, -1, perm_dev, tau_dev,
+                         lam0_dev, gs, NT, oz.Bs, oz.er, c, st));
+    }
+    const int ks = oz_pick_split(D, K, live0, NT, SPLIT_MAX);
+    {
+      const double fsl = (std::min(pw, 5) + 1) / 6.0;
+      KTimer kt(p, K_LOOP_P_TC, st, 2.0 * D * D * K * live0, (double)live0 * D * D * 8 + 16.0 * D * K * live0,
+                oz_pair_flops(D, K, D, pw) * live0,
+                (double)live0 * (oz_rows_elems(D) * 2 + oz_cols_elems(D, K, NT) * 2) * fsl + 16.0 * ks * D * K * live0);
+      CK(oz_product(oz.Ps, oz.ep, perm_dev, false, oz.Bs, oz.er, D, K, live0, NT, ks, oz.Zhi, oz.Zlo, p->status, st,
+                    pw));
+    }
+    {
+      KTimer kt(p, K_LOOP_P, st, 0, (double)live0 * K * D * (16.0 * ks + 24 + 12));
+      CK(oz_update_slice(oz.Zhi, NT == 64 ? nullptr : oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er,
+                         (int64_t)oz_cols_exps(K, NT), live0, K, D, K, 0, U0, U1, p->Ut, perm_dev, gs, live1,
+                         oz_tile_n((int64_t)K * std::max(live1, 1)), oz.Bs, oz.eb, 1, st));
+    }
+  } else {
+    // u_00 = P_l c for every interval
     GemmShape sh{D, K, D, 0};
     KTimer kt(p, K_LOOP_P, st, 2.0 * D * D * K * L, (double)L * D * D * 8);
     CK((launch_gemm_n<Mode>(sh, L, LdCMatA<Mode>{p->Pinv, D, D * D, perm_dev},
@@ -1735,7 +1744,6 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
   }
   CBuf Uin = U0, Uout = U1;
   const int J = pl.jmax > 0 ? pl.jmax : (1 << 30);
-  const int pw = oz.resid ? oz.pw : pl.slice_w;  // pair weight of the P_l R products
   for (int i = 1; i < pl.kmax; ++i) {
     int live = 0;
     while (live < L && pl.k[order[live]] > i) ++live;
@@ -1783,7 +1791,7 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
       // fused path the previous step's update already sliced them)
       const int64_t ncat = nold * live;
       const int NT = oz_tile_n(ncat);
-      if (!fused || i == 1) {
+      if (!fused || (i == 1 && !oz.resid)) {  // (the residual form's first update cut v_0)
         KTimer kt(p, K_LOOP_SLICE, st, 0, 8.0 * D * ncat + 12.0 * D * ncat);
         CK(oz_slice_cols(Uin, D, 1, ncat, NT, nold, gs, perm_dev, oz.Bs, oz.eb, st));
       }
@@ -1865,7 +1873,8 @@ static cudaError_t basis_loop(ihsbin_problem* p, CBuf c, CBuf U0, CBuf U1, CBuf 
         const int NTn = (live_next > 0 && !(oz.mform_from > 0 && i + 1 >= oz.mform_from)) ? oz_tile_n(nnew * live_next)
                                                                                        : 16;
         KTimer kt(p, K_LOOP_P, st, 0, (double)live * nnew * D * (16.0 * ks + 24 + 12));
-        CK(oz_update_slice(oz.Zhi, oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er, (int64_t)oz_cols_exps(nnew, NT),
+        CK(oz_update_slice(oz.Zhi, NT == 64 ? nullptr : oz.Zlo, ks, oz.ep, (int64_t)oz_rows_exps(D), oz.er,
+                           (int64_t)oz_cols_exps(nnew, NT),
                            live, nnew, D, K, i, Uin, Uout, p->Ut, perm_dev, gs, live_next, NTn, oz.Bs, oz.eb,
                            oz.resid ? 1 : 0, st));
       } else {
@@ -2028,7 +2037,12 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   // the sketched Hessian), so they run on the problem's side stream, forked here and joined
   // before the recursion: their tensor-core work fills the SMs that the factorization's small
   // launches leave idle.  Allocations in this section are ordered on the side stream.
-  if (!p->side) CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+  // Stream priorities: the factorization's chain of small dependent launches is the critical
+  // path, so its CTAs are scheduled first whenever SMs free up; the Gram's long tensor-core CTAs
+  // (lowest priority) fill the rest.
+  int prio_lo = 0, prio_hi = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  if (!p->side) CK(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_lo));
   cudaStream_t s2 = p->side;
   CK(cudaEventRecord(ev[5], st));
   CK(cudaStreamWaitEvent(s2, ev[5], 0));
@@ -2066,7 +2080,7 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   // a2: factor + inverse of the shifted sketched Hessians, on the problem's second internal
   // stream (forked with the Gram's, joined before the recursion).  Allocations in this section
   // are ordered on that stream.
-  if (!p->fac) CK(cudaStreamCreateWithFlags(&p->fac, cudaStreamNonBlocking));
+  if (!p->fac) CK(cudaStreamCreateWithPriority(&p->fac, cudaStreamNonBlocking, prio_hi));
   cudaStream_t sf = p->fac;
   CK(cudaStreamWaitEvent(sf, ev[5], 0));
   {
@@ -2168,6 +2182,8 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
     }
     // the largest split partials of any step, replaying the recursion's (live, columns, splits)
     size_t ymax = 1, zmax = 1;
+    if (resid)  // the residual form's first step: P_l (-c) for every interval
+      zmax = (size_t)oz_pick_split(D, K, L, oz_tile_n(K, pw), SPLIT_MAX) * L * K * D;
     {
       const int J = pl.jmax > 0 ? pl.jmax : (1 << 30);
       for (int i = 1; i < pl.kmax; ++i) {

@@ -76,10 +76,9 @@ struct OzCfg {
   static constexpr int EPI_WARPS = NT == 16 ? 4 : 8;
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr int COLS = NT == 16 ? 256 : 512;     // two buffers of (WMAX + 1) NT accumulator columns
-  // an epilogue warpgroup drains WPG weights of EC columns: NT = 32 splits the weights between
-  // the two warpgroups, NT = 64 the columns
-  static constexpr int WPG = NT == 16 ? OZ_NW : 4;
-  static constexpr int EC = WIDE ? 32 : NT;
+  // an epilogue warpgroup drains every weight (WPG) of EC of the tile's columns
+  static constexpr int WPG = WMAX + 1;
+  static constexpr int EC = NT / (EPI_WARPS / 4);
 };
 
 struct OzArgs {
@@ -107,7 +106,25 @@ struct OzArgs {
   long long* olo;
   int* status;
   int wmax;              // slice pairs kept: s + t <= wmax (<= OZ_W); the others weigh below 2^(-8 (wmax + 1))
+  int epi;               // OZ_EPI_*: exact partials, or the joined float-float value written into out
+  CBuf out;
+  int64_t out_ld, out_gs, out_r0, out_c0;
 };
+
+// The float-float epilogue of a product with one k-split: C_ij = hi 2^(ea_i + eb_j - 38) +
+// lo 2^(ea_i + eb_j - 62) (oz_join), written as OzGemm's epi mode says.
+__device__ __forceinline__ void oz_epilogue_dd(const OzArgs& a, int g, int ag, int bg, int64_t i, int64_t j,
+                                               long long hi, long long lo) {
+  if (a.epi != OZ_EPI_STORE_NEG && i > j) return;  // symmetric results: the entries i <= j
+  const dd v = oz_join(hi, lo, a.ea[(int64_t)ag * a.ea_gstride + i], a.eb[(int64_t)bg * a.eb_gstride + j]);
+  const int64_t base = (int64_t)g * a.out_gs;
+  if (a.epi == OZ_EPI_STORE_NEG) {
+    DD::st(a.out, base + (a.out_r0 + i) * a.out_ld + a.out_c0 + j, dd_neg(v));
+  } else {
+    DD::st(a.out, base + j * a.out_ld + i, v);
+    DD::st(a.out, base + i * a.out_ld + j, v);
+  }
+}
 
 // Persistent: CTA b takes work items b, b + gridDim.x, ...; item = ((g * ksplit + sp) * MT + mt) * NTL + nt
 // (column tiles fastest, so CTAs running at the same time share the A rows in L2).  The stage ring
@@ -264,8 +281,8 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
     }
   } else {  // epilogue warps: warpgroup qg drains weights [w0, w0 + WPG) of columns [c0, c0 + EC)
     const int qg = (warp - 2) >> 2, lq = warp & 3;
-    const int w0 = C::WIDE ? 0 : qg * C::WPG;
-    const int c0 = C::WIDE ? qg * C::EC : 0;
+    const int w0 = 0;
+    const int c0 = qg * C::EC;
     const int r = lq * 32 + lane;  // Tensor Memory lane = row of the tile
     uint32_t cc = 0;
     for (int item = blockIdx.x; item < items; item += gridDim.x) {
@@ -308,9 +325,10 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
       // every epilogue warp reaches this barrier; after it they agree on aborting
       tc::named_sync(1, 32 * C::EPI_WARPS);
       if (*abort_v) break;
-      // The weights joined exactly in int64 (|acc_w| < 2^31); the consumer adds the splits and
-      // converts (with the row / column exponents) at full occupancy:
-      //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6.
+      // The weights joined exactly in int64 (|acc_w| < 2^31):
+      //   hi = acc_0 2^24 + acc_1 2^16 + acc_2 2^8 + acc_3,  lo = acc_4 2^16 + acc_5 2^8 + acc_6;
+      // either written per k-split for the consumer to add and convert at full occupancy, or (one
+      // k-split) converted here and written into the float-float result.
       const int64_t i = (int64_t)w.mt * 128 + r;
       constexpr int E = C::EC;
       if (i < a.M && !w.skip) {
@@ -318,18 +336,16 @@ __global__ void __launch_bounds__(OzCfg<NT>::THREADS, 1) k_oz_mma(OzArgs a) {
         for (int j = 0; j < E; ++j) {
           const int64_t jj = (int64_t)w.nt * NT + c0 + j;
           if (jj >= a.N) break;
-          const int64_t o = (((int64_t)w.sp * a.groups + w.g) * a.N + jj) * a.M + i;
-          if constexpr (C::WIDE) {  // weights 0..3 only
-            a.ohi[o] = (((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j]) * 256 + acc[3 * E + j];
-            a.olo[o] = 0;
+          const long long hi =
+              (((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j]) * 256 + acc[3 * E + j];
+          long long lo = 0;
+          if constexpr (C::WPG == OZ_NW) lo = ((long long)acc[4 * E + j] * 256 + acc[5 * E + j]) * 256 + acc[6 * E + j];
+          if (a.epi == OZ_EPI_PARTIALS) {
+            const int64_t o = (((int64_t)w.sp * a.groups + w.g) * a.N + jj) * a.M + i;
+            a.ohi[o] = hi;
+            if constexpr (!C::WIDE) a.olo[o] = lo;  // (weights 0..3 only: no lo partial, its consumer reads none)
           } else {
-            if (qg == 0)
-              a.ohi[o] = (((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j]) * 256 + acc[3 * E + j];
-            if constexpr (C::EPI_WARPS == 8) {
-              if (qg == 1) a.olo[o] = ((long long)acc[j] * 256 + acc[E + j]) * 256 + acc[2 * E + j];  // weights 4..6
-            } else {
-              a.olo[o] = ((long long)acc[4 * E + j] * 256 + acc[5 * E + j]) * 256 + acc[6 * E + j];
-            }
+            oz_epilogue_dd(a, w.g, w.ag, w.bg, i, jj, hi, lo);
           }
         }
       }
@@ -694,6 +710,7 @@ __device__ __forceinline__ ColPart col_part(int64_t D, int KBC) {
 
 // Sum of n exact int64 split partials of up to two entries (offsets o1, o2; the second only when
 // two is true): eight splits of every array per round, all loads of a round issued together.
+// b == nullptr: the products wrote no lo partials (weights 0..3 only), which count as zero.
 __device__ __forceinline__ void oz_sum_splits2(const long long* __restrict__ a, const long long* __restrict__ b, int n,
                                                int64_t stride, int64_t o1, int64_t o2, bool two, long long& s1a,
                                                long long& s1b, long long& s2a, long long& s2b) {
@@ -705,9 +722,9 @@ __device__ __forceinline__ void oz_sum_splits2(const long long* __restrict__ a, 
       const bool in = s0 + q < n;
       const int64_t so = (int64_t)(s0 + q) * stride;
       v1a[q] = in ? __ldg(a + so + o1) : 0LL;
-      v1b[q] = in ? __ldg(b + so + o1) : 0LL;
+      v1b[q] = (in && b) ? __ldg(b + so + o1) : 0LL;
       v2a[q] = (in && two) ? __ldg(a + so + o2) : 0LL;
-      v2b[q] = (in && two) ? __ldg(b + so + o2) : 0LL;
+      v2b[q] = (in && two && b) ? __ldg(b + so + o2) : 0LL;
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -799,7 +816,9 @@ __global__ void __launch_bounds__(OZ_COL_THREADS_MAX, 2) k_make_R_oz_slice(const
         const int64_t cc = (int64_t)g * nold + col, yo = cc * D + k;
         long long h, w, h2, w2;
         oz_sum_splits2(Yhi, Ylo, ny, ny_stride, yo, yo, false, h, w, h2, w2);
-        r = dd_mul(tl, dd_add(oz_join(h, w, eg[k], eu[cc]), dd_mul(lm, DD::ld(U, o))));
+        // ny = 0: no product (the residual form's first step, v = 0): R = -c
+        const dd y = ny > 0 ? oz_join(h, w, eg[k], eu[cc]) : DD::zero();
+        r = dd_mul(tl, dd_add(y, dd_mul(lm, DD::ld(U, o))));
         if (j > 0) r = dd_add(r, dd_mul(lm, DD::ld(U, o - K * D)));
         else if (Cr.p0) r = dd_sub(r, DD::ld(Cr, col * D + k));  // residual form: minus c in the j = 0 term
       }
@@ -1021,6 +1040,13 @@ cudaError_t oz_gemm(const OzGemm& q, cudaStream_t st) {
   a.status = q.status;
   if (q.wmax < 1 || q.wmax > OZ_W) return cudaErrorInvalidValue;
   a.wmax = q.wmax;
+  if (q.epi != OZ_EPI_PARTIALS && (a.ksplit != 1 || q.pair || !q.ea || !q.eb || !q.out.p0)) return cudaErrorInvalidValue;
+  a.epi = q.epi;
+  a.out = q.out;
+  a.out_ld = q.out_ld;
+  a.out_gs = q.out_gs;
+  a.out_r0 = q.out_r0;
+  a.out_c0 = q.out_c0;
   return q.NT == 16 ? launch_oz<16>(a, st) : q.NT == 32 ? launch_oz<32>(a, st) : launch_oz<64>(a, st);
 }
 
