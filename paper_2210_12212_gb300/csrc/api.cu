@@ -131,8 +131,28 @@ cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope) {
   DevBuf b{*out, bytes};
   if (scope == SCOPE_SCRATCH && g_scratch) g_scratch->push_back(b);
   else if (scope == SCOPE_PERSIST) p->owned.push_back(b);
+  else if (scope == SCOPE_PRE) p->pre_bufs.push_back(b);
   else p->basis_bufs.push_back(b);
   return cudaSuccess;
+}
+
+// Waits for a background Gram of an earlier sketch and frees its buffers (on the side stream).
+void pre_gram_discard(ihsbin_problem* p) {
+  if (p->side) cudaStreamSynchronize(p->side);
+  {
+    CallStream cs(p->side);
+    free_list(p, p->pre_bufs);
+  }
+  if (p->pre_tune) {  // a tuning sample that no build completed
+    if (p->pre_tune->timed) {
+      cudaEventDestroy(p->pre_tune->e0);
+      cudaEventDestroy(p->pre_tune->e1);
+    }
+    delete p->pre_tune;
+    p->pre_tune = nullptr;
+  }
+  p->gram_pre = p->pre_taken = false;
+  p->G_pre = p->c_pre = CBuf{};
 }
 
 CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaError_t* err) {
@@ -240,6 +260,11 @@ ihsbin_status ihsbin_ctx_create(int device, uint64_t budget, ihsbin_ctx** out) {
   }
   uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool for the next request
   cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  // No reuse that would make an allocation wait for another stream's pending free: the problem's
+  // streams run concurrently (the sketch beside the background Gram, the factorization beside the
+  // Gram), and such a wait would serialise them; the pool grows instead.
+  int no_deps = 0;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolReuseAllowInternalDependencies, &no_deps);
   *out = c;
   return IHSBIN_OK;
 }
@@ -430,6 +455,9 @@ ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p) {
   CallStream cs(nullptr);
   for (auto e : p->ev_pool) cudaEventDestroy(e);
   p->ev_pool.clear();
+  pre_gram_discard(p);
+  for (auto& e : p->pre_ev)
+    if (e) cudaEventDestroy(e);
   for (cudaStream_t* sp : {&p->side, &p->fac})
     if (*sp) {
       cudaStreamSynchronize(*sp);
@@ -468,6 +496,7 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
   }
   cudaError_t e = cudaSetDevice(p->ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "sketch");
+  pre_gram_discard(p);
   CallStream cs(st);
   // discard any previous sketch and basis
   prob_free_basis(p);
@@ -503,16 +532,42 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
     return cuda_fail(e, "sketch");
   if ((e = prob_alloc(p, std::max<int64_t>(1, p->sk_sign_count), (void**)&p->sk_sign, SCOPE_PERSIST)) != cudaSuccess)
     return cuda_fail(e, "sketch");
+  if (pre_gram_eligible(p) && ensure_streams(p) == cudaSuccess) {
+    // the Gram of A and A^T b for the next build, on the side stream beside the sketch (its
+    // scratch is freed in that stream's order); a failure here only means the build forms them
+    CallStream side(p->side);
+    ScratchScope pre_scratch(p);
+    if (pre_gram_launch(p) != cudaSuccess) {
+      cudaGetLastError();
+      pre_gram_discard(p);
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  cudaEventRecord(e0, st);
-  if (sk->kind == IHSBIN_SK_GAUSSIAN) e = sketch_gaussian(p, st);
-  else if (sk->kind == IHSBIN_SK_SRHT) e = sketch_srht(p, st);
-  else e = sketch_countsketch(p, st);
-  if (e == cudaSuccess) e = sketch_gram(p, st);
-  cudaEventRecord(e1, st);
+  // With a background Gram running, the sketch's kernels go to the problem's high-priority stream
+  // (forked from and joined back to the caller's), so that the Gram only takes what they leave.
+  cudaStream_t ks = p->gram_pre ? p->fac : st;
+  double* tr_dev = nullptr;
+  if (ks != st) {
+    cudaEventRecord(e0, st);
+    cudaStreamWaitEvent(ks, e0, 0);
+  }
+  {
+    CallStream kcs(ks);
+    cudaEventRecord(e0, ks);
+    if (sk->kind == IHSBIN_SK_GAUSSIAN) e = sketch_gaussian(p, ks);
+    else if (sk->kind == IHSBIN_SK_SRHT) e = sketch_srht(p, ks);
+    else e = sketch_countsketch(p, ks);
+    if (e == cudaSuccess) e = sketch_gram(p, ks);
+    // tr(G_S) for the next build, read after this call's synchronisation
+    if (e == cudaSuccess) e = prob_alloc(p, sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH);
+    if (e == cudaSuccess) e = gs_trace_launch(p, tr_dev, ks);
+    cudaEventRecord(e1, ks);
+  }
+  if (ks != st) cudaStreamWaitEvent(st, e1, 0);
   if (e != cudaSuccess) {
+    cudaStreamSynchronize(ks);
     cudaStreamSynchronize(st);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -520,6 +575,8 @@ ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, voi
     return cuda_fail(e, "sketch");
   }
   ihsbin_status s = check_status(p, st, "sketch");
+  if (s == IHSBIN_OK && cudaMemcpy(&p->trGS, tr_dev, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    s = fail(IHSBIN_ERR_CUDA, "sketch: trace copy failed");
   cudaEventElapsedTime(&p->phase_ms[0], e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -673,8 +730,20 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   if (e != cudaSuccess) return cuda_fail(e, "build_basis");
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   CallStream cs(st);
+  const bool take_pre = p->gram_pre && pl.compute == IHSBIN_COMPUTE_F32X2 && pl.gram == IHSBIN_GRAM_SLICES &&
+                        pl.product == IHSBIN_PRODUCT_GRAM;
+  if (p->gram_pre && !take_pre) pre_gram_discard(p);
   prob_free_basis(p);
   p->plan = pl;
+  if (take_pre) {
+    // the background Gram joins the basis; its right-hand side stays a pre buffer until the end
+    std::vector<DevBuf> keep;
+    for (auto& b : p->pre_bufs)
+      (b.p == p->G_pre.p0 || b.p == p->G_pre.p1 ? p->basis_bufs : keep).push_back(b);
+    p->pre_bufs.swap(keep);
+    p->G = p->G_pre;
+    p->pre_taken = true;
+  }
   if (!pl.auto_rho) finalize_plan(p, nullptr);
   // phases: factor ev[0] -> ev[1] (factor stream); Gram + rhs ev[5] -> ev[2] (side stream,
   // overlapping the factor); recursion ev[6] -> ev[3] (caller's stream, after both joins)
@@ -691,6 +760,7 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
       if (p->fac) cudaStreamSynchronize(p->fac);
       for (auto& x : ev) cudaEventDestroy(x);
       prob_free_basis(p);
+      pre_gram_discard(p);
       cudaMemset(p->status, 0, sizeof(int));  // nothing of the failed build is reported later
       tune_discard();
       return cuda_fail(e, "build_basis");
@@ -699,8 +769,10 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
   }
   float t01 = 0, t12 = 0, t23 = 0;
   cudaEventElapsedTime(&t01, ev[0], ev[1]);
-  cudaEventElapsedTime(&t12, ev[5], ev[2]);
+  if (p->pre_taken) cudaEventElapsedTime(&t12, p->pre_ev[0], p->pre_ev[1]);
+  else cudaEventElapsedTime(&t12, ev[5], ev[2]);
   cudaEventElapsedTime(&t23, ev[6], ev[3]);
+  pre_gram_discard(p);  // the right-hand side of a background Gram (the stream is idle here)
   p->phase_ms[1] = t01;
   p->phase_ms[2] = t12;
   p->phase_ms[3] = t23;
@@ -710,6 +782,8 @@ ihsbin_status ihsbin_build_basis(ihsbin_problem* p, const ihsbin_path_desc* d, v
     return s;
   }
   p->built = true;
+  p->last_compute = pl.compute;
+  p->last_gram = pl.gram;
   return IHSBIN_OK;
 }
 
@@ -926,6 +1000,12 @@ ihsbin_status ihsbin_adaptive_sketch(ihsbin_problem* p, const ihsbin_adaptive_de
   cudaStream_t st = stream ? (cudaStream_t)stream : cudaStreamPerThread;
   ihsbin_sketch_desc sk = desc->sketch;
   const uint64_t seed0 = sk.seed;
+  // the re-sketches of Algorithm 4 start no background Gram (no build follows them here)
+  struct PreOff {
+    ihsbin_problem* p;
+    explicit PreOff(ihsbin_problem* q) : p(q) { p->pre_off = true; }
+    ~PreOff() { p->pre_off = false; }
+  } pre_off_(p);
   ihsbin_status s = ihsbin_sketch(p, &sk, stream);
   if (s != IHSBIN_OK) return s;
   cudaError_t e = cudaSetDevice(p->ctx->device);

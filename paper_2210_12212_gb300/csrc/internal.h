@@ -84,6 +84,10 @@ struct KStat {
 
 }  // namespace ihsbin
 
+namespace ihsbin {
+struct TuneLaunch;
+}
+
 struct ihsbin_problem {
   ihsbin_ctx* ctx = nullptr;
   cudaStream_t side = nullptr;  // build_basis: the Gram's stream, overlapping ...
@@ -100,6 +104,7 @@ struct ihsbin_problem {
   ihsbin_sketch_desc sk{};
   double* SA = nullptr;                  // m x D FP64
   double* GS = nullptr;                  // D x D FP64
+  double trGS = 0.0;                     // its trace (host copy, for the residual form's pair weight)
   int64_t* sk_idx = nullptr;             // device
   int8_t* sk_sign = nullptr;             // device
   int64_t sk_idx_count = 0, sk_sign_count = 0;
@@ -111,6 +116,17 @@ struct ihsbin_problem {
   ihsbin::CBuf Ut;                       // L x jc x K x D
   ihsbin::CBuf W;                        // dual: L x jc x K x N (primal basis)
   std::vector<ihsbin::DevBuf> basis_bufs;
+  // The Gram of A and A^T b that ihsbin_sketch starts on the side stream for the next build
+  // (float-float, sliced Gram, dense data; they do not depend on the sketch): taken by that build
+  // when its mode matches, else waited for and freed.
+  bool gram_pre = false;
+  ihsbin::CBuf G_pre, c_pre;
+  std::vector<ihsbin::DevBuf> pre_bufs;
+  cudaEvent_t pre_ev[2] = {nullptr, nullptr};  // start / end of the background Gram (side stream)
+  bool pre_taken = false;                      // the running build uses them
+  ihsbin::TuneLaunch* pre_tune = nullptr;      // the SMs it leaves free: tuned from its start to the build's join
+  int last_compute = -1, last_gram = -1;       // mode of the last successful build (-1: none)
+  bool pre_off = false;                        // set while Algorithm 4 re-sketches (no build follows)
   float phase_ms[5] = {0, 0, 0, 0, 0};
   // per-launch accounting: counts and algorithmic work always; event timing when enabled
   bool timing = false;
@@ -135,9 +151,10 @@ struct CallStream {
 
 // ----- allocation helpers (api.cu) --------------------------------------------
 // Lifetime of a device allocation: the problem, the current basis, or the current call.
-enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2 };
+enum Scope : int { SCOPE_PERSIST = 0, SCOPE_BASIS = 1, SCOPE_SCRATCH = 2, SCOPE_PRE = 3 };
 cudaError_t prob_alloc(ihsbin_problem* p, size_t bytes, void** out, int scope);
 void prob_free_basis(ihsbin_problem* p);
+void pre_gram_discard(ihsbin_problem* p);  // waits for a background Gram (if any) and frees it
 CBuf alloc_cbuf(ihsbin_problem* p, int compute, size_t elems, int scope, cudaError_t* err);
 
 // Records one launch of category `cat` with its algorithmic flops / bytes, and
@@ -162,7 +179,7 @@ struct TuneLaunch {
   bool timed = false;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
-enum TuneSite : int { TUNE_COL_R = 1, TUNE_COL_UPDATE = 2, TUNE_COL_MW = 3, TUNE_GRAM_RESERVE = 4 };
+enum TuneSite : int { TUNE_COL_R = 1, TUNE_COL_UPDATE = 2, TUNE_COL_MW = 3, TUNE_GRAM_RESERVE = 4, TUNE_PRE_RESERVE = 5 };
 uint64_t tune_key(int site, int64_t a, int64_t b, int64_t c);
 int shape_class(int64_t n);  // ceil(log2 n)
 // The geometry value to launch with (values[cand]); while the key is being tuned the launch is
@@ -213,6 +230,14 @@ cudaError_t launch_round_tf32(const float* src, int64_t ld, int64_t rows, int64_
 // rhs != nullptr: also c = A_hat^T B (column-major D x K) from the same slices of A_hat
 cudaError_t gram_dense_slices(ihsbin_problem* p, int compute, cudaStream_t st, int reserve_sms = 0,
                               CBuf* rhs = nullptr);
+// The problem's two internal streams (created once): the side stream at the lowest priority (the
+// Gram), the factorization's at the highest.
+cudaError_t ensure_streams(ihsbin_problem* p);
+cudaError_t gs_trace_launch(ihsbin_problem* p, double* out, cudaStream_t st);  // tr(G_S) into out (device)
+// Whether ihsbin_sketch starts the Gram of A and A^T b in the background, and the launch itself
+// (on p->side, into SCOPE_PRE buffers; the caller owns the scratch scope on that stream).
+bool pre_gram_eligible(const ihsbin_problem* p);
+cudaError_t pre_gram_launch(ihsbin_problem* p);
 // G_S = (S A_hat)^T (S A_hat) from the FP64 sketch on the tensor cores (7 slices, FP64-class)
 cudaError_t sketch_gram_slices(ihsbin_problem* p, cudaStream_t st);
 uint64_t gram_slices_scratch_bytes(int64_t N, int64_t D);

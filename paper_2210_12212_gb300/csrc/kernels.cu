@@ -1664,6 +1664,11 @@ __global__ void k_diag_sum(const double* M, int64_t D, double* out) {
   if (threadIdx.x == 0) *out = part[0];
 }
 
+cudaError_t gs_trace_launch(ihsbin_problem* p, double* out, cudaStream_t st) {
+  k_diag_sum<<<1, 256, 0, st>>>(p->GS, p->A.D, out);
+  return cudaGetLastError();
+}
+
 // The residual form's default pair weight for P_l r.  Dropping the pairs s + t > w makes each
 // application of P_l wrong by about eps_w = 2^(-8(w+1)) of |P_l| |r| (relative to the row and
 // column maxima), i.e. by up to kappa eps_w relative, kappa <= 1 + tr(G_S) / lam0 bounding the
@@ -1982,6 +1987,56 @@ __global__ void k_eval_chunks(CBuf Bm, int64_t rows, int64_t K, int jc, int64_t 
 }
 
 // ============================================================ orchestration
+cudaError_t ensure_streams(ihsbin_problem* p) {
+  // Stream priorities: the factorization's chain of small dependent launches is the critical
+  // path, so its CTAs are scheduled first whenever SMs free up; the Gram's long tensor-core CTAs
+  // (lowest priority) fill the rest.
+  int prio_lo = 0, prio_hi = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+  if (!p->side) CK(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_lo));
+  if (!p->fac) CK(cudaStreamCreateWithPriority(&p->fac, cudaStreamNonBlocking, prio_hi));
+  return cudaSuccess;
+}
+
+// ihsbin_sketch starts the Gram of A and A^T b (which do not depend on the sketch) on the side
+// stream when the next build will most likely take them: dense FP32/BF16/TF32 data with the
+// right-hand side formed from the Gram's slices (K >= 32, not the dual), the float-float compute
+// mode with the sliced Gram (the defaults; or the last build's mode), and per-launch timing off
+// (its events are read at the call's own synchronisation).  The draws of the sketch, an ALU load,
+// then run beside the Gram's tensor-core work, and the build's factorization beside the rest.
+bool pre_gram_eligible(const ihsbin_problem* p) {
+  const Tall& A = p->A;
+  return !p->timing && !p->pre_off && A.layout == IHSBIN_DENSE_ROWMAJOR && A.elem != ELEM_F64 && !p->dual &&
+         p->K >= 32 &&
+         (p->last_compute < 0 || (p->last_compute == IHSBIN_COMPUTE_F32X2 && p->last_gram == IHSBIN_GRAM_SLICES));
+}
+
+cudaError_t pre_gram_launch(ihsbin_problem* p) {
+  CK(ensure_streams(p));
+  cudaStream_t s2 = p->side;
+  const int64_t D = p->A.D, K = p->K;
+  for (auto& e : p->pre_ev)
+    if (!e) CK(cudaEventCreate(&e));
+  CK(cudaEventRecord(p->pre_ev[0], s2));
+  // the SMs the Gram's launches leave free for the sketch and then the factorization beside it,
+  // tuned on the time from here to the build's join (tune_end there)
+  static const int cands[] = {40, 24, 64, 0};
+  p->pre_tune = new TuneLaunch(
+      tune_begin(tune_key(TUNE_PRE_RESERVE, D, shape_class(p->A.N), K), "pre_gram_reserve_sms", cands, 4, s2));
+  cudaError_t err = cudaSuccess;
+  p->G_pre = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)D * D, SCOPE_PRE, &err);
+  p->c_pre = alloc_cbuf(p, IHSBIN_COMPUTE_F32X2, (size_t)D * K, SCOPE_PRE, &err);
+  CK(err);
+  const CBuf G_keep = p->G;
+  p->G = p->G_pre;
+  err = gram_dense_slices(p, IHSBIN_COMPUTE_F32X2, s2, p->pre_tune->value, &p->c_pre);
+  p->G = G_keep;
+  CK(err);
+  CK(cudaEventRecord(p->pre_ev[1], s2));
+  p->gram_pre = true;
+  return cudaSuccess;
+}
+
 template <class Mode, int ET>
 static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* ev) {
   const Tall& A = p->A;
@@ -2008,24 +2063,15 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
 
   // the recursion's form (resolved after the factorization, when the plan is final): the residual
   // form is possible where the fused tensor-core recursion runs; every other configuration carries
-  // the increments of Algorithm 2 as printed.  tr(G_S) for the default pair weight is read here,
-  // where the stream is idle (the sketch call ended with a synchronisation).
+  // the increments of Algorithm 2 as printed.
   const bool oz_on = Mode::id == 1 && pl.loop == IHSBIN_LOOP_SLICES;
   const bool resid_ok = oz_on && pl.product == IHSBIN_PRODUCT_GRAM && oz_fused_ok(D) && pl.form != IHSBIN_FORM_INCREMENT;
-  double trGS = 0.0;
-  if (resid_ok && pl.precond_req == 0) {
-    double* tr_dev = nullptr;
-    CK(prob_alloc(p, sizeof(double), (void**)&tr_dev, SCOPE_SCRATCH));
-    k_diag_sum<<<1, 256, 0, st>>>(p->GS, D, tr_dev);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(&trGS, tr_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-  }
+  const double trGS = p->trGS;  // tr(G_S), read by the sketch call
 
   // SMs the Gram's tensor-core launches leave to the factorization running beside them: chosen by
   // the autotuner per shape class, timing the whole fork-join region of both streams
   const bool tune_reserve =
-      pl.product == IHSBIN_PRODUCT_GRAM && A.layout != IHSBIN_CSR && pl.gram == IHSBIN_GRAM_SLICES;
+      pl.product == IHSBIN_PRODUCT_GRAM && A.layout != IHSBIN_CSR && pl.gram == IHSBIN_GRAM_SLICES && !p->pre_taken;
   TuneLaunch rtune{};
   int gram_reserve = 0;
   if (tune_reserve) {
@@ -2037,18 +2083,17 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   // the sketched Hessian), so they run on the problem's side stream, forked here and joined
   // before the recursion: their tensor-core work fills the SMs that the factorization's small
   // launches leave idle.  Allocations in this section are ordered on the side stream.
-  // Stream priorities: the factorization's chain of small dependent launches is the critical
-  // path, so its CTAs are scheduled first whenever SMs free up; the Gram's long tensor-core CTAs
-  // (lowest priority) fill the rest.
-  int prio_lo = 0, prio_hi = 0;
-  CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
-  if (!p->side) CK(cudaStreamCreateWithPriority(&p->side, cudaStreamNonBlocking, prio_lo));
+  CK(ensure_streams(p));
   cudaStream_t s2 = p->side;
-  CK(cudaEventRecord(ev[5], st));
-  CK(cudaStreamWaitEvent(s2, ev[5], 0));
   const bool csr = A.layout == IHSBIN_CSR;
   CBuf c{};
-  {
+  if (p->pre_taken) {
+    // the Gram of A and A^T b were started by ihsbin_sketch on the side stream (joined below)
+    c = p->c_pre;
+    CK(cudaEventRecord(ev[5], st));
+  } else {
+    CK(cudaEventRecord(ev[5], st));
+    CK(cudaStreamWaitEvent(s2, ev[5], 0));
     CallStream side_alloc(s2);
     c = cb((size_t)D * K);
     CK(err);
@@ -2080,7 +2125,6 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
   // a2: factor + inverse of the shifted sketched Hessians, on the problem's second internal
   // stream (forked with the Gram's, joined before the recursion).  Allocations in this section
   // are ordered on that stream.
-  if (!p->fac) CK(cudaStreamCreateWithPriority(&p->fac, cudaStreamNonBlocking, prio_hi));
   cudaStream_t sf = p->fac;
   CK(cudaStreamWaitEvent(sf, ev[5], 0));
   {
@@ -2112,9 +2156,14 @@ static cudaError_t build_typed(ihsbin_problem* p, cudaStream_t st, cudaEvent_t* 
 
   // join both forks before the recursion
   CK(cudaStreamWaitEvent(st, ev[1], 0));
-  CK(cudaStreamWaitEvent(st, ev[2], 0));
+  CK(cudaStreamWaitEvent(st, p->pre_taken ? p->pre_ev[1] : ev[2], 0));
   CK(cudaEventRecord(ev[6], st));
   if (tune_reserve) tune_end(rtune, st);
+  if (p->pre_taken && p->pre_tune) {
+    tune_end(*p->pre_tune, st);
+    delete p->pre_tune;
+    p->pre_tune = nullptr;
+  }
 
   // a4: the recursion, in the residual form when it is possible and asked for (RESIDUAL, or an
   // explicit precond_weight) or when AUTO's pair weight is at most 4

@@ -60,7 +60,7 @@ constexpr int SK_SMEM = SK_STAGES * SK_STAGE;      // 192 KiB
 constexpr int SK_THREADS = 192;
 constexpr int SK_TMEM_COLS = 512;               // two 128 x 256 FP32 accumulators
 constexpr int SK_MARGIN = 24;                   // fall-back window around a BF16 midpoint (FP32 ulps)
-constexpr int SK_FIXBUF = 4096;                 // per-block staging of fall-back entries
+constexpr int SK_FIXBUF = 3072;                 // per-block staging of fall-back entries (24 KiB: a draw CTA fits beside a Gram CTA)
 constexpr int SK_DRAW_THREADS = 256;
 
 // A window [i0, i0 + rows) x [j0, j0 + cols) of the m x N sketch, drawn into image blocks.
