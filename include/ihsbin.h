@@ -273,7 +273,13 @@ IHSBIN_API ihsbin_status ihsbin_problem_destroy(ihsbin_problem* p);
  * (FP64-class accuracy).  Re-sketching an already sketched problem discards the basis.
  * Limits: the SRHT needs dense A, m <= N_pad and N_pad <= 2^24 rows (beyond that its
  * launches exceed the grid limits and the call fails with IHSBIN_ERR_CUDA); CountSketch and
- * Gaussian sketches take any row count. */
+ * Gaussian sketches take any row count.
+ * For dense FP32/BF16/TF32 data with K >= 32 (not the dual), and unless per-launch timing is on,
+ * the call also starts the Gram of A_hat and A_hat^T B on the problem's low-priority internal
+ * stream; it returns when the sketch is done, with that Gram still running.  The next
+ * ihsbin_build_basis takes it when it runs the float-float mode with the sliced Gram (the
+ * defaults); any other call that needs the problem's memory waits for it first.  An error of
+ * that background work is reported by the build. */
 IHSBIN_API ihsbin_status ihsbin_sketch(ihsbin_problem* p, const ihsbin_sketch_desc* sk, void* stream);
 
 /* Bit-exact export of the sketch's integer draws, for tests.
