@@ -73,3 +73,21 @@ def test_sketch_without_build(ctx):
     gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed, entries="bf16")
     gp.close()   # waits for the background Gram and frees it
     assert ctx.memory() == before
+
+
+def test_many_right_hand_sides_fp32(ctx):
+    """FP32 data with 40 right-hand sides (the background Gram, the fused right-hand side and the
+    tiled path evaluation for K >= 16) against the oracle at the float-float tolerance."""
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = make_problem("c2_small", seed=2, K=40)
+    L = ob.num_intervals(prob.lambda_min, prob.lambda_max)
+    r1, r2, kk = default_params(prob, L, 30)
+    gp = gpu_problem(ihs, ctx, prob)
+    gp.sketch(prob.sketch, prob.m, prob.s, prob.sketch_seed)
+    gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, compute="f32x2")
+    X = gp.eval_path(prob.lambdas)
+    gp.close()
+    plan = ob.make_plan(prob.lambda_min, prob.lambda_max, r1, r2, kk, L=L)
+    ref = ob.ihs_bin_path(oracle_A(prob), prob.B, prob.sketch, prob.m, prob.s, prob.sketch_seed, plan, prob.lambdas)
+    assert X.shape == ref.X.shape
+    assert rel_err_max(X, ref.X) <= 1e-9
