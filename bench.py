@@ -530,12 +530,17 @@ def main():
                                   test_dtype=prob.storage, stream=stream)
         return pp.eval_path(prob.lambdas, out=out, stream=stream)
 
-    # untimed steps until the library's autotuner has settled every launch site it met (each
-    # candidate geometry is timed on a few launches first), then the W warm-up steps
+    # untimed steps until the library's autotuner has settled every launch site the steps use (each
+    # candidate geometry is timed on a few launches first: the table stops changing), then the W
+    # warm-up steps
+    prev = None
     for _ in range(32):
-        if "chosen=-1" not in ihs.tuning_report():
-            break
         step(p, X_dev)
+        torch.cuda.synchronize()
+        rep = ihs.tuning_report()
+        if rep == prev:
+            break
+        prev = rep
     for _ in range(max(args.warmup, 0)):
         step(p, X_dev)
     torch.cuda.synchronize()
