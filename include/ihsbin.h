@@ -257,8 +257,10 @@ IHSBIN_API const char* ihsbin_last_error(void);
 /* Create a problem for A and right-hand side(s) B (n x K, row stride ldb >= K,
  * element type b_dtype, host or device per b_on_device; copied).  If n < d the
  * problem is solved through the dual (Section 5.2).  Allocates the problem's
- * device state (counted against the context budget).  Release with
- * ihsbin_problem_destroy. */
+ * device state (counted against the context budget).  CSR structure is checked on the device
+ * before any kernel indexes with it: row_ptr must run from 0 to nnz without decreasing and each
+ * row's column indices must lie in [0, d) and increase strictly; otherwise the call fails with
+ * IHSBIN_ERR_INVALID_ARG and creates nothing.  Release with ihsbin_problem_destroy. */
 IHSBIN_API ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, const void* B,
                                     int64_t K, int64_t ldb, ihsbin_dtype b_dtype, int b_on_device,
                                     ihsbin_problem** out);

@@ -400,6 +400,18 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
       ci = (const int32_t*)dci;
       val = dval;
     }
+    {  // the structure every later kernel indexes with (violations become INVALID_ARG, not faults)
+      if ((e = launch_csr_check(rp, ci, A->n, A->d, A->nnz, p->status, 0)) != cudaSuccess) return bail(e, "problem_create");
+      int st_word = 0;
+      if ((e = cudaMemcpy(&st_word, p->status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return bail(e, "problem_create");
+      if (st_word != 0) {
+        ihsbin_problem_destroy(p);
+        return fail(IHSBIN_ERR_INVALID_ARG,
+                    "problem_create: CSR structure invalid (row_ptr must run from 0 to nnz without decreasing, "
+                    "and each row's column indices must lie in [0, d) and increase)");
+      }
+    }
     if (p->tf32) {  // rounded values (in place when the copy is ours)
       float* rval = (float*)(A->on_device ? nullptr : val);
       if (!rval && (e = prob_alloc(p, (size_t)std::max<int64_t>(1, A->nnz) * 4, (void**)&rval, SCOPE_PERSIST)) != cudaSuccess)

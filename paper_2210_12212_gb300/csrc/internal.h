@@ -194,6 +194,8 @@ void tune_reset();
 // ----- kernel launchers (kernels.cu); all return the first CUDA error --------
 cudaError_t launch_transpose_dense(const void* src, int elem, int64_t rows, int64_t cols, int64_t ld,
                                    void* dst, cudaStream_t st);
+cudaError_t launch_csr_check(const int64_t* rp, const int32_t* ci, int64_t rows, int64_t cols, int64_t nnz,
+                             int* status, cudaStream_t st);
 cudaError_t launch_csr_transpose(ihsbin_problem* p, const int64_t* rp, const int32_t* ci, const void* val,
                                  int elem, int64_t rows, int64_t cols, int64_t nnz, int64_t** rpT,
                                  int32_t** ciT, void** valT, cudaStream_t st);

@@ -117,6 +117,37 @@ __global__ void k_scatter_rows(const int64_t* rp, const int32_t* ci, const E* va
   }
 }
 
+// The CSR structure a problem is created from, before any kernel indexes with it: row_ptr starts at
+// 0, never decreases and ends at nnz, and every row's column indices lie in [0, cols) and increase
+// strictly.  One thread per row; a row's columns are read only once its range has been checked.
+// A violation records DEV_BOUNDS in the status word.
+__global__ void k_csr_check(const int64_t* rp, const int32_t* ci, int64_t rows, int64_t cols, int64_t nnz,
+                            int* status) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = rp[r], b = rp[r + 1];
+    if (a < 0 || b < a || b > nnz || (r == 0 && a != 0) || (r == rows - 1 && b != nnz)) {
+      dev_fail(status, DEV_BOUNDS);
+      continue;
+    }
+    int32_t prev = -1;
+    for (int64_t k = a; k < b; ++k) {
+      const int32_t c = ci[k];
+      if (c <= prev || c >= cols) {
+        dev_fail(status, DEV_BOUNDS);
+        break;
+      }
+      prev = c;
+    }
+  }
+}
+
+cudaError_t launch_csr_check(const int64_t* rp, const int32_t* ci, int64_t rows, int64_t cols, int64_t nnz,
+                             int* status, cudaStream_t st) {
+  const int64_t blocks = std::min<int64_t>((rows + 255) / 256, 4096);
+  k_csr_check<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(rp, ci, rows, cols, nnz, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_csr_transpose(ihsbin_problem* p, const int64_t* rp, const int32_t* ci, const void* val, int elem,
                                  int64_t rows, int64_t cols, int64_t nnz, int64_t** rpT, int32_t** ciT, void** valT,
                                  cudaStream_t st) {

@@ -113,3 +113,30 @@ def test_explicit_tau(ctx, compute):
         gp.build_basis(prob.lambda_min, prob.lambda_max, L=L, k=kk, rho1=r1, rho2=r2, tau=bad, compute=compute)
     assert e.value.status == ihs.ERR_INVALID_ARG
     gp.close()
+
+
+@pytest.mark.parametrize("fault", ["column_out_of_range", "column_not_increasing", "row_ptr_decreasing",
+                                   "row_ptr_end"])
+def test_invalid_csr_structure_is_rejected(ctx, fault):
+    """CSR structure is checked on the device before any kernel indexes with it (every read of the
+    check stays inside the arrays' stated sizes), so bad input is INVALID_ARG, not a fault."""
+    import dataclasses
+    from paper_2210_12212_gb300 import ihsbin as ihs
+    prob = small("c3_small")
+    rp, ci = prob.row_ptr.copy(), prob.col_idx.copy()
+    if fault == "column_out_of_range":
+        ci[rp[7]] = prob.d                      # one past the last column
+    elif fault == "column_not_increasing":
+        ci[rp[3] + 1] = ci[rp[3]]               # a duplicate within row 3
+    elif fault == "row_ptr_decreasing":
+        rp[5] = rp[4] - 1
+    else:
+        rp[-1] = rp[-1] - 1                     # does not end at nnz
+    bad = dataclasses.replace(prob, row_ptr=rp, col_idx=ci)
+    before = ctx.memory()
+    with pytest.raises(ihs.IhsbinError) as e:
+        gpu_problem(ihs, ctx, bad)
+    assert e.value.status == ihs.ERR_INVALID_ARG
+    assert ctx.memory() == before
+    gp = gpu_problem(ihs, ctx, prob)           # the valid structure still goes through
+    gp.close()
