@@ -21,15 +21,21 @@
 // int64 (two Horner groups); the conversion to float-float uses FP32 operations only.
 // Accuracy: every operand entry is held to 2^-47 of its row's (column's) largest
 // magnitude and the dropped pairs weigh at most 2^-52 of the leading product, the
-// accuracy class of the float-float contraction these products replace.
+// accuracy class of the float-float contraction these products replace.  A product may
+// keep fewer pairs, s + t <= wmax (the residual form's P_l r: its errors are corrected by
+// the later steps of the recursion); it then reads only the slices 0 .. wmax of each
+// block, and with wmax <= 3 it runs on 128 x 64 tiles (four accumulators of 64 columns fit
+// the Tensor Memory twice).
 //
 // Kernel roles (persistent: one CTA per SM walks the work items, a work item being a
 // 128-row tile x NT-column tile x group x k-range): warp 0 (one lane) streams each
-// k-block's 6 A slices (48 KiB) and 6 B slices with two bulk copies into a ring of
-// stages; warp 1 owns the Tensor Memory and one lane issues the 52 MMAs (M = 128,
-// N = NT, K = 16) of a stage; the epilogue warps drain finished accumulators into
-// int32 while the MMAs of the next chunk (of this or the next item) run into the
-// other buffer.  All waits are bounded in time (DEV_TIMEOUT in the status word).
+// k-block's A slices (up to 48 KiB) and B slices with two bulk copies into a ring of
+// stages; warp 1 owns the Tensor Memory and one lane issues one MMA per A slice and
+// K = 16 step (M = 128, N = the stacked B slices it meets); the epilogue warps, each
+// warpgroup on its own columns, drain finished accumulators into int32 while the MMAs of
+// the next chunk (of this or the next item) run into the other buffer, and write either
+// the exact int64 partials or, for a product with one k-split, the joined float-float
+// value itself.  All waits are bounded in time (DEV_TIMEOUT in the status word).
 #include <algorithm>
 #include <cfloat>
 
