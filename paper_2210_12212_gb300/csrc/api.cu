@@ -443,7 +443,10 @@ ihsbin_status ihsbin_problem_create(ihsbin_ctx* ctx, const ihsbin_matrix* A, con
   // B -> device FP64, packed n x K
   if ((e = prob_alloc(p, (size_t)A->n * K * 8, (void**)&p->B, SCOPE_PERSIST)) != cudaSuccess) return bail(e, "problem_create");
   const size_t bes = elem_size(b_dtype);
-  if (!b_on_device) {
+  if (!b_on_device && b_dtype == IHSBIN_F64 && ldb == K) {
+    // packed FP64 rows: one copy straight from the caller's buffer (DMA when it is pinned)
+    e = cudaMemcpy(p->B, B, (size_t)A->n * K * 8, cudaMemcpyHostToDevice);
+  } else if (!b_on_device) {
     std::vector<double> hb((size_t)A->n * K);
     for (int64_t i = 0; i < A->n; ++i)
       for (int64_t r = 0; r < K; ++r)
